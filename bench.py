@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark: Euler+Newton path-steps/s of hpt_step at n=16, 65,536 paths.
+
+One "step" is one hpt_step call with nsteps=1 over all 65,536 paths of the
+throughput workload (random Laurent system, n=16, 32 monomials/equation,
+4 nonzero exponents in [-3,3] per monomial, alpha in [-8,8]^16, lifting in
+{0..64}, beta the lower envelope; points y_j = exp(g + i phi), g ~ N(0,1),
+phi ~ U[0,2pi), t ~ U(0,1)): evaluation of H, H_y, H_tau (log, exponent
+GEMM, complex exp, coefficient GEMM, diag(1/y) scaling), the consolidated
+Euler+Newton LU solve and the step control, for every path.  The state is
+restored before every timed step (so every step does the same work on all
+paths) and L2 is flushed by a 256 MiB write between timed steps.
+
+The headline value is the mixed split-BF16/FP32 tensor-core form; the plain
+FP64 form is measured in the same run.  --impl reference times the CPU
+oracle (complex128, OpenMP over paths) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_VARS, M_PER_EQ, PATHS = 16, 32, 65536
+WORKLOAD = ("random Laurent system n=16, 32 monomials/equation (M=512), 4 nonzero exponents "
+            "in [-3,3] per monomial, alpha in [-8,8]^16, lifting {0..64}; 65,536 paths; one "
+            "hpt_step (evaluate + consolidated Euler/Newton solve + step control) per step")
+METRIC = "Euler+Newton steps/s at n=16, 64K paths: mixed vs FP64 form, % of roofline"
+UNIT = "path-steps/s"
+
+# algorithmic work per path-step (dense within each equation's block)
+FLOP_EXP_GEMM = 2 * (2 * N_VARS + 1) * N_VARS * M_PER_EQ          # 33,792
+FLOP_COEF_GEMM = 8 * (N_VARS + 2) * N_VARS * M_PER_EQ             # 73,728
+CEXP = N_VARS * M_PER_EQ                                           # 512
+n = N_VARS
+FLOP_LU = 8 * (n - 1) * n * (2 * n - 1) // 6 + 6 * n * (n - 1) // 2
+FLOP_SOLVE = 16 * n * n + 16 * n
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def shard_seed(rank: int) -> int:
+    """Weak scaling: every rank tracks its own 65,536 paths (seed 1 + rank)."""
+    return 1 + rank
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self._proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        time.sleep(0.2)
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _workload():
+    import workloads as W
+    sysm, alpha = W.config3(N_VARS, M_PER_EQ)
+    cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
+    return sysm, cell
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, valid only while
+    the kernel's source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2111_14317_gb300", "csrc", rec["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
+        return None
+    return rec["bytes_per_launch_full"]
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2111_14317_gb300 import build as hbuild
+    hbuild.build()
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    sysm, cell = _workload()
+    y_np, t_np = W.random_points(shard_seed(rank), PATHS, N_VARS)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for form, prec in (("mixed", hpt.HPT_MIXED), ("fp64", hpt.HPT_FP64)):
+        h = hpt.System.from_laurent(sysm, cell, prec)
+        prm = hpt.Params(tol_accept=3e-3 if prec == hpt.HPT_MIXED else 1e-3)
+        st = hpt.PathState(PATHS, N_VARS, prec, device=dev)
+        yd = torch.from_numpy(y_np).to(dev, h.cdtype)
+        st.y.copy_(yd)
+        st.y_acc.copy_(yd)
+        st.tau.copy_(torch.from_numpy(np.log(t_np)))
+        st.tau_acc.copy_(st.tau)
+        st.dtau.fill_(0.01)
+        st.accepts.fill_(1)
+        pristine = {k: v.clone() for k, v in st.to_host().items()}
+        pristine_dev = {k: v.to(dev) for k, v in pristine.items()}
+
+        def restore():
+            for k, v in pristine_dev.items():
+                getattr(st, k).copy_(v)
+
+        steps = args.steps if form == "mixed" else max(3, min(args.steps, args.fp64_steps))
+        for _ in range(args.warmup):
+            restore()
+            h.step(st, 1, prm)
+        torch.cuda.synchronize()
+
+        def timed(profile):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            h.profile(profile)
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            for i in range(steps):
+                restore()
+                flush.zero_()
+                ev[i][0].record()
+                h.step(st, 1, prm)
+                ev[i][1].record()
+            torch.cuda.synchronize()
+            if ws > 1:
+                dist.barrier()
+            h.profile(False)
+            return [a.elapsed_time(b) for a, b in ev]
+
+        # headline pass (no per-kernel events), clocks sampled meanwhile
+        with ClockSampler(local) as clk:
+            ms = timed(False)
+        tot = sum(ms)
+        if ws > 1:
+            t = torch.tensor([tot], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        # second pass: CUDA events around every kernel on the launching stream
+        timed(True)
+        kern = h.profile_read()
+        # end-to-end through the C ABI: pinned host state -> device, step, -> host
+        host = {k: v.pin_memory() for k, v in pristine.items()}
+        back = {k: torch.empty_like(v).pin_memory() for k, v in pristine.items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        e2e_steps = max(3, steps // 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for k, v in host.items():
+                getattr(st, k).copy_(v, non_blocking=True)
+            h.step(st, 1, prm)
+            for k, v in back.items():
+                v.copy_(getattr(st, k), non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        out[form] = dict(steps=steps, ms_per_step=tot / steps, ms_list=ms, kernels=kern,
+                         clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=h2d,
+                         launches=sum(v[0] for v in kern.values()))
+        assert h.device_error() == 0, "device-side wait timed out"
+        h.close()
+        del st, pristine_dev
+        torch.cuda.empty_cache()
+    if ws > 1:
+        dist.destroy_process_group()
+    return out, ws, rank
+
+
+def cpu_baseline(seconds=12.0, max_paths=PATHS):
+    """Times the oracle's step (as it stands) on growing slices of the same
+    workload until about `seconds` of work is done."""
+    import oracle
+    import workloads as W
+    from oracle import cells
+    sysm, cell = _workload()
+    te = cells.t_exponents(sysm, cell)
+    osys = oracle.System(sysm, te["e"], te["D"])
+    y, t = W.random_points(1, PATHS, N_VARS)
+    P = oracle.Params()
+    done, el, q0, chunk = 0, 0.0, 0, 256
+    while el < seconds and done < max_paths:
+        cnt = min(chunk, PATHS - q0)
+        st = oracle.PathState.start(y[q0:q0 + cnt], 0.0, 0.01)
+        st.tau[:] = np.log(t[q0:q0 + cnt])
+        st.tauacc[:] = st.tau
+        st.accepts[:] = 1
+        t0 = time.perf_counter()
+        osys.step(P, st, 1)
+        el += time.perf_counter() - t0
+        done += cnt
+        q0 = (q0 + cnt) % PATHS
+        chunk = min(chunk * 2, 8192)
+    return done / el, oracle.num_threads(), f"{done} of the {PATHS} paths, one step each, complex128 oracle"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    ws, rank, _ = _dist()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ms = []
+        for _ in range(args.warmup):
+            cpu_baseline(0.5)
+        vals = []
+        for _ in range(args.steps):
+            v, cores, sample = cpu_baseline(max(1.0, args.cpu_seconds / max(args.steps, 1)))
+            vals.append(v)
+        val = statistics.median(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": PATHS / val * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_VARS, "m": M_PER_EQ,
+                                                 "paths": PATHS},
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": sample + " per step"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    out, ws, rank = run_gpu(args)
+    if rank != 0:
+        return
+    peaks, peak_kind = _peaks()
+    mx, fp = out["mixed"], out["fp64"]
+    value = ws * PATHS / (mx["ms_per_step"] * 1e-3)
+    fp_value = ws * PATHS / (fp["ms_per_step"] * 1e-3)
+    # per-kernel roofline of the mixed step
+    kinfo = {}
+    for name, (launches, msum) in mx["kernels"].items():
+        avg = msum / max(launches, 1) * 1e-3
+        paths_per_launch = PATHS * mx["steps"] / max(launches, 1)
+        if name.startswith("eval_mixed"):
+            flops = (FLOP_EXP_GEMM + FLOP_COEF_GEMM) * paths_per_launch
+            ach = flops / avg / 1e12
+            kinfo[name] = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
+                           "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "ms_avg": avg * 1e3,
+                           "launches": launches, "share": msum}
+        else:
+            byts = paths_per_launch * (N_VARS * (N_VARS + 2) * 8 + 3 * N_VARS * 8 * 2 + 3 * 8 * 2 + 5 * 4 * 2)
+            ach = byts / avg / 1e9
+            kinfo[name] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": ach / peaks["hbm_gbs"], "ms_avg": avg * 1e3, "launches": launches,
+                           "share": msum}
+    total_k = sum(v["share"] for v in kinfo.values()) or 1.0
+    for v in kinfo.values():
+        v["share"] = v["share"] / total_k
+    dom = max(kinfo, key=lambda k: kinfo[k]["share"])
+    roof = {k: kinfo[dom][k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+    roof["kernel"] = dom
+    roof["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json, burst)"
+    roof["traffic"] = _traffic(dom)
+    cpu_v, cores, sample = cpu_baseline(args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": mx["steps"],
+        "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3-split/f32 (mixed form)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_VARS, "m": M_PER_EQ, "paths": PATHS,
+                   "steps_per_call": 1, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{ws} (paths shard, no collective)"},
+        "fp64_form": {"value": fp_value, "unit": UNIT, "ms_per_step": fp["ms_per_step"],
+                      "steps": fp["steps"], "kernels": {k: {"launches": v[0], "ms": v[1]}
+                                                        for k, v in fp["kernels"].items()}},
+        "mixed_vs_fp64": value / fp_value,
+        "roofline": roof,
+        "kernels": kinfo,
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": ws * PATHS / mx["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": mx["h2d"],
+                "d2h_bytes_per_step": mx["d2h"]},
+        "clocks": mx["clocks"],
+        "gpu_launches": mx["launches"],
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

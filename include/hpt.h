@@ -1,0 +1,238 @@
+/*
+ * hpt.h -- C ABI of libhpt, a GB300 (sm_103a) implementation of the data-parallel
+ * core of a polyhedral-homotopy path tracker (T. Chen, "GPU-accelerated path
+ * tracker for polyhedral homotopy", arXiv:2111.14317).
+ *
+ * What the library computes, for a square Laurent system F = (f_1..f_n),
+ * f_k(x) = sum_{a in S_k} c_{k,a} x^a (Section 2), an integer lifting w and a
+ * cell (alpha, beta) of the lifted supports:
+ *
+ *   H_k(y, t) = sum_{a in S_k} c_{k,a} y^a t^{s_{k,a}},
+ *   s_{k,a}   = <a, alpha> + w_k(a) - beta_k = e_{k,a} / D   (e integer, D >= 1),
+ *
+ * i.e. the polyhedral homotopy of eq. (1) after the change of variables
+ * x = y t^alpha and division of h_k by t^{beta_k}; H(y, 1) = F(y).  The path
+ * parameter is tau = ln t (Section 2.1, eq. (2)); tracking runs from tau0 < 0
+ * to tau = 0.
+ *
+ * Evaluation follows Section 5: z = log y (eq. (6)), the monomials of every
+ * point are exp of one row of Z A (eq. (7)), and [D_z h_k | D_tau h_k | h_k]
+ * = e^{Z A} B_k^T with B_k = [A diag(c_k); c_k^T] (eq. (8) and the extended
+ * Jacobian that follows), scaled by diag(e^{-z}, 1, 1) to y-coordinates.  The
+ * Euler direction dE and the Newton direction dN (Section 2.3, affine form)
+ * come from one factorisation of H_y with two right-hand sides, the affine
+ * counterpart of the consolidated system eq. (11) of Section 6:
+ *
+ *   H_y [dE dN] = [-H_tau, -H].
+ *
+ * Conventions for every entry point:
+ *   - Complex numbers are interleaved (re, im).  HPT_FP64 systems use
+ *     complex128 (2 doubles) for y and every output; HPT_MIXED systems use
+ *     complex64 (2 floats) for y, the step state and hpt_eval's outputs.
+ *     Track outputs and the adjoint are always complex128.
+ *   - Pointers named *_dev are device pointers owned by the caller; the
+ *     library never frees them.  The library owns the handle's constants and
+ *     its scratch (per-handle, grown on demand by cudaMalloc, released by
+ *     hpt_destroy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; only hpt_track and the host-side
+ *     getters synchronise.
+ *   - A handle may be used by one host thread at a time.
+ *   - The library never aborts and has no CPU fallback.  Argument errors are
+ *     returned as status codes; per-path numerical failures go to the per-path
+ *     status arrays, never to the return code.  hpt_last_error() returns a
+ *     message for the last failing call of the calling thread.
+ *   - Device-side waits are bounded; a wait that gives up sets a flag that
+ *     hpt_device_error() reports as HPT_ETIMEOUT.
+ */
+#ifndef HPT_H_
+#define HPT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hpt_system_s* hpt_system;
+
+typedef enum {
+  HPT_OK = 0,
+  HPT_EINVAL = 1,    /* bad argument (null pointer, size out of range, bad enum) */
+  HPT_ENOMEM = 2,    /* device or host allocation failed */
+  HPT_ECUDA = 3,     /* a CUDA runtime call failed */
+  HPT_ERANGE = 4,    /* integer overflow, or a value not exactly representable in
+                        the precision form that needs it */
+  HPT_ENOTCELL = 5,  /* the cell is singular, not a lower facet, or the lifting is
+                        not generic for it */
+  HPT_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+  HPT_ENOTSUP = 7    /* shape not supported by the requested precision form */
+} hpt_status;
+
+typedef enum { HPT_FP64 = 0, HPT_MIXED = 1 } hpt_precision;
+
+/* Per-path status codes written by hpt_step / hpt_track. */
+typedef enum {
+  HPT_PATH_ACTIVE = 0,
+  HPT_PATH_CONVERGED = 1,   /* reached tau = 0 (then polished by hpt_track) */
+  HPT_PATH_DIVERGED = 2,    /* |y_j| left [1/div_bound, div_bound] */
+  HPT_PATH_UNDERFLOW = 3,   /* step size fell below dtau_min */
+  HPT_PATH_SINGULAR = 4,    /* singular or non-finite system before any accept */
+  HPT_PATH_MAX_STEPS = 5    /* step budget exhausted */
+} hpt_path_status;
+
+typedef enum { HPT_CELL_PAIRS = 0, HPT_CELL_EXPLICIT = 1, HPT_CELL_LOWER = 2 } hpt_cell_kind;
+
+/* Cell of the lifted supports (Section 2 defers the cell step to Huber and
+ * Sturmfels; these are its three standard descriptions).
+ *   HPT_CELL_PAIRS:    pairs[2k], pairs[2k+1] are two local monomial indices of
+ *                      S_k.  alpha solves V alpha = (w_{k,p0} - w_{k,p1})_k with
+ *                      V_k = a_{k,p1} - a_{k,p0}; D is the least positive common
+ *                      denominator of alpha; alpha_num = D alpha; beta_num_k =
+ *                      <a_{k,p0}, alpha_num> + D w_{k,p0}.  Every other monomial
+ *                      must get e > 0 (HPT_ENOTCELL otherwise).
+ *   HPT_CELL_EXPLICIT: alpha_num (n), beta_num (n), denom = D > 0 as given;
+ *                      every e must be >= 0.
+ *   HPT_CELL_LOWER:    alpha_num (n), denom = D > 0; beta_num_k = min over S_k of
+ *                      <a, alpha_num> + D w(a) (so min_i e_{k,i} = 0).
+ * In all kinds e_{k,i} = <a_{k,i}, alpha_num> + D w_{k,i} - beta_num_k.      */
+typedef struct {
+  int32_t kind;
+  const int32_t* pairs;      /* 2n, kind PAIRS */
+  const int64_t* alpha_num;  /* n, kinds EXPLICIT and LOWER */
+  const int64_t* beta_num;   /* n, kind EXPLICIT */
+  int64_t denom;             /* kinds EXPLICIT and LOWER */
+} hpt_cell;
+
+/* Step-size control (the paper fixes one Euler prediction and one Newton
+ * iteration per step, Section 8; the control rule is this library's).  A
+ * step evaluates at the predicted point y(tau); it is accepted when
+ * |dN|_inf / max(1, |y|_inf) <= tol_accept; then y_acc = y + dN, and after
+ * grow_after accepts in a row dtau = min(grow * dtau, dtau_max).  On reject
+ * dtau *= shrink (below dtau_min: HPT_PATH_UNDERFLOW).  The next prediction is
+ * y = y_acc + h dE_acc, tau = tau_acc + h, h = min(dtau, -tau_acc).  Before the
+ * first accept a rejected step keeps correcting at tau0 (y += dN).            */
+typedef struct {
+  double tol_accept;    /* default 1e-3 (FP64) -- use 3e-3 for HPT_MIXED */
+  double dtau_init;     /* default 0.05 */
+  double dtau_min;      /* default 1e-8 */
+  double dtau_max;      /* default 0.5 */
+  double grow;          /* default 2 */
+  double shrink;        /* default 0.5 */
+  int32_t grow_after;   /* default 3 */
+  int32_t max_steps;    /* default 10000 */
+  double div_bound;     /* default 1e8 */
+  double polish_tol;    /* default 1e-13: FP64 Newton polish at t = 1 stops below */
+  int32_t polish_iters; /* default 8 */
+  int32_t check_every;  /* hpt_track: steps between host checks, default 32 */
+  double cond_max;      /* HPT_MIXED: pivot-ratio bound above which the solve is
+                           redone in FP64, default 1e6 */
+  double eps0;          /* tau0 = ln(eps0) / s_min (smallest positive e/D), default 1e-10 */
+} hpt_params;
+
+/* Structure-of-arrays path state (caller-owned device buffers, p paths).
+ * y, y_acc, dE_acc: p x n complex of the system's precision, row-major. */
+typedef struct {
+  void* y;            /* predicted point at tau */
+  double* tau;
+  double* dtau;
+  void* y_acc;        /* last accepted (corrected) point */
+  double* tau_acc;
+  void* dE_acc;       /* Euler direction at the last accepted point */
+  int32_t* status;    /* hpt_path_status */
+  int32_t* steps;     /* step attempts */
+  int32_t* accepts;
+  int32_t* rejects;
+  int32_t* streak;    /* accepts in a row since the last growth or reject */
+} hpt_paths;
+
+/* Fills the defaults listed in hpt_params. */
+void hpt_default_params(hpt_params* out);
+
+const char* hpt_status_string(hpt_status s);
+const char* hpt_last_error(void);
+
+/* Host-only exact bookkeeping (no device work; usable without a GPU).
+ * Inputs: n (1..32); support_sizes[n] = m_k >= 1 (pairs need m_k >= 2);
+ * exponents[M*n] int32, row-major, grouped by equation (M = sum m_k);
+ * lifting[M] int64; cell as above.  Outputs (any may be NULL): texp[M] the
+ * numerators e, *denom D, alpha_num[n], beta_num[n].  Exact int64 arithmetic
+ * with 128-bit intermediates; HPT_ERANGE on overflow, HPT_ENOTCELL as above. */
+hpt_status hpt_lift_exponents(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
+                              const int64_t* lifting, const hpt_cell* cell, int64_t* texp,
+                              int64_t* denom, int64_t* alpha_num, int64_t* beta_num);
+
+/* Algorithm 1 (Initialize): exact bookkeeping as hpt_lift_exponents, then one
+ * upload of the constants (A with the t-exponent row, B_k for every k, and for
+ * HPT_MIXED their split-BF16 operand images) to the current device.
+ * coeffs[2M] are c_{k,i} as (re, im) doubles.  HPT_MIXED needs |a_j| <= 256 and
+ * sum_j |a_j| <= 64 for every monomial (HPT_ERANGE), n <= 32, m_k <= 128
+ * (HPT_ENOTSUP).  *out receives the handle. */
+hpt_status hpt_create_system(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
+                             const double* coeffs, const int64_t* lifting, const hpt_cell* cell,
+                             hpt_precision prec, hpt_system* out);
+
+hpt_status hpt_destroy(hpt_system sys);
+
+/* Host getters: sizes, form, tau0 for params->eps0 (NULL = default), and the
+ * exact integer data the handle was built from (arrays may be NULL). */
+hpt_status hpt_get_info(hpt_system sys, int32_t* n, int32_t* M, int32_t* prec, double eps0,
+                        double* tau0);
+hpt_status hpt_get_texp(hpt_system sys, int64_t* texp, int64_t* denom, int64_t* alpha_num,
+                        int64_t* beta_num);
+
+/* Algorithm 2 (Evaluate) for p points: y_dev[p*n] complex, t_dev[p] doubles
+ * in (0, 1].  Writes H_dev[p*n] (H_k), Hy_dev[p*n*n] (dH_k/dy_j at [q][k][j])
+ * and Ht_dev[p*n] (dH_k/dt = (dH_k/dtau) / t), complex of the system's
+ * precision.  Any output pointer may be NULL.  p = 0 is a no-op. */
+hpt_status hpt_eval(hpt_system sys, int64_t p, const void* y_dev, const double* t_dev,
+                    void* H_dev, void* Hy_dev, void* Ht_dev, void* stream);
+
+/* Prepares a path state for tracking from start points y0_dev[p*n] complex128
+ * at tau0 (from params->eps0): y = y_acc = y0, tau = tau_acc = tau0,
+ * dtau = dtau_init, dE_acc = 0, counters 0, status ACTIVE. */
+hpt_status hpt_paths_init(hpt_system sys, int64_t p, const void* y0_dev, const hpt_params* params,
+                          const hpt_paths* state, void* stream);
+
+/* nsteps Euler-Newton steps (Section 8: one Euler prediction, one Newton
+ * iteration) for every ACTIVE path of the state (Algorithms 2 and 3 per step).
+ * Paths that are not ACTIVE are left unchanged. */
+hpt_status hpt_step(hpt_system sys, int64_t p, const hpt_paths* state, int32_t nsteps,
+                    const hpt_params* params, void* stream);
+
+/* Whole tracks: start points y0_dev[p*n] complex128 at tau0 -> tau = 0, then an
+ * FP64 Newton polish at t = 1 of the converged paths.  Writes x_out_dev[p*n]
+ * complex128, status_dev[p], steps_dev[p].  Synchronises the stream. */
+hpt_status hpt_track(hpt_system sys, int64_t p, const void* y0_dev, const hpt_params* params,
+                     void* x_out_dev, int32_t* status_dev, int32_t* steps_dev, void* stream);
+
+/* FP64 Newton polish at t = 1 of x_dev[p*n] complex128 in place, for paths
+ * whose status_dev entry is HPT_PATH_CONVERGED (status_dev NULL: all paths). */
+hpt_status hpt_polish(hpt_system sys, int64_t p, void* x_dev, const int32_t* status_dev,
+                      const hpt_params* params, void* stream);
+
+/* Implicit-function adjoint at solutions x_dev[p*n] complex128 of F = H(., 1):
+ * with J = F_x and gx_dev[p*n] = dL/dRe x + i dL/dIm x of a real loss L, solves
+ * J^H lambda = gx per solution and writes gc_dev[M] complex128 =
+ * -sum over solutions of lambda_k conj(x^{a_{k,i}}), the gradient of L with
+ * respect to the coefficients in the same convention (FP64). */
+hpt_status hpt_adjoint(hpt_system sys, int64_t p, const void* x_dev, const void* gx_dev,
+                       void* gc_dev, void* stream);
+
+/* Reads and clears the handle's device error flag (synchronises the device):
+ * HPT_OK or HPT_ETIMEOUT. */
+hpt_status hpt_device_error(hpt_system sys);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel the handle launches while enabled.  hpt_profile_read returns,
+ * for up to cap kernels, the name, the number of launches and the summed
+ * milliseconds (synchronises), and the number of distinct kernels. */
+hpt_status hpt_profile_enable(hpt_system sys, int32_t enable);
+hpt_status hpt_profile_read(hpt_system sys, int32_t cap, const char** names, int64_t* launches,
+                            double* ms, int32_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPT_H_ */

@@ -1,0 +1,275 @@
+// Entry points of libhpt that enqueue device work: hpt_eval, hpt_paths_init,
+// hpt_step, hpt_track, hpt_polish, hpt_adjoint.
+#include <string.h>
+
+#include <algorithm>
+
+#include "hpt_internal.h"
+
+namespace hpt {
+namespace {
+
+// Paths per evaluate/solve round of hpt_step: the extended Jacobian of a
+// chunk (n (n+2) complex per path) stays resident in L2 between the two
+// kernels.  A multiple of the tensor-core tile.
+constexpr int64_t kChunk = 32768;
+
+inline size_t csize(const hpt_system s) { return s->prec == HPT_FP64 ? 16 : 8; }
+
+hpt_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? HPT_ENOMEM : HPT_ECUDA;
+}
+
+hpt_status check_params(const hpt_params* prm) {
+  if (!prm) { set_error("params is NULL"); return HPT_EINVAL; }
+  if (!(prm->tol_accept > 0) || !(prm->dtau_init > 0) || !(prm->dtau_min > 0) ||
+      !(prm->dtau_max >= prm->dtau_min) || !(prm->grow >= 1) || !(prm->shrink > 0 && prm->shrink < 1) ||
+      prm->grow_after < 1 || prm->max_steps < 1 || !(prm->div_bound > 1) || !(prm->polish_tol > 0) ||
+      prm->polish_iters < 0) {
+    set_error("params out of range");
+    return HPT_EINVAL;
+  }
+  return HPT_OK;
+}
+
+hpt_paths offset_paths(const hpt_paths& S, int64_t q0, int n, size_t cs) {
+  hpt_paths o = S;
+  o.y = (char*)S.y + q0 * n * cs;
+  o.y_acc = (char*)S.y_acc + q0 * n * cs;
+  o.dE_acc = (char*)S.dE_acc + q0 * n * cs;
+  o.tau = S.tau + q0;
+  o.dtau = S.dtau + q0;
+  o.tau_acc = S.tau_acc + q0;
+  o.status = S.status + q0;
+  o.steps = S.steps + q0;
+  o.accepts = S.accepts + q0;
+  o.rejects = S.rejects + q0;
+  o.streak = S.streak + q0;
+  return o;
+}
+
+cudaError_t eval_form(hpt_system s, int64_t p, const void* y, const double* tau, int tau_is_t,
+                      const EvalOut& out, cudaStream_t st) {
+  return s->prec == HPT_FP64 ? launch_eval_fp64(s, p, y, tau, tau_is_t, out, st)
+                             : launch_eval_mixed(s, p, y, tau, tau_is_t, out, st);
+}
+
+hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps,
+                     const hpt_params& prm, cudaStream_t st) {
+  const int n = s->n;
+  const int64_t chunk = std::min<int64_t>(p, kChunk);
+  hpt_status rc = ensure_scratch(s, (size_t)chunk * n * (n + 2) * csize(s));
+  if (rc) return rc;
+  for (int r = 0; r < nsteps; ++r) {
+    for (int64_t q0 = 0; q0 < p; q0 += chunk) {
+      const int64_t cnt = std::min(chunk, p - q0);
+      hpt_paths sub = offset_paths(S, q0, n, csize(s));
+      EvalOut out;
+      out.ext = s->d_scratch;
+      cudaError_t e = eval_form(s, cnt, sub.y, sub.tau, 0, out, st);
+      if (e != cudaSuccess) return cuda_fail(e, "evaluation launch");
+      StepArgs a;
+      a.n = n;
+      a.p = cnt;
+      a.ext = s->d_scratch;
+      a.st = sub;
+      a.prm = prm;
+      a.err = s->d_err;
+      e = launch_solve_update(s, a, st);
+      if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+    }
+  }
+  return HPT_OK;
+}
+
+hpt_status polish_impl(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm,
+                       cudaStream_t st) {
+  const int n = s->n;
+  const int64_t chunk = std::min<int64_t>(p, kChunk);
+  hpt_status rc = ensure_scratch(s, (size_t)chunk * n * (n + 2) * 16);
+  if (rc) return rc;
+  for (int it = 0; it < prm.polish_iters; ++it) {
+    for (int64_t q0 = 0; q0 < p; q0 += chunk) {
+      const int64_t cnt = std::min(chunk, p - q0);
+      EvalOut out;
+      out.ext = s->d_scratch;
+      void* xq = (char*)x + q0 * n * 16;
+      cudaError_t e = launch_eval_fp64(s, cnt, xq, nullptr, 0, out, st);
+      if (e != cudaSuccess) return cuda_fail(e, "polish evaluation launch");
+      e = launch_newton_update(s, cnt, s->d_scratch, xq, done + q0, prm.polish_tol, st);
+      if (e != cudaSuccess) return cuda_fail(e, "polish update launch");
+    }
+  }
+  return HPT_OK;
+}
+
+hpt_status check_sys(hpt_system s) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device) {
+    set_error("the handle belongs to device %d, current device is %d", s->device, dev);
+    return HPT_EINVAL;
+  }
+  return HPT_OK;
+}
+
+}  // namespace
+}  // namespace hpt
+
+using namespace hpt;
+
+extern "C" {
+
+hpt_status hpt_eval(hpt_system s, int64_t p, const void* y, const double* t, void* H, void* Hy,
+                    void* Ht, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
+  if (p == 0) return HPT_OK;
+  if (!y || !t) { set_error("y or t is NULL"); return HPT_EINVAL; }
+  if (!H && !Hy && !Ht) return HPT_OK;
+  EvalOut out;
+  out.H = H;
+  out.Hy = Hy;
+  out.Ht = Ht;
+  cudaError_t e = eval_form(s, p, y, t, 1, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "evaluation launch");
+  return HPT_OK;
+}
+
+hpt_status hpt_paths_init(hpt_system s, int64_t p, const void* y0, const hpt_params* prm,
+                          const hpt_paths* S, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if ((rc = check_params(prm))) return rc;
+  if (p < 0 || !S) { set_error("bad p or state"); return HPT_EINVAL; }
+  if (p == 0) return HPT_OK;
+  if (!y0 || !S->y || !S->y_acc || !S->dE_acc || !S->tau || !S->dtau || !S->tau_acc ||
+      !S->status || !S->steps || !S->accepts || !S->rejects || !S->streak) {
+    set_error("NULL pointer in the path state");
+    return HPT_EINVAL;
+  }
+  double tau0 = 0;
+  hpt_get_info(s, nullptr, nullptr, nullptr, prm->eps0, &tau0);
+  cudaError_t e = launch_paths_init(s, p, y0, tau0, *prm, *S, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "init launch");
+  return HPT_OK;
+}
+
+hpt_status hpt_step(hpt_system s, int64_t p, const hpt_paths* S, int32_t nsteps,
+                    const hpt_params* prm, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if ((rc = check_params(prm))) return rc;
+  if (p < 0 || !S || nsteps < 0) { set_error("bad p, state or nsteps"); return HPT_EINVAL; }
+  if (p == 0 || nsteps == 0) return HPT_OK;
+  if (!S->y || !S->y_acc || !S->dE_acc || !S->tau || !S->dtau || !S->tau_acc || !S->status ||
+      !S->steps || !S->accepts || !S->rejects || !S->streak) {
+    set_error("NULL pointer in the path state");
+    return HPT_EINVAL;
+  }
+  return step_impl(s, p, *S, nsteps, *prm, (cudaStream_t)stream);
+}
+
+hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* prm, void* x_out,
+                     int32_t* status_out, int32_t* steps_out, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if ((rc = check_params(prm))) return rc;
+  if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
+  if (p == 0) return HPT_OK;
+  if (!y0 || !x_out) { set_error("y0 or x_out is NULL"); return HPT_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = s->n;
+  const size_t cs = csize(s);
+  // state layout inside the library's track scratch
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  const size_t o_y = take(p * n * cs), o_ya = take(p * n * cs), o_de = take(p * n * cs);
+  const size_t o_tau = take(p * 8), o_dt = take(p * 8), o_ta = take(p * 8);
+  const size_t o_st = take(p * 4), o_sp = take(p * 4), o_ac = take(p * 4), o_rj = take(p * 4),
+               o_sk = take(p * 4), o_done = take(p * 4), o_cnt = take(4);
+  if ((rc = ensure_track(s, off))) return rc;
+  char* b = (char*)s->d_track;
+  hpt_paths S;
+  S.y = b + o_y;
+  S.y_acc = b + o_ya;
+  S.dE_acc = b + o_de;
+  S.tau = (double*)(b + o_tau);
+  S.dtau = (double*)(b + o_dt);
+  S.tau_acc = (double*)(b + o_ta);
+  S.status = (int32_t*)(b + o_st);
+  S.steps = (int32_t*)(b + o_sp);
+  S.accepts = (int32_t*)(b + o_ac);
+  S.rejects = (int32_t*)(b + o_rj);
+  S.streak = (int32_t*)(b + o_sk);
+  int32_t* done = (int32_t*)(b + o_done);
+  int32_t* cnt = (int32_t*)(b + o_cnt);
+  if ((rc = hpt_paths_init(s, p, y0, prm, &S, stream))) return rc;
+  const int every = prm->check_every > 0 ? prm->check_every : 32;
+  int64_t total = 0;
+  for (;;) {
+    if ((rc = step_impl(s, p, S, every, *prm, st))) return rc;
+    total += every;
+    cudaError_t e = launch_count_active(p, S.status, cnt, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_count, cnt, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "active-path count");
+    if (*s->h_count == 0 || total > (int64_t)prm->max_steps + every) break;
+  }
+  cudaError_t e = launch_finish_track(s, p, S, x_out, status_out, steps_out, done, st);
+  if (e != cudaSuccess) return cuda_fail(e, "track output");
+  if ((rc = polish_impl(s, p, x_out, done, *prm, st))) return rc;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "track");
+  return HPT_OK;
+}
+
+hpt_status hpt_polish(hpt_system s, int64_t p, void* x, const int32_t* status, const hpt_params* prm,
+                      void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if ((rc = check_params(prm))) return rc;
+  if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
+  if (p == 0) return HPT_OK;
+  if (!x) { set_error("x is NULL"); return HPT_EINVAL; }
+  if ((rc = ensure_track(s, (size_t)p * 4))) return rc;
+  int32_t* done = (int32_t*)s->d_track;
+  cudaError_t e = launch_init_done(p, status, done, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "polish init");
+  return polish_impl(s, p, x, done, *prm, (cudaStream_t)stream);
+}
+
+hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, void* gc, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if (p < 0 || !gc) { set_error("bad p or gc is NULL"); return HPT_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(gc, 0, (size_t)s->M * 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint init");
+  if (p == 0) return HPT_OK;
+  if (!x || !gx) { set_error("x or gx is NULL"); return HPT_EINVAL; }
+  const int n = s->n;
+  const int64_t chunk = std::min<int64_t>(p, 8192);
+  const size_t ext_bytes = ((size_t)chunk * n * (n + 2) * 16 + 255) / 256 * 256;
+  if ((rc = ensure_scratch(s, ext_bytes + (size_t)chunk * s->M * 16))) return rc;
+  void* contrib = (char*)s->d_scratch + ext_bytes;
+  for (int64_t q0 = 0; q0 < p; q0 += chunk) {
+    const int64_t cnt = std::min(chunk, p - q0);
+    EvalOut out;
+    out.ext = s->d_scratch;
+    const void* xq = (const char*)x + q0 * n * 16;
+    e = launch_eval_fp64(s, cnt, xq, nullptr, 0, out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint evaluation launch");
+    e = launch_adjoint(s, cnt, s->d_scratch, xq, (const char*)gx + q0 * n * 16, contrib, 0, gc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  }
+  return HPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// FP64 evaluation of the homotopy and its extended Jacobian (Algorithm 2,
+// Section 5) on the CUDA cores.
+//
+// For every point: z = log y (eq. (6)); for every monomial W = <z, a> +
+// tau e/D (one row of Z A, eq. (7)); E = exp(W); the extended Jacobian row of
+// equation k is sum_i E_i B_k[:, i] = [D_z h_k | D_tau h_k | h_k] (eq. (8) and
+// the extended-Jacobian identity), and D_y h_k = D_z h_k diag(e^{-z}).
+//
+// Mapping: a block owns 32 points (one per lane) and its four warps take the
+// equations k = warp, warp + 4, ...; all lanes of a warp read the same
+// monomial constants (broadcast), z is staged in shared memory transposed so
+// that lane q reads column q without bank conflicts.
+#include <math.h>
+
+#include "hpt_internal.h"
+
+namespace hpt {
+namespace {
+
+template <int NMAX>
+__global__ void __launch_bounds__(128)
+eval_fp64_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t* __restrict__ off,
+                 const double* __restrict__ ahat, const double2* __restrict__ bcol,
+                 const double2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
+                 double2* __restrict__ ext, double2* __restrict__ oH, double2* __restrict__ oHy,
+                 double2* __restrict__ oHt) {
+  __shared__ double2 zs[NMAX][32];
+  __shared__ double2 iys[NMAX][32];
+  __shared__ double taus[32];
+  __shared__ double tinv[32];
+  const int64_t base = (int64_t)blockIdx.x * 32;
+
+  // op. 1 of Algorithm 2: Z <- log Y (principal branch), and 1/y for the
+  // final diag(e^{-z}) scaling.
+  for (int idx = threadIdx.x; idx < 32 * n; idx += blockDim.x) {
+    const int q = idx / n, j = idx - q * n;
+    const int64_t path = base + q;
+    double2 v = make_double2(1.0, 0.0);
+    if (path < p) v = y[path * n + j];
+    const double r2 = v.x * v.x + v.y * v.y;
+    zs[j][q] = make_double2(log(hypot(v.x, v.y)), atan2(v.y, v.x));
+    iys[j][q] = make_double2(v.x / r2, -v.y / r2);
+  }
+  if (threadIdx.x < 32) {
+    const int64_t path = base + threadIdx.x;
+    double tv = (path < p && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);   // no tin: t = 1
+    double tau = tau_is_t ? log(tv) : tv;
+    taus[threadIdx.x] = tau;
+    tinv[threadIdx.x] = tau_is_t ? 1.0 / tv : exp(-tau);
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t path = base + lane;
+  const double tau = taus[lane];
+  const int np2 = n + 2;
+  for (int k = warp; k < n; k += 4) {
+    double2 accJ[NMAX];
+#pragma unroll
+    for (int u = 0; u < NMAX; ++u) accJ[u] = make_double2(0.0, 0.0);
+    double2 accT = make_double2(0.0, 0.0), accH = make_double2(0.0, 0.0);
+    const int i0 = off[k], i1 = off[k] + msz[k];
+    for (int i = i0; i < i1; ++i) {
+      // op. 2 of Algorithm 2, one monomial: W = [z, tau] . A[:, i]
+      const double* a = ahat + (size_t)i * (n + 1);
+      double wr = a[n] * tau, wi = 0.0;
+#pragma unroll
+      for (int j = 0; j < NMAX; ++j) {
+        if (j < n) {
+          const double aj = a[j];
+          const double2 z = zs[j][lane];
+          wr = fma(aj, z.x, wr);
+          wi = fma(aj, z.y, wi);
+        }
+      }
+      double sn, cs;
+      sincos(wi, &sn, &cs);
+      const double mag = exp(wr);
+      const double er = mag * cs, ei = mag * sn;
+      // ... times B_k[:, i] (complex), accumulated over the equation's monomials
+      const double2* bb = bcol + (size_t)i * np2;
+#pragma unroll
+      for (int u = 0; u < NMAX; ++u) {
+        if (u < n) {
+          const double2 c = bb[u];
+          accJ[u].x = fma(er, c.x, fma(-ei, c.y, accJ[u].x));
+          accJ[u].y = fma(er, c.y, fma(ei, c.x, accJ[u].y));
+        }
+      }
+      const double2 ct = bb[n], ch = bb[n + 1];
+      accT.x = fma(er, ct.x, fma(-ei, ct.y, accT.x));
+      accT.y = fma(er, ct.y, fma(ei, ct.x, accT.y));
+      accH.x = fma(er, ch.x, fma(-ei, ch.y, accH.x));
+      accH.y = fma(er, ch.y, fma(ei, ch.x, accH.y));
+    }
+    if (path >= p) continue;
+    // op. 3 of Algorithm 2: D_y h_k = D_z h_k diag(e^{-z})
+    if (ext) {
+      double2* row = ext + ((size_t)path * n + k) * np2;
+#pragma unroll
+      for (int u = 0; u < NMAX; ++u) {
+        if (u < n) {
+          const double2 iy = iys[u][lane];
+          row[u] = make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
+        }
+      }
+      row[n] = accT;
+      row[n + 1] = accH;
+    }
+    if (oHy) {
+      double2* row = oHy + ((size_t)path * n + k) * n;
+#pragma unroll
+      for (int u = 0; u < NMAX; ++u) {
+        if (u < n) {
+          const double2 iy = iys[u][lane];
+          row[u] = make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
+        }
+      }
+    }
+    if (oH) oH[(size_t)path * n + k] = accH;
+    if (oHt) {
+      const double ti = tinv[lane];   // dH/dt = (dH/dtau) / t
+      oHt[(size_t)path * n + k] = make_double2(accT.x * ti, accT.y * ti);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const double* tau,
+                             int tau_is_t, const EvalOut& out, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  const int64_t blocks = (p + 31) / 32;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  int pi = prof_begin(s, "eval_fp64", st);
+  const double2* yy = (const double2*)y;
+  double2* ext = (double2*)out.ext;
+  double2* H = (double2*)out.H;
+  double2* Hy = (double2*)out.Hy;
+  double2* Ht = (double2*)out.Ht;
+  const double2* b = (const double2*)s->d_b;
+  if (s->n <= 8)
+    eval_fp64_kernel<8><<<(unsigned)blocks, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, b, yy, tau, tau_is_t, ext, H, Hy, Ht);
+  else if (s->n <= 16)
+    eval_fp64_kernel<16><<<(unsigned)blocks, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, b, yy, tau, tau_is_t, ext, H, Hy, Ht);
+  else
+    eval_fp64_kernel<32><<<(unsigned)blocks, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, b, yy, tau, tau_is_t, ext, H, Hy, Ht);
+  prof_end(s, pi, st);
+  return cudaGetLastError();
+}
+
+}  // namespace hpt

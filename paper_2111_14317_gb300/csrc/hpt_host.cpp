@@ -1,0 +1,610 @@
+// Host side of libhpt: exact integer bookkeeping of the cell, constant images
+// of Algorithm 1 (Initialize), handle lifetime, scratch, errors, profiling.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hpt_internal.h"
+
+namespace hpt {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// ------------------------------------------------------------ exact rationals
+typedef __int128 i128;
+static const i128 kLim = ((i128)1) << 62;   // every stored value stays below
+
+static i128 iabs(i128 v) { return v < 0 ? -v : v; }
+static i128 igcd(i128 a, i128 b) {
+  a = iabs(a);
+  b = iabs(b);
+  while (b) { i128 t = a % b; a = b; b = t; }
+  return a;
+}
+
+struct Rat {
+  i128 num = 0, den = 1;
+};
+
+static bool norm(Rat& r) {
+  if (r.den < 0) { r.num = -r.num; r.den = -r.den; }
+  i128 g = igcd(r.num, r.den);
+  if (g > 1) { r.num /= g; r.den /= g; }
+  if (r.num == 0) r.den = 1;
+  return iabs(r.num) < kLim && r.den < kLim;
+}
+static bool rmul(const Rat& a, const Rat& b, Rat& out) {
+  // reduce crosswise first so the products stay small
+  i128 g1 = igcd(a.num, b.den), g2 = igcd(b.num, a.den);
+  if (g1 == 0) g1 = 1;
+  if (g2 == 0) g2 = 1;
+  out.num = (a.num / g1) * (b.num / g2);
+  out.den = (a.den / g2) * (b.den / g1);
+  return norm(out);
+}
+static bool rsub(const Rat& a, const Rat& b, Rat& out) {
+  i128 g = igcd(a.den, b.den);
+  i128 l = a.den / g * b.den;
+  if (iabs(l) >= kLim) return false;
+  out.num = a.num * (l / a.den) - b.num * (l / b.den);
+  out.den = l;
+  return norm(out);
+}
+static bool rdiv(const Rat& a, const Rat& b, Rat& out) {
+  Rat inv;
+  inv.num = b.den;
+  inv.den = b.num;
+  if (!norm(inv)) return false;
+  return rmul(a, inv, out);
+}
+
+// Solves V x = rhs exactly (Gauss-Jordan over the rationals).  Returns
+// HPT_OK, HPT_ENOTCELL (singular) or HPT_ERANGE.
+static hpt_status solve_exact(int n, const std::vector<int64_t>& V, const std::vector<int64_t>& rhs,
+                              std::vector<Rat>& x) {
+  std::vector<Rat> A((size_t)n * (n + 1));
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) A[i * (n + 1) + j].num = V[i * n + j];
+    A[i * (n + 1) + n].num = rhs[i];
+  }
+  for (int j = 0; j < n; ++j) {
+    int piv = -1;
+    for (int i = j; i < n; ++i)
+      if (A[i * (n + 1) + j].num != 0) { piv = i; break; }
+    if (piv < 0) return HPT_ENOTCELL;
+    if (piv != j)
+      for (int c = 0; c <= n; ++c) std::swap(A[j * (n + 1) + c], A[piv * (n + 1) + c]);
+    for (int i = 0; i < n; ++i) {
+      if (i == j || A[i * (n + 1) + j].num == 0) continue;
+      Rat f;
+      if (!rdiv(A[i * (n + 1) + j], A[j * (n + 1) + j], f)) return HPT_ERANGE;
+      for (int c = j; c <= n; ++c) {
+        Rat t;
+        if (!rmul(f, A[j * (n + 1) + c], t)) return HPT_ERANGE;
+        if (!rsub(A[i * (n + 1) + c], t, A[i * (n + 1) + c])) return HPT_ERANGE;
+      }
+    }
+  }
+  x.resize(n);
+  for (int i = 0; i < n; ++i)
+    if (!rdiv(A[i * (n + 1) + n], A[i * (n + 1) + i], x[i])) return HPT_ERANGE;
+  return HPT_OK;
+}
+
+struct Lifted {
+  std::vector<int64_t> e, alpha, beta;
+  int64_t D = 1;
+};
+
+static hpt_status check_shape(int32_t n, const int32_t* msz, int32_t* M_out) {
+  if (n < 1 || n > kMaxN) { set_error("n=%d outside [1,%d]", n, kMaxN); return HPT_EINVAL; }
+  if (!msz) { set_error("support_sizes is NULL"); return HPT_EINVAL; }
+  int64_t M = 0;
+  for (int k = 0; k < n; ++k) {
+    if (msz[k] < 1 || msz[k] > 4096) { set_error("m_%d=%d outside [1,4096]", k, msz[k]); return HPT_EINVAL; }
+    M += msz[k];
+  }
+  if (M > (1 << 20)) { set_error("too many monomials"); return HPT_EINVAL; }
+  *M_out = (int32_t)M;
+  return HPT_OK;
+}
+
+static hpt_status lift(int32_t n, const int32_t* msz, const int32_t* exps, const int64_t* lifting,
+                       const hpt_cell* cell, Lifted& L) {
+  int32_t M;
+  hpt_status rc = check_shape(n, msz, &M);
+  if (rc) return rc;
+  if (!exps || !lifting || !cell) { set_error("NULL exponents, lifting or cell"); return HPT_EINVAL; }
+  std::vector<int32_t> off(n);
+  for (int k = 0, acc = 0; k < n; ++k) { off[k] = acc; acc += msz[k]; }
+  for (int64_t i = 0; i < (int64_t)M * n; ++i)
+    if (exps[i] < -(1 << 20) || exps[i] > (1 << 20)) { set_error("exponent too large"); return HPT_ERANGE; }
+  for (int i = 0; i < M; ++i)
+    if (lifting[i] < -(1LL << 40) || lifting[i] > (1LL << 40)) { set_error("lifting too large"); return HPT_ERANGE; }
+  L.alpha.assign(n, 0);
+  L.beta.assign(n, 0);
+  std::vector<int> p0(n, -1), p1(n, -1);
+  if (cell->kind == HPT_CELL_PAIRS) {
+    if (!cell->pairs) { set_error("cell.pairs is NULL"); return HPT_EINVAL; }
+    std::vector<int64_t> V((size_t)n * n), rhs(n);
+    for (int k = 0; k < n; ++k) {
+      p0[k] = cell->pairs[2 * k];
+      p1[k] = cell->pairs[2 * k + 1];
+      if (p0[k] < 0 || p1[k] < 0 || p0[k] >= msz[k] || p1[k] >= msz[k] || p0[k] == p1[k]) {
+        set_error("bad pair for equation %d", k);
+        return HPT_EINVAL;
+      }
+      const int32_t* a0 = exps + (size_t)(off[k] + p0[k]) * n;
+      const int32_t* a1 = exps + (size_t)(off[k] + p1[k]) * n;
+      for (int j = 0; j < n; ++j) V[k * n + j] = (int64_t)a1[j] - a0[j];
+      rhs[k] = lifting[off[k] + p0[k]] - lifting[off[k] + p1[k]];
+    }
+    std::vector<Rat> alpha;
+    rc = solve_exact(n, V, rhs, alpha);
+    if (rc == HPT_ENOTCELL) { set_error("pair matrix is singular"); return rc; }
+    if (rc) { set_error("overflow solving for alpha"); return rc; }
+    i128 D = 1;
+    for (int j = 0; j < n; ++j) {
+      i128 g = igcd(D, alpha[j].den);
+      D = D / g * alpha[j].den;
+      if (D >= kLim) { set_error("denominator overflow"); return HPT_ERANGE; }
+    }
+    L.D = (int64_t)D;
+    for (int j = 0; j < n; ++j) {
+      i128 v = alpha[j].num * (D / alpha[j].den);
+      if (iabs(v) >= kLim) { set_error("alpha overflow"); return HPT_ERANGE; }
+      L.alpha[j] = (int64_t)v;
+    }
+    for (int k = 0; k < n; ++k) {
+      const int32_t* a0 = exps + (size_t)(off[k] + p0[k]) * n;
+      i128 b = (i128)L.D * lifting[off[k] + p0[k]];
+      for (int j = 0; j < n; ++j) b += (i128)a0[j] * L.alpha[j];
+      if (iabs(b) >= kLim) { set_error("beta overflow"); return HPT_ERANGE; }
+      L.beta[k] = (int64_t)b;
+    }
+  } else if (cell->kind == HPT_CELL_EXPLICIT || cell->kind == HPT_CELL_LOWER) {
+    if (!cell->alpha_num || (cell->kind == HPT_CELL_EXPLICIT && !cell->beta_num)) {
+      set_error("cell.alpha_num / beta_num is NULL");
+      return HPT_EINVAL;
+    }
+    if (cell->denom < 1 || cell->denom >= (int64_t)kLim) { set_error("cell.denom must be >= 1"); return HPT_EINVAL; }
+    L.D = cell->denom;
+    for (int j = 0; j < n; ++j) {
+      if (cell->alpha_num[j] <= -(1LL << 40) || cell->alpha_num[j] >= (1LL << 40)) {
+        set_error("alpha too large");
+        return HPT_ERANGE;
+      }
+      L.alpha[j] = cell->alpha_num[j];
+    }
+    for (int k = 0; k < n; ++k) {
+      if (cell->kind == HPT_CELL_EXPLICIT) {
+        L.beta[k] = cell->beta_num[k];
+        continue;
+      }
+      i128 best = 0;
+      for (int i = 0; i < msz[k]; ++i) {
+        const int32_t* a = exps + (size_t)(off[k] + i) * n;
+        i128 v = (i128)L.D * lifting[off[k] + i];
+        for (int j = 0; j < n; ++j) v += (i128)a[j] * L.alpha[j];
+        if (i == 0 || v < best) best = v;
+      }
+      if (iabs(best) >= kLim) { set_error("beta overflow"); return HPT_ERANGE; }
+      L.beta[k] = (int64_t)best;
+    }
+  } else {
+    set_error("unknown cell kind %d", cell->kind);
+    return HPT_EINVAL;
+  }
+  L.e.assign(M, 0);
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < msz[k]; ++i) {
+      const int32_t* a = exps + (size_t)(off[k] + i) * n;
+      i128 v = (i128)L.D * lifting[off[k] + i] - L.beta[k];
+      for (int j = 0; j < n; ++j) v += (i128)a[j] * L.alpha[j];
+      if (iabs(v) >= kLim) { set_error("t-exponent overflow"); return HPT_ERANGE; }
+      L.e[off[k] + i] = (int64_t)v;
+      const bool on_pair = (cell->kind == HPT_CELL_PAIRS) && (i == p0[k] || i == p1[k]);
+      if (on_pair && v != 0) { set_error("internal: pair off its facet"); return HPT_ENOTCELL; }
+      if (!on_pair && v < 0) { set_error("monomial %d of equation %d lies below the cell", i, k); return HPT_ENOTCELL; }
+      if (cell->kind == HPT_CELL_PAIRS && !on_pair && v == 0) {
+        set_error("lifting not generic: monomial %d of equation %d on the cell's facet", i, k);
+        return HPT_ENOTCELL;
+      }
+    }
+  }
+  return HPT_OK;
+}
+
+// ------------------------------------------------------------ bf16 (host)
+// Round-to-nearest-even of an IEEE binary32 to its upper 16 bits.
+static uint16_t bf16_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40);
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+static float bf16_value(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+static void split2(double v, uint16_t& hi, uint16_t& lo) {
+  hi = bf16_bits((float)v);
+  lo = bf16_bits((float)(v - (double)bf16_value(hi)));
+}
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+static MixedLayout mixed_layout(int n, int max_m) {
+  MixedLayout L;
+  L.MP = round_up(max_m, 16);
+  L.KX = round_up(3 * n, 16);
+  L.NJ = round_up(2 * (n + 2), 16);
+  L.KC = 2 * L.MP;
+  L.off_bexp = 0;
+  L.off_bhi = L.MP * L.KX * 2;
+  L.off_blo = L.off_bhi + L.NJ * L.KC * 2;
+  L.off_texp = L.off_blo + L.NJ * L.KC * 2;
+  L.chunk_bytes = round_up(L.off_texp + L.MP * 4, 128);
+  int cols = 2 * L.MP + L.NJ, t = 32;
+  while (t < cols) t *= 2;
+  L.tmem_cols = t;
+  return L;
+}
+
+}  // namespace hpt
+
+using namespace hpt;
+
+extern "C" {
+
+void hpt_default_params(hpt_params* o) {
+  if (!o) return;
+  o->tol_accept = 1e-3;
+  o->dtau_init = 0.05;
+  o->dtau_min = 1e-8;
+  o->dtau_max = 0.5;
+  o->grow = 2.0;
+  o->shrink = 0.5;
+  o->grow_after = 3;
+  o->max_steps = 10000;
+  o->div_bound = 1e8;
+  o->polish_tol = 1e-13;
+  o->polish_iters = 8;
+  o->check_every = 32;
+  o->cond_max = 1e6;
+  o->eps0 = 1e-10;
+}
+
+const char* hpt_status_string(hpt_status s) {
+  switch (s) {
+    case HPT_OK: return "ok";
+    case HPT_EINVAL: return "invalid argument";
+    case HPT_ENOMEM: return "out of memory";
+    case HPT_ECUDA: return "CUDA error";
+    case HPT_ERANGE: return "value out of range";
+    case HPT_ENOTCELL: return "not a cell";
+    case HPT_ETIMEOUT: return "device wait timed out";
+    case HPT_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+const char* hpt_last_error(void) { return g_err; }
+
+hpt_status hpt_lift_exponents(int32_t n, const int32_t* msz, const int32_t* exps,
+                              const int64_t* lifting, const hpt_cell* cell, int64_t* texp,
+                              int64_t* denom, int64_t* alpha_num, int64_t* beta_num) {
+  Lifted L;
+  hpt_status rc = lift(n, msz, exps, lifting, cell, L);
+  if (rc) return rc;
+  if (texp) memcpy(texp, L.e.data(), L.e.size() * sizeof(int64_t));
+  if (denom) *denom = L.D;
+  if (alpha_num) memcpy(alpha_num, L.alpha.data(), n * sizeof(int64_t));
+  if (beta_num) memcpy(beta_num, L.beta.data(), n * sizeof(int64_t));
+  return HPT_OK;
+}
+
+#define CU(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));              \
+      hpt_destroy(s);                                                         \
+      return e_ == cudaErrorMemoryAllocation ? HPT_ENOMEM : HPT_ECUDA;        \
+    }                                                                         \
+  } while (0)
+
+hpt_status hpt_create_system(int32_t n, const int32_t* msz, const int32_t* exps,
+                             const double* coeffs, const int64_t* lifting, const hpt_cell* cell,
+                             hpt_precision prec, hpt_system* out) {
+  if (!out) { set_error("out is NULL"); return HPT_EINVAL; }
+  *out = nullptr;
+  if (prec != HPT_FP64 && prec != HPT_MIXED) { set_error("bad precision"); return HPT_EINVAL; }
+  if (!coeffs) { set_error("coeffs is NULL"); return HPT_EINVAL; }
+  Lifted L;
+  hpt_status rc = lift(n, msz, exps, lifting, cell, L);
+  if (rc) return rc;
+  int32_t M = (int32_t)L.e.size();
+  for (int i = 0; i < 2 * M; ++i)
+    if (!isfinite(coeffs[i])) { set_error("coefficient %d is not finite", i / 2); return HPT_EINVAL; }
+  int max_m = 0;
+  for (int k = 0; k < n; ++k) max_m = std::max(max_m, (int)msz[k]);
+  if (prec == HPT_MIXED) {
+    if (max_m > kMixedMaxM) { set_error("mixed form supports m_k <= %d", kMixedMaxM); return HPT_ENOTSUP; }
+    for (int i = 0; i < M; ++i) {
+      int64_t s1 = 0;
+      for (int j = 0; j < n; ++j) {
+        int a = exps[(size_t)i * n + j];
+        if (a > 256 || a < -256) { set_error("|a| > 256 is not exact in bf16"); return HPT_ERANGE; }
+        s1 += a < 0 ? -a : a;
+      }
+      if (s1 > 64) { set_error("mixed form needs sum |a_j| <= 64"); return HPT_ERANGE; }
+      if (L.e[i] >= (1 << 24) || L.e[i] <= -(1 << 24)) { set_error("t-exponent not exact in fp32"); return HPT_ERANGE; }
+    }
+  }
+  hpt_system s = new hpt_system_s();
+  s->n = n;
+  s->M = M;
+  s->prec = prec;
+  s->max_m = max_m;
+  s->msz.assign(msz, msz + n);
+  s->off.resize(n);
+  for (int k = 0, acc = 0; k < n; ++k) { s->off[k] = acc; acc += msz[k]; }
+  s->exps.assign(exps, exps + (size_t)M * n);
+  s->coef.assign(coeffs, coeffs + 2 * (size_t)M);
+  s->texp = L.e;
+  s->D = L.D;
+  s->alpha_num = L.alpha;
+  s->beta_num = L.beta;
+  CU(cudaGetDevice(&s->device));
+
+  // FP64 constants: A_hat columns (a; e/D) and B_k columns [c a; c e/D; c].
+  std::vector<double> ahat((size_t)M * (n + 1)), b((size_t)M * (n + 2) * 2);
+  for (int i = 0; i < M; ++i) {
+    const double sexp = (double)L.e[i] / (double)L.D;
+    const double cr = coeffs[2 * i], ci = coeffs[2 * i + 1];
+    for (int j = 0; j < n; ++j) {
+      const double a = (double)exps[(size_t)i * n + j];
+      ahat[(size_t)i * (n + 1) + j] = a;
+      b[((size_t)i * (n + 2) + j) * 2] = cr * a;
+      b[((size_t)i * (n + 2) + j) * 2 + 1] = ci * a;
+    }
+    ahat[(size_t)i * (n + 1) + n] = sexp;
+    b[((size_t)i * (n + 2) + n) * 2] = cr * sexp;
+    b[((size_t)i * (n + 2) + n) * 2 + 1] = ci * sexp;
+    b[((size_t)i * (n + 2) + n + 1) * 2] = cr;
+    b[((size_t)i * (n + 2) + n + 1) * 2 + 1] = ci;
+  }
+  CU(cudaMalloc(&s->d_msz, n * sizeof(int32_t)));
+  CU(cudaMalloc(&s->d_off, n * sizeof(int32_t)));
+  CU(cudaMalloc(&s->d_ahat, ahat.size() * sizeof(double)));
+  CU(cudaMalloc(&s->d_b, b.size() * sizeof(double)));
+  CU(cudaMalloc(&s->d_err, sizeof(int32_t)));
+  CU(cudaMemcpy(s->d_msz, msz, n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_off, s->off.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_ahat, ahat.data(), ahat.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(s->d_b, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMemset(s->d_err, 0, sizeof(int32_t)));
+  CU(cudaMallocHost(&s->h_count, sizeof(int32_t)));
+
+  if (prec == HPT_MIXED) {
+    MixedLayout& ml = s->ml;
+    ml = mixed_layout(n, max_m);
+    std::vector<uint8_t> img((size_t)n * ml.chunk_bytes, 0);
+    for (int k = 0; k < n; ++k) {
+      uint8_t* ch = img.data() + (size_t)k * ml.chunk_bytes;
+      uint16_t* bexp = (uint16_t*)(ch + ml.off_bexp);
+      uint16_t* bhi = (uint16_t*)(ch + ml.off_bhi);
+      uint16_t* blo = (uint16_t*)(ch + ml.off_blo);
+      float* tf = (float*)(ch + ml.off_texp);
+      for (int i = 0; i < msz[k]; ++i) {
+        const int idx = s->off[k] + i;
+        for (int sp = 0; sp < 3; ++sp)
+          for (int j = 0; j < n; ++j)
+            bexp[canon_offset(i, sp * n + j, ml.KX) / 2] = bf16_bits((float)exps[(size_t)idx * n + j]);
+        tf[i] = (float)L.e[idx];
+        // realified B_k^T: output column 2u = Re J_u, 2u+1 = Im J_u; K index
+        // i = Re E_i, MP + i = Im E_i.
+        for (int u = 0; u < n + 2; ++u) {
+          const double br = b[((size_t)idx * (n + 2) + u) * 2], bi = b[((size_t)idx * (n + 2) + u) * 2 + 1];
+          uint16_t h, l;
+          split2(br, h, l);
+          bhi[canon_offset(2 * u, i, ml.KC) / 2] = h;
+          blo[canon_offset(2 * u, i, ml.KC) / 2] = l;
+          split2(-bi, h, l);
+          bhi[canon_offset(2 * u, ml.MP + i, ml.KC) / 2] = h;
+          blo[canon_offset(2 * u, ml.MP + i, ml.KC) / 2] = l;
+          split2(bi, h, l);
+          bhi[canon_offset(2 * u + 1, i, ml.KC) / 2] = h;
+          blo[canon_offset(2 * u + 1, i, ml.KC) / 2] = l;
+          split2(br, h, l);
+          bhi[canon_offset(2 * u + 1, ml.MP + i, ml.KC) / 2] = h;
+          blo[canon_offset(2 * u + 1, ml.MP + i, ml.KC) / 2] = l;
+        }
+      }
+    }
+    CU(cudaMalloc(&s->d_chunks, img.size()));
+    CU(cudaMemcpy(s->d_chunks, img.data(), img.size(), cudaMemcpyHostToDevice));
+  }
+  *out = s;
+  return HPT_OK;
+}
+#undef CU
+
+hpt_status hpt_destroy(hpt_system s) {
+  if (!s) return HPT_EINVAL;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaFree(s->d_msz);
+  cudaFree(s->d_off);
+  cudaFree(s->d_ahat);
+  cudaFree(s->d_b);
+  cudaFree(s->d_chunks);
+  cudaFree(s->d_err);
+  cudaFree(s->d_scratch);
+  cudaFree(s->d_track);
+  if (s->h_count) cudaFreeHost(s->h_count);
+  for (auto& k : s->stats)
+    for (auto& pr : k.pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  for (auto ev : s->event_pool) cudaEventDestroy(ev);
+  cudaSetDevice(prev);
+  delete s;
+  return HPT_OK;
+}
+
+hpt_status hpt_get_info(hpt_system s, int32_t* n, int32_t* M, int32_t* prec, double eps0,
+                        double* tau0) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  if (n) *n = s->n;
+  if (M) *M = s->M;
+  if (prec) *prec = (int32_t)s->prec;
+  if (tau0) {
+    if (!(eps0 > 0.0 && eps0 < 1.0)) eps0 = 1e-10;
+    int64_t emin = 0;
+    for (int64_t v : s->texp)
+      if (v > 0 && (emin == 0 || v < emin)) emin = v;
+    *tau0 = emin == 0 ? log(eps0) : log(eps0) / ((double)emin / (double)s->D);
+  }
+  return HPT_OK;
+}
+
+hpt_status hpt_get_texp(hpt_system s, int64_t* texp, int64_t* denom, int64_t* alpha_num,
+                        int64_t* beta_num) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  if (texp) memcpy(texp, s->texp.data(), s->texp.size() * sizeof(int64_t));
+  if (denom) *denom = s->D;
+  if (alpha_num) memcpy(alpha_num, s->alpha_num.data(), s->n * sizeof(int64_t));
+  if (beta_num) memcpy(beta_num, s->beta_num.data(), s->n * sizeof(int64_t));
+  return HPT_OK;
+}
+
+hpt_status hpt_device_error(hpt_system s) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  int32_t v = 0;
+  if (cudaMemcpy(&v, s->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("reading the device error flag failed");
+    return HPT_ECUDA;
+  }
+  if (v) {
+    cudaMemset(s->d_err, 0, sizeof(int32_t));
+    set_error("a bounded device wait gave up (code %d)", v);
+    return HPT_ETIMEOUT;
+  }
+  return HPT_OK;
+}
+
+hpt_status hpt_profile_enable(hpt_system s, int32_t enable) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  s->profiling = enable != 0;
+  return HPT_OK;
+}
+
+hpt_status hpt_profile_read(hpt_system s, int32_t cap, const char** names, int64_t* launches,
+                            double* ms, int32_t* count) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  for (auto& k : s->stats) {
+    for (auto& pr : k.pending) {
+      cudaEventSynchronize(pr.second);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, pr.first, pr.second);
+      k.ms += t;
+      s->event_pool.push_back(pr.first);
+      s->event_pool.push_back(pr.second);
+    }
+    k.pending.clear();
+  }
+  int i = 0;
+  for (auto& k : s->stats) {
+    if (i < cap) {
+      if (names) names[i] = k.name.c_str();
+      if (launches) launches[i] = k.launches;
+      if (ms) ms[i] = k.ms;
+    }
+    ++i;
+  }
+  if (count) *count = (int32_t)s->stats.size();
+  return HPT_OK;
+}
+
+}  // extern "C"
+
+namespace hpt {
+
+hpt_status ensure_scratch(hpt_system s, size_t bytes) {
+  if (bytes <= s->scratch_bytes) return HPT_OK;
+  cudaFree(s->d_scratch);
+  s->d_scratch = nullptr;
+  s->scratch_bytes = 0;
+  if (cudaMalloc(&s->d_scratch, bytes) != cudaSuccess) {
+    set_error("scratch allocation of %zu bytes failed", bytes);
+    return HPT_ENOMEM;
+  }
+  s->scratch_bytes = bytes;
+  return HPT_OK;
+}
+
+hpt_status ensure_track(hpt_system s, size_t bytes) {
+  if (bytes <= s->track_bytes) return HPT_OK;
+  cudaFree(s->d_track);
+  s->d_track = nullptr;
+  s->track_bytes = 0;
+  if (cudaMalloc(&s->d_track, bytes) != cudaSuccess) {
+    set_error("track state allocation of %zu bytes failed", bytes);
+    return HPT_ENOMEM;
+  }
+  s->track_bytes = bytes;
+  return HPT_OK;
+}
+
+static cudaEvent_t pool_event(hpt_system s) {
+  if (!s->event_pool.empty()) {
+    cudaEvent_t e = s->event_pool.back();
+    s->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int prof_begin(hpt_system s, const char* name, cudaStream_t st) {
+  if (!s->profiling) return -1;
+  int idx = -1;
+  for (size_t i = 0; i < s->stats.size(); ++i)
+    if (s->stats[i].name == name) idx = (int)i;
+  if (idx < 0) {
+    s->stats.push_back(KernelStat());
+    s->stats.back().name = name;
+    idx = (int)s->stats.size() - 1;
+  }
+  cudaEvent_t a = pool_event(s), b = pool_event(s);
+  cudaEventRecord(a, st);
+  s->stats[idx].pending.push_back({a, b});
+  return idx;
+}
+
+void prof_end(hpt_system s, int idx, cudaStream_t st) {
+  if (idx < 0) return;
+  KernelStat& k = s->stats[idx];
+  cudaEventRecord(k.pending.back().second, st);
+  k.launches += 1;
+}
+
+}  // namespace hpt

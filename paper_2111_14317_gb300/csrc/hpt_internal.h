@@ -1,0 +1,154 @@
+// Internal declarations of libhpt (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hpt.h"
+
+namespace hpt {
+
+constexpr int kMaxN = 32;          // variables (= equations)
+constexpr int kMixedMaxM = 128;    // monomials per equation in the mixed form
+constexpr int kTile = 128;         // paths per tensor-core tile (MMA M)
+
+// Per-equation constant image of the mixed form, laid out exactly as the
+// kernel's shared-memory operands (bulk-copied per equation).
+//   bexp : MP x KX bf16, exponent operand, K index s*n + j holds a_j for the
+//          three splits s of log y (K-major, 8x8 core matrices, no swizzle)
+//   bhi  : NJ x KC bf16, high part of the realified B_k^T
+//   blo  : NJ x KC bf16, low part
+//   texp : MP floats, t-exponent numerators e (0 on padding)
+struct MixedLayout {
+  int MP = 0;   // monomials per equation, padded to 16
+  int KX = 0;   // 3n padded to 16
+  int NJ = 0;   // 2(n+2) padded to 16
+  int KC = 0;   // 2 MP
+  int off_bexp = 0, off_bhi = 0, off_blo = 0, off_texp = 0;
+  int chunk_bytes = 0;
+  int tmem_cols = 0;     // power of two >= 2 MP + NJ
+  int smem_bytes = 0;    // dynamic shared memory of the eval kernel
+};
+
+// Byte offset of element (r, k) of an R x K bf16 operand in the canonical
+// K-major no-swizzle layout used by the tensor-core descriptors: 8-row x
+// 16-byte core matrices, K-adjacent cores 128 bytes apart (leading byte
+// offset), 8-row groups K*16 bytes apart (stride byte offset).
+inline int canon_offset(int r, int k, int K) {
+  return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+struct KernelStat {
+  std::string name;
+  int64_t launches = 0;
+  double ms = 0.0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+void set_error(const char* fmt, ...);
+
+}  // namespace hpt
+
+struct hpt_system_s {
+  int n = 0, M = 0;
+  hpt_precision prec = HPT_FP64;
+  int device = 0;
+  std::vector<int32_t> msz, off, exps;
+  std::vector<double> coef;          // 2M
+  std::vector<int64_t> texp;         // M
+  int64_t D = 1;
+  std::vector<int64_t> alpha_num, beta_num;
+  int max_m = 0;
+
+  // device constants, FP64 form (also used by the mixed form's polish)
+  int32_t* d_msz = nullptr;
+  int32_t* d_off = nullptr;
+  double* d_ahat = nullptr;          // M x (n+1): a_{k,i} and e/D
+  double* d_b = nullptr;             // M x (n+2) complex: B_k columns
+  // device constants, mixed form
+  hpt::MixedLayout ml;
+  uint8_t* d_chunks = nullptr;       // n x chunk_bytes
+
+  // device error flag (bounded waits)
+  int32_t* d_err = nullptr;
+
+  // scratch (grown on demand)
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  void* d_track = nullptr;           // hpt_track state
+  size_t track_bytes = 0;
+  int32_t* h_count = nullptr;        // pinned host counter
+
+  // profiling
+  bool profiling = false;
+  std::vector<hpt::KernelStat> stats;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace hpt {
+
+// Scratch helpers (hpt_host.cpp).
+hpt_status ensure_scratch(hpt_system s, size_t bytes);
+hpt_status ensure_track(hpt_system s, size_t bytes);
+
+// Profiling helpers: returns an index to pass to prof_end, or -1.
+int prof_begin(hpt_system s, const char* name, cudaStream_t st);
+void prof_end(hpt_system s, int idx, cudaStream_t st);
+
+// Kernel launchers (return cudaSuccess or the launch error).
+// Output layout: either the extended Jacobian ext[p][n][n+2] (row k =
+// [dH_k/dy_0..dH_k/dy_{n-1}, dH_k/dtau, H_k]) or the user layout of hpt_eval.
+struct EvalOut {
+  void* ext = nullptr;       // extended Jacobian (step scratch)
+  void* H = nullptr;         // user layout
+  void* Hy = nullptr;
+  void* Ht = nullptr;
+};
+
+// FP64 SIMT evaluation.  Points are y[p][n] complex128 and either tau[p]
+// (tau_is_t = 0) or t[p] (tau_is_t = 1).
+cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const double* tau,
+                             int tau_is_t, const EvalOut& out, cudaStream_t st);
+
+// Mixed tensor-core evaluation, complex64 in and out.
+cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const double* tau,
+                              int tau_is_t, const EvalOut& out, cudaStream_t st);
+
+struct StepArgs {
+  int n;
+  int64_t p;
+  const void* ext;           // extended Jacobian of every path
+  hpt_paths st;
+  hpt_params prm;
+  int32_t* err;
+};
+
+// Consolidated solve + update + step control.  T = double for HPT_FP64,
+// float for HPT_MIXED.
+cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st);
+
+// Newton update at t = 1 for the polish: x += dN where the relative
+// correction is still above tol; done[q] set once it is below.
+cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void* x,
+                                 int32_t* done, double tol, cudaStream_t st);
+
+// Adjoint: per-solution lambda and the per-block partial sums of the
+// coefficient gradient (two kernels).
+cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void* x,
+                           const void* gx, void* partial, int64_t nblk, void* gc,
+                           cudaStream_t st);
+
+// State init / conversion helpers.
+cudaError_t launch_paths_init(hpt_system s, int64_t p, const void* y0, double tau0,
+                              const hpt_params& prm, const hpt_paths& st, cudaStream_t stm);
+cudaError_t launch_count_active(int64_t p, const int32_t* status, int32_t* count,
+                                cudaStream_t st);
+cudaError_t launch_finish_track(hpt_system s, int64_t p, const hpt_paths& st, void* x_out,
+                                int32_t* status_out, int32_t* steps_out, int32_t* done,
+                                cudaStream_t stm);
+cudaError_t launch_init_done(int64_t p, const int32_t* status, int32_t* done, cudaStream_t st);
+
+}  // namespace hpt

@@ -1,0 +1,444 @@
+// Mixed-precision evaluation of the homotopy and its extended Jacobian on the
+// fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// Algorithm 2 (Section 5) for a tile of 128 points, one CTA of 128 threads,
+// thread r <-> point r <-> tensor-memory lane r:
+//   op. 1   z = log y in FP32 (principal branch), Re z and Im z each split into
+//           three BF16 parts (hi + mid + lo carries the full FP32 value);
+//   op. 2a  per equation k: W = Z A_k by tcgen05.mma kind::f16 with FP32
+//           accumulation, K = the three splits of the n coordinates; the
+//           integer exponents are exact in BF16.  Re W and Im W are two MMAs
+//           that share the B operand;
+//   exp     E = exp(Re W + (tau/D) e) (cos Im W, sin Im W): the t-exponent term
+//           is added in FP32 (e exact in FP32), Im W is reduced mod 2 pi with a
+//           two-constant Cody-Waite reduction before the MUFU sine/cosine; E is
+//           split into BF16 hi + lo and written as the A operand of op. 2b;
+//   op. 2b  [D_z h_k | D_tau h_k | h_k] = E_k B_k^T as a real GEMM on
+//           [Re E, Im E] x [[Re B, Im B], [-Im B, Re B]]^T, three passes
+//           hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory;
+//   op. 3   D_y h_k = D_z h_k diag(1/y), written out.
+// The per-equation constants (exponent operand, B_k hi/lo, e) are one
+// contiguous image per equation, double-buffered into shared memory with
+// cp.async.bulk (the bulk-copy engine) while the previous equation computes.
+// Operands use the canonical K-major layout without swizzle (8 x 16-byte core
+// matrices; K-adjacent cores 128 bytes apart, 8-row groups K*16 bytes apart).
+// Every wait on an mbarrier is bounded (about two seconds of global time);
+// a wait that gives up sets the device error flag and the CTA winds down.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "hpt_internal.h"
+
+namespace hpt {
+namespace {
+
+struct MixedArgs {
+  int n, MP, KX, NJ, KC;
+  int chunk_bytes, off_bexp, off_bhi, off_blo, off_texp;
+  int tmem_cols;
+  int nbuf;   // constant-image buffers: 2 (prefetch next equation) or 1
+  // shared-memory carve-up (bytes from the 1024-aligned base)
+  int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_bar;
+  float inv_D;
+  int64_t p;
+  int ntiles;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);           // start address
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;       // leading byte offset (K)
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;       // stride byte offset (M/N)
+  d |= (uint64_t)1 << 46;                            // descriptor version
+  return d;                                          // no swizzle, base offset 0
+}
+
+// kind::f16 instruction descriptor: FP32 D, BF16 A and B, both K-major.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: gives up after ~2 s of global time.
+__device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  if (mbar_try(mbar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    if (mbar_try(mbar, parity)) return true;
+    if (gtimer() - t0 > 2000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ int canon(int r, int k, int K) {
+  return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint16_t bf16_rn(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ float bf16_f(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+// 2 pi split for the Cody-Waite reduction: hi is the float nearest to 2 pi,
+// lo the float nearest to the remainder (2 pi - hi).
+constexpr float kTwoPiHi = 6.28318548202514648f;
+constexpr float kTwoPiLo = -1.74845553e-07f;
+constexpr float kInvTwoPi = 0.159154943091895336f;
+
+__global__ void __launch_bounds__(128, 1)
+eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
+                  const uint8_t* __restrict__ chunks, float2* __restrict__ ext, float2* __restrict__ oH,
+                  float2* __restrict__ oHy, float2* __restrict__ oHt, int32_t* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sAre = sm + P.s_are;
+  uint8_t* sAim = sm + P.s_aim;
+  float2* sInvY = (float2*)(sm + P.s_invy);        // [n][128]
+  uint8_t* sAcHi = sm + P.s_achi;
+  uint8_t* sAcLo = sm + P.s_aclo;
+  uint64_t* bars = (uint64_t*)(sm + P.s_bar);      // [0],[1] const buffers, [2] mma
+  uint32_t* tslot = (uint32_t*)(sm + P.s_bar + 32);
+  int* sAbort = (int*)(sm + P.s_bar + 36);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int n = P.n;
+  const int my_tiles = (P.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  if (my_tiles <= 0) return;
+  const int g_total = my_tiles * n;
+
+  if (tid == 0) {
+    mbar_init(su32(&bars[0]), 1);
+    mbar_init(su32(&bars[1]), 1);
+    mbar_init(su32(&bars[2]), 1);
+    *sAbort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(P.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t t_wre = tbase, t_wim = tbase + P.MP, t_j = tbase + 2 * P.MP;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+
+  // constant images for the first nbuf equations
+  if (tid == 0) {
+    for (int g = 0; g < P.nbuf && g < g_total; ++g)
+      bulk_load(su32(sm + (g ? P.s_const1 : P.s_const0)), chunks + (size_t)(g % n) * P.chunk_bytes, P.chunk_bytes, su32(&bars[g]));
+  }
+  uint32_t mma_phase = 0;
+  int g = 0;
+  const uint32_t idx_x = idesc_bf16(128, P.MP), idx_c = idesc_bf16(128, P.NJ);
+  const int kx_steps = P.KX / 16, kc_steps = P.KC / 16;
+  const uint32_t sbo_x = P.KX * 16, sbo_c = P.KC * 16;
+
+  for (int it = 0; it < my_tiles; ++it) {
+    const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+    const int64_t path = (int64_t)tile * 128 + tid;
+    const bool live = path < P.p;
+    // ---- op. 1: z = log y, three-way BF16 split, 1/y
+    double tv = (live && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);
+    const double tau = tau_is_t ? log(tv) : tv;
+    const float tau_d = (float)(tau * (double)P.inv_D);
+    const float t_inv = (float)(tau_is_t ? 1.0 / tv : exp(-tau));
+    for (int j = 0; j < n; ++j) {
+      float2 v = live ? y[path * n + j] : make_float2(1.f, 0.f);
+      const float zr = logf(hypotf(v.x, v.y)), zi = atan2f(v.y, v.x);
+      const float r2 = v.x * v.x + v.y * v.y;
+      sInvY[j * 128 + tid] = make_float2(v.x / r2, -v.y / r2);
+      float rem_r = zr, rem_i = zi;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const uint16_t hr = bf16_rn(rem_r), hi = bf16_rn(rem_i);
+        *(uint16_t*)(sAre + canon(tid, s * n + j, P.KX)) = hr;
+        *(uint16_t*)(sAim + canon(tid, s * n + j, P.KX)) = hi;
+        rem_r -= bf16_f(hr);
+        rem_i -= bf16_f(hi);
+      }
+    }
+    for (int q = 3 * n; q < P.KX; ++q) {
+      *(uint16_t*)(sAre + canon(tid, q, P.KX)) = 0;
+      *(uint16_t*)(sAim + canon(tid, q, P.KX)) = 0;
+    }
+    proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+
+    for (int k = 0; k < n; ++k, ++g) {
+      const int buf = P.nbuf == 2 ? (g & 1) : 0;
+      const uint32_t use = P.nbuf == 2 ? (uint32_t)(g >> 1) : (uint32_t)g;   // uses of this buffer so far
+      // ---- op. 2a: W = Z A_k (exponent GEMM)
+      bool ok = mbar_wait(su32(&bars[buf]), use & 1u);
+      if (!ok) atomicExch(sAbort, 1);
+      __syncthreads();
+      if (*sAbort) goto teardown;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t cb = su32(sm + (buf ? P.s_const1 : P.s_const0));
+        for (int s = 0; s < kx_steps; ++s) {
+          const uint64_t bd = smem_desc(cb + P.off_bexp + s * 256, 128, sbo_x);
+          mma_bf16(t_wre, smem_desc(su32(sAre) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
+          mma_bf16(t_wim, smem_desc(su32(sAim) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
+        }
+        mma_commit(su32(&bars[2]));
+      }
+      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[2]), mma_phase));
+      mma_phase ^= 1;
+      if (!ok) atomicExch(sAbort, 1);
+      tc_fence_after();
+      // ---- complex exponential, BF16 hi/lo split into the op. 2b A operand
+      {
+        const float* texp = (const float*)(sm + (buf ? P.s_const1 : P.s_const0) + P.off_texp);
+        for (int c0 = 0; c0 < P.MP; c0 += 16) {
+          uint32_t wre[16], wim[16];
+          tmem_ld16(t_wre + lane_base + c0, wre);
+          tmem_ld16(t_wim + lane_base + c0, wim);
+          tmem_wait_ld();
+          uint32_t hr[8], hi_[8], lr[8], li[8];
+#pragma unroll
+          for (int q = 0; q < 16; q += 2) {
+            float er[2], ei[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const float wr = fmaf(tau_d, texp[c0 + q + u], __uint_as_float(wre[q + u]));
+              const float wi = __uint_as_float(wim[q + u]);
+              const float kq = rintf(wi * kInvTwoPi);
+              const float rr = fmaf(-kq, kTwoPiLo, fmaf(-kq, kTwoPiHi, wi));
+              float sn, cs;
+              __sincosf(rr, &sn, &cs);
+              const float m = __expf(wr);
+              er[u] = m * cs;
+              ei[u] = m * sn;
+            }
+            const uint16_t h0 = bf16_rn(er[0]), h1 = bf16_rn(er[1]);
+            const uint16_t g0 = bf16_rn(ei[0]), g1 = bf16_rn(ei[1]);
+            hr[q / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+            hi_[q / 2] = (uint32_t)g0 | ((uint32_t)g1 << 16);
+            lr[q / 2] = (uint32_t)bf16_rn(er[0] - bf16_f(h0)) | ((uint32_t)bf16_rn(er[1] - bf16_f(h1)) << 16);
+            li[q / 2] = (uint32_t)bf16_rn(ei[0] - bf16_f(g0)) | ((uint32_t)bf16_rn(ei[1] - bf16_f(g1)) << 16);
+          }
+          // Re E at K = c0.., Im E at K = MP + c0..; 16 values = two core columns
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int kre = c0 + 8 * h, kim = P.MP + c0 + 8 * h;
+            *(uint4*)(sAcHi + canon(tid, kre, P.KC)) = make_uint4(hr[4 * h], hr[4 * h + 1], hr[4 * h + 2], hr[4 * h + 3]);
+            *(uint4*)(sAcLo + canon(tid, kre, P.KC)) = make_uint4(lr[4 * h], lr[4 * h + 1], lr[4 * h + 2], lr[4 * h + 3]);
+            *(uint4*)(sAcHi + canon(tid, kim, P.KC)) = make_uint4(hi_[4 * h], hi_[4 * h + 1], hi_[4 * h + 2], hi_[4 * h + 3]);
+            *(uint4*)(sAcLo + canon(tid, kim, P.KC)) = make_uint4(li[4 * h], li[4 * h + 1], li[4 * h + 2], li[4 * h + 3]);
+          }
+        }
+      }
+      proxy_fence();
+      tc_fence_before();
+      __syncthreads();
+      if (*sAbort) goto teardown;
+      // ---- op. 2b: [D_z h | D_tau h | h] = E_k B_k^T, split passes
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t cb = su32(sm + (buf ? P.s_const1 : P.s_const0));
+        for (int s = 0; s < kc_steps; ++s) {
+          const uint64_t ah = smem_desc(su32(sAcHi) + s * 256, 128, sbo_c);
+          const uint64_t al = smem_desc(su32(sAcLo) + s * 256, 128, sbo_c);
+          const uint64_t bh = smem_desc(cb + P.off_bhi + s * 256, 128, sbo_c);
+          const uint64_t bl = smem_desc(cb + P.off_blo + s * 256, 128, sbo_c);
+          mma_bf16(t_j, ah, bh, idx_c, s > 0);
+          mma_bf16(t_j, ah, bl, idx_c, 1);
+          mma_bf16(t_j, al, bh, idx_c, 1);
+        }
+        mma_commit(su32(&bars[2]));
+      }
+      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[2]), mma_phase));
+      mma_phase ^= 1;
+      if (!ok) atomicExch(sAbort, 1);
+      tc_fence_after();
+      // both GEMMs of equation k are done: the constant buffer is free
+      if (tid == 0 && ok && g + P.nbuf < g_total) {
+        proxy_fence();
+        bulk_load(su32(sm + (buf ? P.s_const1 : P.s_const0)), chunks + (size_t)((g + P.nbuf) % n) * P.chunk_bytes,
+                  P.chunk_bytes, su32(&bars[buf]));
+      }
+      // ---- op. 3: scale to y-coordinates and write row k
+      if (ok) {
+        for (int c0 = 0; c0 < P.NJ; c0 += 16) {
+          uint32_t jr[16];
+          tmem_ld16(t_j + lane_base + c0, jr);
+          tmem_wait_ld();
+          if (!live) continue;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int u = c0 / 2 + q;
+            const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
+            if (u < n) {
+              const float2 iy = sInvY[u * 128 + tid];
+              const float2 hy = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
+              if (ext) ext[((size_t)path * n + k) * (n + 2) + u] = hy;
+              if (oHy) oHy[((size_t)path * n + k) * n + u] = hy;
+            } else if (u == n) {
+              if (ext) ext[((size_t)path * n + k) * (n + 2) + n] = v;
+              if (oHt) oHt[(size_t)path * n + k] = make_float2(v.x * t_inv, v.y * t_inv);
+            } else if (u == n + 1) {
+              if (ext) ext[((size_t)path * n + k) * (n + 2) + n + 1] = v;
+              if (oH) oH[(size_t)path * n + k] = v;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (*sAbort) goto teardown;
+    }
+  }
+
+teardown:
+  if (*sAbort) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // let copies still in flight land before the CTA's shared memory goes away
+      for (int q = g; q < g + P.nbuf && q < g_total; ++q) {
+        const int b = P.nbuf == 2 ? (q & 1) : 0;
+        mbar_wait(su32(&bars[b]), (uint32_t)(P.nbuf == 2 ? (q >> 1) : q) & 1u);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(P.tmem_cols));
+  }
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const double* tin, int tau_is_t,
+                              const EvalOut& out, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  const MixedLayout& L = s->ml;
+  MixedArgs a;
+  a.n = s->n;
+  a.MP = L.MP;
+  a.KX = L.KX;
+  a.NJ = L.NJ;
+  a.KC = L.KC;
+  a.chunk_bytes = L.chunk_bytes;
+  a.off_bexp = L.off_bexp;
+  a.off_bhi = L.off_bhi;
+  a.off_blo = L.off_blo;
+  a.off_texp = L.off_texp;
+  a.tmem_cols = L.tmem_cols;
+  int off = 0;
+  auto take = [&](int bytes) {
+    int o = off;
+    off += (bytes + 1023) / 1024 * 1024;
+    return o;
+  };
+  a.s_are = take(128 * L.KX * 2);
+  a.s_aim = take(128 * L.KX * 2);
+  a.s_invy = take(128 * s->n * 8);
+  a.s_achi = take(128 * L.KC * 2);
+  a.s_aclo = take(128 * L.KC * 2);
+  a.s_const0 = take(L.chunk_bytes);
+  const int off_single = off;
+  a.s_const1 = take(L.chunk_bytes);
+  a.s_bar = take(64);
+  int smem = off + 1024;   // slack for aligning the dynamic base
+  a.inv_D = (float)(1.0 / (double)s->D);
+  a.p = p;
+  const int64_t ntiles = (p + 127) / 128;
+  if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
+  a.ntiles = (int)ntiles;
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  int max_smem = 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  a.nbuf = 2;
+  if (smem > max_smem) {   // large shapes: one constant buffer, no prefetch
+    off = off_single;
+    a.s_const1 = a.s_const0;
+    a.s_bar = take(64);
+    smem = off + 1024;
+    a.nbuf = 1;
+  }
+  if (smem > max_smem) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(eval_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  // resident CTAs per SM are bounded by tensor memory (512 columns)
+  const int per_sm = 512 / L.tmem_cols >= 2 ? 2 : 1;
+  int64_t grid = (int64_t)g_num_sms * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  int pi = prof_begin(s, "eval_mixed_tc", st);
+  eval_mixed_kernel<<<(unsigned)grid, 128, smem, st>>>(a, (const float2*)y, tin, tau_is_t, s->d_chunks,
+                                                       (float2*)out.ext, (float2*)out.H, (float2*)out.Hy,
+                                                       (float2*)out.Ht, s->d_err);
+  prof_end(s, pi, st);
+  return cudaGetLastError();
+}
+
+}  // namespace hpt

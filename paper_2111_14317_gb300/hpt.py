@@ -1,0 +1,307 @@
+"""Thin Python binding of libhpt's C ABI (include/hpt.h).
+
+Argument marshalling only: every step of the path runs in libhpt's CUDA
+kernels.  PyTorch provides device memory (tensors) and streams.  There is no
+CPU fallback: if ``libhpt.so`` is missing the import of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhpt.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhpt.so not built ({LIB_PATH}); run paper_2111_14317_gb300.build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+HPT_FP64, HPT_MIXED = 0, 1
+CELL_PAIRS, CELL_EXPLICIT, CELL_LOWER = 0, 1, 2
+ACTIVE, CONVERGED, DIVERGED, UNDERFLOW, SINGULAR, MAX_STEPS = range(6)
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error",
+                4: "value out of range", 5: "not a cell", 6: "device wait timed out",
+                7: "not supported"}
+
+EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lift_exponents",
+           "hpt_create_system", "hpt_destroy", "hpt_get_info", "hpt_get_texp", "hpt_eval",
+           "hpt_paths_init", "hpt_step", "hpt_track", "hpt_polish", "hpt_adjoint",
+           "hpt_device_error", "hpt_profile_enable", "hpt_profile_read"]
+
+
+class HptError(RuntimeError):
+    def __init__(self, code, where):
+        msg = _lib.hpt_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} ({msg})")
+        self.code = code
+
+
+class _Cell(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pairs", ctypes.c_void_p),
+                ("alpha_num", ctypes.c_void_p), ("beta_num", ctypes.c_void_p),
+                ("denom", ctypes.c_int64)]
+
+
+class Params(ctypes.Structure):
+    """hpt_params; defaults from hpt_default_params."""
+    _fields_ = [("tol_accept", ctypes.c_double), ("dtau_init", ctypes.c_double),
+                ("dtau_min", ctypes.c_double), ("dtau_max", ctypes.c_double),
+                ("grow", ctypes.c_double), ("shrink", ctypes.c_double),
+                ("grow_after", ctypes.c_int32), ("max_steps", ctypes.c_int32),
+                ("div_bound", ctypes.c_double), ("polish_tol", ctypes.c_double),
+                ("polish_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("cond_max", ctypes.c_double), ("eps0", ctypes.c_double)]
+
+    def __init__(self, **kw):
+        super().__init__()
+        _lib.hpt_default_params(ctypes.byref(self))
+        for k, v in kw.items():
+            setattr(self, k, v)
+
+
+class _Paths(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in
+                ("y", "tau", "dtau", "y_acc", "tau_acc", "dE_acc", "status", "steps", "accepts",
+                 "rejects", "streak")]
+
+
+_VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+_lib.hpt_status_string.restype = ctypes.c_char_p
+_lib.hpt_last_error.restype = ctypes.c_char_p
+for _name, _args in {
+    "hpt_lift_exponents": [_I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_create_system": [_I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP],
+    "hpt_destroy": [_VP],
+    "hpt_get_info": [_VP, _VP, _VP, _VP, ctypes.c_double, _VP],
+    "hpt_get_texp": [_VP, _VP, _VP, _VP, _VP],
+    "hpt_eval": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_paths_init": [_VP, _I64, _VP, _VP, _VP, _VP],
+    "hpt_step": [_VP, _I64, _VP, _I32, _VP, _VP],
+    "hpt_track": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_polish": [_VP, _I64, _VP, _VP, _VP, _VP],
+    "hpt_adjoint": [_VP, _I64, _VP, _VP, _VP, _VP],
+    "hpt_device_error": [_VP],
+    "hpt_profile_enable": [_VP, _I32],
+    "hpt_profile_read": [_VP, _I32, _VP, _VP, _VP, _VP],
+}.items():
+    getattr(_lib, _name).argtypes = _args
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise HptError(rc, where)
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _t_ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _cell_struct(cell, keep):
+    c = _Cell()
+    kind = cell["kind"]
+    if kind == "pairs":
+        pr = np.ascontiguousarray(np.asarray(cell["pairs"], dtype=np.int32).reshape(-1))
+        keep.append(pr)
+        c.kind, c.pairs = CELL_PAIRS, pr.ctypes.data
+    elif kind in ("explicit", "lower"):
+        al = np.ascontiguousarray(np.asarray(cell["alpha_num"], dtype=np.int64))
+        keep.append(al)
+        c.alpha_num, c.denom = al.ctypes.data, int(cell["denom"])
+        if kind == "explicit":
+            be = np.ascontiguousarray(np.asarray(cell["beta_num"], dtype=np.int64))
+            keep.append(be)
+            c.kind, c.beta_num = CELL_EXPLICIT, be.ctypes.data
+        else:
+            c.kind = CELL_LOWER
+    else:
+        raise ValueError(kind)
+    return c
+
+
+def _arrays(n, m, exponents, coeffs, lifting):
+    msz = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1))
+    ex = np.ascontiguousarray(np.asarray(exponents, dtype=np.int32))
+    M = int(msz.sum())
+    assert msz.shape == (n,) and ex.shape == (M, n)
+    co = np.asarray(coeffs, dtype=np.complex128).reshape(M)
+    co = np.ascontiguousarray(np.stack([co.real, co.imag], -1).reshape(-1))
+    li = np.ascontiguousarray(np.asarray(lifting, dtype=np.int64).reshape(M))
+    return msz, ex, co, li, M
+
+
+def lift_exponents(n, m, exponents, lifting, cell):
+    """Host-only exact t-exponents: dict(e, D, alpha_num, beta_num)."""
+    msz, ex, _, li, M = _arrays(n, m, exponents, np.zeros(sum(np.atleast_1d(m))), lifting)
+    keep = []
+    c = _cell_struct(cell, keep)
+    e = np.zeros(M, np.int64)
+    D = ctypes.c_int64(0)
+    al = np.zeros(n, np.int64)
+    be = np.zeros(n, np.int64)
+    _check(_lib.hpt_lift_exponents(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(li), ctypes.byref(c),
+                                   _np_ptr(e), ctypes.byref(D), _np_ptr(al), _np_ptr(be)),
+           "hpt_lift_exponents")
+    return dict(e=e.tolist(), D=int(D.value), alpha_num=al.tolist(), beta_num=be.tolist())
+
+
+class PathState:
+    """Caller-owned structure-of-arrays path state on the device."""
+
+    def __init__(self, p, n, precision, device="cuda"):
+        cdt = torch.complex128 if precision == HPT_FP64 else torch.complex64
+        z = lambda *s, dt: torch.zeros(*s, dtype=dt, device=device)  # noqa: E731
+        self.p, self.n = p, n
+        self.y, self.y_acc, self.dE_acc = (z(p, n, dt=cdt) for _ in range(3))
+        self.tau, self.dtau, self.tau_acc = (z(p, dt=torch.float64) for _ in range(3))
+        self.status, self.steps, self.accepts, self.rejects, self.streak = (
+            z(p, dt=torch.int32) for _ in range(5))
+
+    def _c(self):
+        return _Paths(*[t.data_ptr() for t in (self.y, self.tau, self.dtau, self.y_acc, self.tau_acc,
+                                               self.dE_acc, self.status, self.steps, self.accepts,
+                                               self.rejects, self.streak)])
+
+    def to_host(self):
+        return {k: getattr(self, k).cpu() for k in ("y", "tau", "dtau", "y_acc", "tau_acc",
+                                                     "dE_acc", "status", "steps", "accepts",
+                                                     "rejects", "streak")}
+
+    def load(self, host):
+        for k, v in host.items():
+            getattr(self, k).copy_(v)
+
+
+class System:
+    """A Laurent system with a cell on the current CUDA device (hpt_system)."""
+
+    def __init__(self, n, m, exponents, coeffs, lifting, cell, precision=HPT_FP64):
+        self.n = int(n)
+        self.precision = int(precision)
+        msz, ex, co, li, M = _arrays(self.n, m, exponents, coeffs, lifting)
+        self.M = M
+        keep = []
+        c = _cell_struct(cell, keep)
+        h = ctypes.c_void_p()
+        _check(_lib.hpt_create_system(self.n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(li),
+                                      ctypes.byref(c), self.precision, ctypes.byref(h)),
+               "hpt_create_system")
+        self._h = h
+        self.cdtype = torch.complex128 if self.precision == HPT_FP64 else torch.complex64
+
+    @classmethod
+    def from_laurent(cls, sysm, cell, precision=HPT_FP64):
+        return cls(sysm.n, sysm.m, sysm.exponents, sysm.coeffs, sysm.lifting, cell, precision)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hpt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- host data
+    def tau0(self, eps0=1e-10):
+        t = ctypes.c_double(0)
+        _check(_lib.hpt_get_info(self._h, None, None, None, ctypes.c_double(eps0), ctypes.byref(t)),
+               "hpt_get_info")
+        return float(t.value)
+
+    def texp(self):
+        e = np.zeros(self.M, np.int64)
+        D = ctypes.c_int64(0)
+        al = np.zeros(self.n, np.int64)
+        be = np.zeros(self.n, np.int64)
+        _check(_lib.hpt_get_texp(self._h, _np_ptr(e), ctypes.byref(D), _np_ptr(al), _np_ptr(be)),
+               "hpt_get_texp")
+        return dict(e=e.tolist(), D=int(D.value), alpha_num=al.tolist(), beta_num=be.tolist())
+
+    def device_error(self):
+        rc = _lib.hpt_device_error(self._h)
+        return rc
+
+    # ----------------------------------------------------------- device work
+    def eval(self, y, t, stream=None, out=None):
+        """H (p,n), H_y (p,n,n), H_t (p,n) at y (p,n) complex, t (p,) float64."""
+        p = y.shape[0]
+        assert y.dtype == self.cdtype and y.is_contiguous() and t.dtype == torch.float64
+        if out is None:
+            out = (torch.empty(p, self.n, dtype=self.cdtype, device=y.device),
+                   torch.empty(p, self.n, self.n, dtype=self.cdtype, device=y.device),
+                   torch.empty(p, self.n, dtype=self.cdtype, device=y.device))
+        H, Hy, Ht = out
+        _check(_lib.hpt_eval(self._h, p, _t_ptr(y), _t_ptr(t), _t_ptr(H), _t_ptr(Hy), _t_ptr(Ht),
+                             _stream(stream)), "hpt_eval")
+        return H, Hy, Ht
+
+    def paths_init(self, state, y0, params=None, stream=None):
+        params = params or Params()
+        assert y0.dtype == torch.complex128 and y0.is_contiguous()
+        c = state._c()
+        _check(_lib.hpt_paths_init(self._h, state.p, _t_ptr(y0), ctypes.byref(params), ctypes.byref(c),
+                                   _stream(stream)), "hpt_paths_init")
+        return state
+
+    def step(self, state, nsteps=1, params=None, stream=None):
+        params = params or Params()
+        c = state._c()
+        _check(_lib.hpt_step(self._h, state.p, ctypes.byref(c), int(nsteps), ctypes.byref(params),
+                             _stream(stream)), "hpt_step")
+        return state
+
+    def track(self, y0, params=None, stream=None):
+        """Returns (x (p,n) complex128, status (p,) int32, steps (p,) int32)."""
+        params = params or Params()
+        p = y0.shape[0]
+        assert y0.dtype == torch.complex128 and y0.is_contiguous()
+        x = torch.empty(p, self.n, dtype=torch.complex128, device=y0.device)
+        st = torch.empty(p, dtype=torch.int32, device=y0.device)
+        sp = torch.empty(p, dtype=torch.int32, device=y0.device)
+        _check(_lib.hpt_track(self._h, p, _t_ptr(y0), ctypes.byref(params), _t_ptr(x), _t_ptr(st),
+                              _t_ptr(sp), _stream(stream)), "hpt_track")
+        return x, st, sp
+
+    def polish(self, x, status=None, params=None, stream=None):
+        params = params or Params()
+        assert x.dtype == torch.complex128 and x.is_contiguous()
+        _check(_lib.hpt_polish(self._h, x.shape[0], _t_ptr(x), _t_ptr(status), ctypes.byref(params),
+                               _stream(stream)), "hpt_polish")
+        return x
+
+    def adjoint(self, x, gx, stream=None):
+        """Coefficient gradient (M,) complex128 of a real loss with gx = dL/dx."""
+        assert x.dtype == torch.complex128 and gx.dtype == torch.complex128
+        gc = torch.empty(self.M, dtype=torch.complex128, device=x.device)
+        _check(_lib.hpt_adjoint(self._h, x.shape[0], _t_ptr(x.contiguous()), _t_ptr(gx.contiguous()),
+                                _t_ptr(gc), _stream(stream)), "hpt_adjoint")
+        return gc
+
+    def profile(self, enable=True):
+        _check(_lib.hpt_profile_enable(self._h, int(bool(enable))), "hpt_profile_enable")
+
+    def profile_read(self):
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        launches = np.zeros(cap, np.int64)
+        ms = np.zeros(cap)
+        cnt = ctypes.c_int32(0)
+        _check(_lib.hpt_profile_read(self._h, cap, names, _np_ptr(launches), _np_ptr(ms),
+                                     ctypes.byref(cnt)), "hpt_profile_read")
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(cnt.value, cap))}
+

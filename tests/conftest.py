@@ -18,3 +18,15 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def hpt():
+    """The CUDA library's binding; the library is built if needed.  Fails (does
+    not skip) when it cannot be built or loaded."""
+    from paper_2111_14317_gb300 import build
+    build.build()
+    from paper_2111_14317_gb300 import hpt as mod
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return mod

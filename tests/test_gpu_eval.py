@@ -1,0 +1,87 @@
+"""Evaluation parity, CUDA path vs the CPU oracle (GPU).
+
+Tolerance (componentwise, scaled by the sum of term magnitudes the oracle
+returns): FP64 form <= 1e-11, mixed split-BF16 form <= 2e-4 per evaluation.
+Sizes span several 128-point tiles and a ragged tail; the full 65,536-point
+throughput workload is checked on sampled points.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cells
+
+import _util
+
+pytestmark = pytest.mark.gpu
+TOL = {0: 1e-11, 1: 2e-4}
+
+
+def _run(hpt, oracle_mod, s, cell, prec, y, t, sample=None):
+    te = cells.t_exponents(s, cell)
+    osys = oracle_mod.System(s, te["e"], te["D"])
+    h = hpt.System.from_laurent(s, cell, prec)
+    assert h.texp()["e"] == te["e"]
+    yd = torch.from_numpy(y).to("cuda", h.cdtype)
+    td = torch.from_numpy(t).cuda()
+    H, Hy, Ht = (a.cpu().numpy() for a in h.eval(yd, td))
+    torch.cuda.synchronize()
+    assert h.device_error() == 0
+    if sample is not None:
+        y, t, H, Hy, Ht = y[sample], t[sample], H[sample], Hy[sample], Ht[sample]
+    Ho, Hyo, Hto = osys.eval(y, np.log(t))
+    SH, SHy, SHt = osys.scale(y, np.log(t))
+    h.close()
+    # the library returns dH/dt = (dH/dtau) / t; the oracle returns dH/dtau
+    return (_util.scaled_err(H, Ho, SH), _util.scaled_err(Hy, Hyo, SHy),
+            _util.scaled_err(Ht, Hto / t[:, None], SHt / t[:, None]))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["n2", "n4", "n7_ragged", "n16", "n24"])
+@pytest.mark.parametrize("p", [1, 333])
+def test_eval_parity(hpt, oracle_mod, name, prec, p):
+    s, cell = _util.eval_case(name)
+    y, t = W.random_points(7, p, s.n)
+    errs = _run(hpt, oracle_mod, s, cell, prec, y, t)
+    assert max(errs) <= TOL[prec], errs
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_eval_full_size_sampled(hpt, oracle_mod, prec):
+    s, cell = _util.eval_case("n16")
+    y, t = W.random_points(1, 65536, 16)
+    sample = np.random.default_rng(0).choice(65536, 384, replace=False)
+    sample = np.concatenate([sample, [0, 127, 128, 65535]])
+    errs = _run(hpt, oracle_mod, s, cell, prec, y, t, sample)
+    assert max(errs) <= TOL[prec], errs
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_eval_tile_edges(hpt, oracle_mod, prec):
+    s, cell = _util.eval_case("n4")
+    for p in (127, 128, 129, 256):
+        y, t = W.random_points(p, p, s.n)
+        assert max(_run(hpt, oracle_mod, s, cell, prec, y, t)) <= TOL[prec]
+
+
+def test_eval_empty_is_noop(hpt):
+    s, cell = _util.eval_case("n4")
+    h = hpt.System.from_laurent(s, cell, 0)
+    y = torch.zeros(0, 4, dtype=torch.complex128, device="cuda")
+    t = torch.zeros(0, dtype=torch.float64, device="cuda")
+    H, Hy, Ht = h.eval(y, t)
+    assert H.shape == (0, 4) and Hy.shape == (0, 4, 4)
+
+
+def test_mixed_rejects_inexact_exponents(hpt):
+    s = W.laurent_system(3, 3, 4, -2, 2, 8)
+    e = s.exponents.copy()
+    e[0, 0] = 300
+    s2 = W.LaurentSystem(3, s.m, e, s.coeffs, s.lifting)
+    cell = {"kind": "lower", "alpha_num": [0, 0, 0], "denom": 1}
+    with pytest.raises(hpt.HptError) as err:
+        hpt.System.from_laurent(s2, cell, 1)
+    assert err.value.code == 4
+    hpt.System.from_laurent(s2, cell, 0).close()   # FP64 form takes it

@@ -1,0 +1,78 @@
+"""Euler-Newton step parity and checkpoint/resume (GPU).
+
+FP64 form: one step from a mid-track state gives the oracle's accept
+decisions and the same new state (relative 1e-10).  The state arrays are the
+whole checkpoint: 2k steps equal k steps, a host round trip and k more."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import cells
+
+import _util
+
+pytestmark = pytest.mark.gpu
+FIELDS = [("y", "y"), ("tau", "tau"), ("dtau", "dtau"), ("yacc", "y_acc"), ("tauacc", "tau_acc"),
+          ("dEacc", "dE_acc"), ("status", "status"), ("steps", "steps"), ("accepts", "accepts"),
+          ("rejects", "rejects"), ("streak", "streak")]
+
+
+def _cell_state(oracle_mod, s, c, nsteps):
+    te = cells.t_exponents(s, {"kind": "pairs", "pairs": c["pairs"]})
+    osys = oracle_mod.System(s, te["e"], te["D"])
+    P = oracle_mod.Params()
+    st = oracle_mod.PathState.start(cells.start_points(s, c["pairs"]), cells.tau0(te["e"], te["D"]),
+                                    P.dtau_init)
+    osys.step(P, st, nsteps)
+    return osys, st, P
+
+
+def _to_gpu(hpt, ost, prec):
+    g = hpt.PathState(ost.p, ost.y.shape[1], prec)
+    for a, b in FIELDS:
+        getattr(g, b).copy_(torch.from_numpy(np.ascontiguousarray(getattr(ost, a))).to(getattr(g, b).dtype))
+    return g
+
+
+@pytest.mark.parametrize("nsteps", [0, 3, 25])
+def test_fp64_step_matches_oracle(hpt, oracle_mod, nsteps):
+    s, cl, _ = _util.first_generic(W.config2)
+    for c in cl[:6]:
+        osys, ost, P = _cell_state(oracle_mod, s, c, nsteps)
+        h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": c["pairs"]}, 0)
+        g = _to_gpu(hpt, ost, 0)
+        h.step(g, 1)
+        osys.step(P, ost, 1)
+        torch.cuda.synchronize()
+        gh = g.to_host()
+        same = gh["accepts"].numpy() == ost.accepts
+        assert same.mean() >= 0.98
+        assert np.array_equal(gh["status"].numpy()[same], ost.status[same])
+        for a, b in (("y", "y"), ("yacc", "y_acc"), ("dEacc", "dE_acc")):
+            ref = getattr(ost, a)[same]
+            got = gh[b].numpy()[same]
+            assert np.max(np.abs(got - ref) / (1 + np.abs(ref))) < 1e-10, a
+        assert np.allclose(gh["tau"].numpy()[same], ost.tau[same], rtol=0, atol=1e-12)
+        h.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_step_resume_is_exact(hpt, oracle_mod, prec):
+    s, cl, _ = _util.first_generic(W.config2)
+    c = max(cl, key=lambda c: c["det"])
+    _, ost, _ = _cell_state(oracle_mod, s, c, 0)
+    h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": c["pairs"]}, prec)
+    a = _to_gpu(hpt, ost, prec)
+    b = _to_gpu(hpt, ost, prec)
+    h.step(a, 20)
+    h.step(b, 10)
+    saved = b.to_host()
+    b2 = hpt.PathState(b.p, b.n, prec)
+    b2.load(saved)
+    h.step(b2, 10)
+    torch.cuda.synchronize()
+    ha, hb = a.to_host(), b2.to_host()
+    for k in ha:
+        assert torch.equal(ha[k], hb[k]), k
+    h.close()
