@@ -247,7 +247,7 @@ def diagonalize(V):
     return U, [A[i][i] for i in range(n)], W
 
 
-def binomial_solutions(V, b):
+def binomial_solutions(V, b, limit=None):
     """All solutions y in (C*)^n of prod_j y_j^{V[k][j]} = b_k, k = 0..n-1.
 
     With U V W = diag(d): zeta = W^{-1} log y satisfies
@@ -261,19 +261,22 @@ def binomial_solutions(V, b):
     Wm = np.array(W, dtype=np.float64)
     sols = []
     for m in itertools.product(*[range(abs(dj)) for dj in d]):
+        if limit is not None and len(sols) >= limit:
+            break
         zeta = np.array([(Ulogb[j] + 2j * np.pi * m[j]) / d[j] for j in range(n)])
         sols.append(np.exp(Wm @ zeta))
     return np.array(sols, dtype=np.complex128).reshape(len(sols), n)
 
 
-def start_points(sysm, pairs):
+def start_points(sysm, pairs, limit=None):
     """Solutions of the cell's binomial start system H(y, t=0) = 0:
-    c_{k,p0} y^{a_{k,p0}} + c_{k,p1} y^{a_{k,p1}} = 0."""
+    c_{k,p0} y^{a_{k,p0}} + c_{k,p1} y^{a_{k,p1}} = 0 (the first `limit` of
+    them in the enumeration order when a limit is given)."""
     off = sysm.offsets
     V = pair_matrix(sysm, pairs)
     b = [-sysm.coeffs[off[k] + int(pairs[k][0])] / sysm.coeffs[off[k] + int(pairs[k][1])]
          for k in range(sysm.n)]
-    return binomial_solutions(V, b)
+    return binomial_solutions(V, b, limit)
 
 
 def tau0(e, D, eps0=1e-10):

@@ -12,7 +12,7 @@ namespace {
 // Paths per evaluate/solve round of hpt_step: the extended Jacobian of a
 // chunk (n (n+2) complex per path) stays resident in L2 between the two
 // kernels.  A multiple of the tensor-core tile.
-constexpr int64_t kChunk = 32768;
+constexpr int64_t kChunk = 65536;
 
 inline size_t csize(const hpt_system s) { return s->prec == HPT_FP64 ? 16 : 8; }
 
@@ -59,8 +59,12 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
                      const hpt_params& prm, cudaStream_t st) {
   const int n = s->n;
   const int64_t chunk = std::min<int64_t>(p, kChunk);
-  hpt_status rc = ensure_scratch(s, (size_t)chunk * n * (n + 2) * csize(s));
+  // scratch: extended Jacobian of a chunk, then the FP64 re-solve list
+  const size_t ext_bytes = ((size_t)chunk * n * (n + 2) * csize(s) + 255) / 256 * 256;
+  hpt_status rc = ensure_scratch(s, ext_bytes + 256 + (size_t)chunk * sizeof(int64_t));
   if (rc) return rc;
+  int32_t* redo_count = (int32_t*)((char*)s->d_scratch + ext_bytes);
+  int64_t* redo_list = (int64_t*)((char*)s->d_scratch + ext_bytes + 256);
   for (int r = 0; r < nsteps; ++r) {
     for (int64_t q0 = 0; q0 < p; q0 += chunk) {
       const int64_t cnt = std::min(chunk, p - q0);
@@ -76,6 +80,8 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
       a.st = sub;
       a.prm = prm;
       a.err = s->d_err;
+      a.redo_count = redo_count;
+      a.redo_list = redo_list;
       e = launch_solve_update(s, a, st);
       if (e != cudaSuccess) return cuda_fail(e, "solve launch");
     }

@@ -124,6 +124,8 @@ struct StepArgs {
   hpt_paths st;
   hpt_params prm;
   int32_t* err;
+  int32_t* redo_count = nullptr;   // mixed form: FP64 re-solve list (scratch)
+  int64_t* redo_list = nullptr;
 };
 
 // Consolidated solve + update + step control.  T = double for HPT_FP64,

@@ -14,6 +14,8 @@
 // from one factorisation.
 #include <math.h>
 
+#include <algorithm>
+
 #include "hpt_internal.h"
 
 namespace hpt {
@@ -70,13 +72,36 @@ __device__ __forceinline__ T group_max(T v) {
   return v;
 }
 
-template <typename T>
-__device__ __forceinline__ T cabs_t(cx<T> a) {
-  return hypot(a.x, a.y);
+__device__ __forceinline__ float t_hypot(float a, float b) { return hypotf(a, b); }
+__device__ __forceinline__ double t_hypot(double a, double b) { return hypot(a, b); }
+__device__ __forceinline__ float t_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double t_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float t_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double t_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float t_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double t_sqrt(double a) { return sqrt(a); }
+// 2^-e for m in [2^(e-1), 2^e): an exact power-of-two scale bringing m to [1/2, 1)
+__device__ __forceinline__ float pow2_inv(float m) {
+  int e;
+  frexpf(m, &e);
+  return (m > 0.f && isfinite(m)) ? ldexpf(1.f, -e) : 1.f;
+}
+__device__ __forceinline__ double pow2_inv(double m) {
+  int e;
+  frexp(m, &e);
+  return (m > 0.0 && isfinite(m)) ? ldexp(1.0, -e) : 1.0;
 }
 
-// Entry j of a register row without dynamic indexing (folds to a[j] when the
-// caller's loop is unrolled).
+template <typename T>
+__device__ __forceinline__ T cabs_t(cx<T> a) {
+  return t_hypot(a.x, a.y);
+}
+template <typename T>
+__device__ __forceinline__ T cmag(cx<T> a) {   // max(|re|, |im|): a cheap magnitude for scaling
+  return t_max(fabs(a.x), fabs(a.y));
+}
+
+// Entry j of a register row without dynamic indexing.
 template <typename T, int G>
 __device__ __forceinline__ cx<T> pick(const cx<T> (&a)[G], int j) {
   cx<T> r = a[0];
@@ -86,83 +111,118 @@ __device__ __forceinline__ cx<T> pick(const cx<T> (&a)[G], int j) {
   return r;
 }
 
+template <typename T, int G>
+__device__ __forceinline__ T pick_s(const T (&a)[G], int j) {
+  T r = a[0];
+#pragma unroll
+  for (int c = 1; c < G; ++c)
+    if (c == j) r = a[c];
+  return r;
+}
+
+// Pivot key: the magnitude |a_jj|^2 rounded to float with the low five
+// mantissa bits replaced by (31 - row), so that one integer max over the
+// group picks the largest magnitude, ties to the lowest row.  Rows already
+// used as pivots get key 0 and are never picked.
+template <typename T>
+__device__ __forceinline__ unsigned pivot_key(T v, bool used, int lane) {
+  if (used) return 0u;
+  float f = (float)v;
+  if (!(f == f)) f = 0.f;   // NaN rows stay eligible; the pivot test flags them
+  return (__float_as_uint(f) & ~31u) | (unsigned)(31 - lane);
+}
+
+// Two-sided equilibration by exact powers of two: every row, then every
+// column of [a] is brought to magnitude [1/2, 1).  The solution of the scaled
+// system is x = diag(dcol) x'; pivots then reflect the matrix's conditioning
+// rather than the scales of y and t^s in its rows and columns.
+template <typename T, int G>
+__device__ __forceinline__ void equilibrate(cx<T> (&a)[G], cx<T>& rhsE, cx<T>& rhsN, T (&dcol)[G]) {
+  T m = T(0);
+#pragma unroll
+  for (int c = 0; c < G; ++c) m = t_max(m, cmag(a[c]));
+  const T dr = pow2_inv(m);
+#pragma unroll
+  for (int c = 0; c < G; ++c) a[c] = mk<T>(a[c].x * dr, a[c].y * dr);
+  rhsE = mk<T>(rhsE.x * dr, rhsE.y * dr);
+  rhsN = mk<T>(rhsN.x * dr, rhsN.y * dr);
+#pragma unroll
+  for (int c = 0; c < G; ++c) {
+    T mc = cmag(a[c]);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) mc = t_max(mc, __shfl_xor_sync(0xffffffffu, mc, o, G));
+    dcol[c] = pow2_inv(mc);
+    a[c] = mk<T>(a[c].x * dcol[c], a[c].y * dcol[c]);
+  }
+}
+
 // Solves rows [a | rhsE | rhsN] of an n x n system held one row per lane
-// (n <= G).  On return lane j (< n) holds xE, xN = solution component j.
-// Returns false (group-uniform) when a pivot is zero or not finite.  cond
-// receives max |u_jj| / min |u_jj| over the pivots.  Every loop has a
-// constant trip count and rows are only indexed by unrolled constants, so the
-// rows stay in registers.
+// (n <= G) with partial pivoting.  prow is this group's shared-memory pivot
+// row buffer (G + 2 entries, 16-byte aligned).  On return lane j (< n) holds
+// xE, xN = solution component j.  Returns false (group-uniform) when a pivot
+// is zero or not finite; cond receives max |u_jj| / min |u_jj|.
 template <typename T, int G>
 __device__ bool group_solve(int n, cx<T> (&a)[G], cx<T>& rhsE, cx<T>& rhsN, cx<T>& xE,
-                            cx<T>& xN, T& cond) {
+                            cx<T>& xN, T& cond, cx<T>* prow) {
   const int lane = threadIdx.x & (G - 1);
   const int gbase = (threadIdx.x & 31) & ~(G - 1);
   bool used = lane >= n;
   int my_col = G;
   bool ok = true;
   T pmax = 0, pmin = 0;
+#pragma unroll 1
+  for (int j = 0; j < n; ++j) {
+    const cx<T> aj = pick<T, G>(a, j);
+    unsigned key = pivot_key<T>(abs2(aj), used, lane);
 #pragma unroll
-  for (int j = 0; j < G; ++j) {
-    if (j < n) {
-      const cx<T> aj = pick<T, G>(a, j);
-      T bv = used ? T(-1) : abs2(aj);
-      if (!used && !(bv == bv)) bv = T(0);   // NaN rows stay eligible, flagged below
-      int bl = lane;
+    for (int o = G / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o, G));
+    const int bl = 31 - (int)(key & 31u);
+    const bool was_used = used;
+    if (lane == bl) {
 #pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, bv, o, G);
-        const int ol = __shfl_xor_sync(0xffffffffu, bl, o, G);
-        if (ov > bv || (ov == bv && ol < bl)) { bv = ov; bl = ol; }
-      }
-      if (!(bv > T(0)) || !isfinite(bv)) ok = false;
-      const T pa = sqrt(bv > T(0) ? bv : T(0));
-      if (j == 0) { pmax = pa; pmin = pa; }
-      else { pmax = fmax(pmax, pa); pmin = fmin(pmin, pa); }
-      // broadcast the pivot row one entry at a time and eliminate
-      const cx<T> pj = shfl<T, G>(aj, bl);
-      const bool elim = !used && lane != bl;
-      const cx<T> l = elim ? cdiv(aj, pj) : mk<T>(0, 0);
-#pragma unroll
-      for (int c = 1; c < G; ++c) {
-        if (c > j && c < n) {
-          const cx<T> pc = shfl<T, G>(a[c], bl);
-          if (elim) a[c] = csub_mul(a[c], l, pc);
-        }
-      }
-      const cx<T> pE = shfl<T, G>(rhsE, bl), pN = shfl<T, G>(rhsN, bl);
-      if (elim) {
-        rhsE = csub_mul(rhsE, l, pE);
-        rhsN = csub_mul(rhsN, l, pN);
-      }
-      if (lane == bl) {
-        used = true;
-        my_col = j;
-      }
+      for (int c = 0; c < G; ++c) prow[c] = a[c];
+      prow[G] = rhsE;
+      prow[G + 1] = rhsN;
+      used = true;
+      my_col = j;
     }
+    __syncwarp();
+    const cx<T> pj = prow[j];
+    const T p2 = abs2(pj);
+    if (!(p2 > T(0)) || !isfinite(p2)) ok = false;
+    const T pa = t_sqrt(p2);
+    if (j == 0) { pmax = pa; pmin = pa; }
+    else { pmax = t_max(pmax, pa); pmin = t_min(pmin, pa); }
+    if (!was_used && lane != bl) {
+      const cx<T> l = cdiv(aj, pj);
+#pragma unroll
+      for (int c = 1; c < G; ++c)
+        if (c > j) a[c] = csub_mul(a[c], l, prow[c]);
+      rhsE = csub_mul(rhsE, l, prow[G]);
+      rhsN = csub_mul(rhsN, l, prow[G + 1]);
+    }
+    __syncwarp();
   }
   xE = mk<T>(0, 0);
   xN = mk<T>(0, 0);
-#pragma unroll
-  for (int jj = 0; jj < G; ++jj) {
-    const int j = G - 1 - jj;
-    if (j < n) {
-      // the lane that pivoted column j
-      const unsigned b = __ballot_sync(0xffffffffu, my_col == j);
-      const unsigned seg = (G == 32) ? b : ((b >> gbase) & ((1u << G) - 1u));
-      const int owner = seg ? (__ffs(seg) - 1) : 0;
-      const cx<T> aj = pick<T, G>(a, j);
-      cx<T> ve = mk<T>(0, 0), vn = mk<T>(0, 0);
-      if (lane == owner) {
-        ve = cdiv(rhsE, aj);
-        vn = cdiv(rhsN, aj);
-      }
-      ve = shfl<T, G>(ve, owner);
-      vn = shfl<T, G>(vn, owner);
-      if (lane == j) { xE = ve; xN = vn; }
-      if (my_col < j) {
-        rhsE = csub_mul(rhsE, aj, ve);
-        rhsN = csub_mul(rhsN, aj, vn);
-      }
+#pragma unroll 1
+  for (int j = n - 1; j >= 0; --j) {
+    // the lane that pivoted column j
+    const unsigned b = __ballot_sync(0xffffffffu, my_col == j);
+    const unsigned seg = (G == 32) ? b : ((b >> gbase) & ((1u << G) - 1u));
+    const int owner = seg ? (__ffs(seg) - 1) : 0;
+    const cx<T> aj = pick<T, G>(a, j);
+    cx<T> ve = mk<T>(0, 0), vn = mk<T>(0, 0);
+    if (lane == owner) {
+      ve = cdiv(rhsE, aj);
+      vn = cdiv(rhsN, aj);
+    }
+    ve = shfl<T, G>(ve, owner);
+    vn = shfl<T, G>(vn, owner);
+    if (lane == j) { xE = ve; xN = vn; }
+    if (my_col < j) {
+      rhsE = csub_mul(rhsE, aj, ve);
+      rhsN = csub_mul(rhsN, aj, vn);
     }
   }
   cond = pmin > T(0) ? pmax / pmin : T(INFINITY);
@@ -218,73 +278,56 @@ __device__ __forceinline__ void load_row(int n, const void* ext, int64_t path, b
   }
 }
 
-// One Euler-Newton step per ACTIVE path: solve, then accept/reject and the
-// next prediction.  T is the state and solve precision; FP32 solves whose
-// pivot ratio exceeds prm.cond_max are redone in FP64 from the same data.
-template <typename T, int G>
-__global__ void __launch_bounds__(128)
-solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
-                    int32_t* __restrict__ n_fp64) {
+// Equilibrated solve of one path's [H_y | -H_tau | -H]; the solution is
+// returned unscaled.  Precision T, extended Jacobian stored in precision S.
+template <typename T, typename S, int G>
+__device__ __forceinline__ bool path_solve(int n, const void* ext, int64_t path, bool valid, cx<T>* prow,
+                                           cx<T>& xE, cx<T>& xN, T& cond) {
   const int lane = threadIdx.x & (G - 1);
-  const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  bool valid = path < p;
-  int32_t status = valid ? S.status[path] : -1;
-  valid = valid && status == HPT_PATH_ACTIVE;
-  if (!__any_sync(0xffffffffu, valid)) return;   // warp-uniform exit
-
-  cx<T> a[G], rhsE, rhsN, xE, xN;
-  load_row<T, T, G>(n, ext, path, valid, a, rhsE, rhsN);
+  cx<T> a[G], rhsE, rhsN;
+  load_row<T, S, G>(n, ext, path, valid, a, rhsE, rhsN);
   bool fin = true;
 #pragma unroll
   for (int c = 0; c < G; ++c) fin = fin && finite(a[c]);
-  fin = fin && finite(rhsE) && finite(rhsN);
-  fin = group_all<G>(fin);
-  T cond;
-  bool ok = group_solve<T, G>(n, a, rhsE, rhsN, xE, xN, cond) && fin;
-  if (sizeof(T) == 4) {
-    // Ill-conditioned in FP32: redo the factorisation in FP64 from the same
-    // (FP32) Jacobian.
-    const bool redo = valid && ok && !(cond <= (T)prm.cond_max);
-    if (__any_sync(0xffffffffu, redo)) {
-      cx<double> a2[G], e2, n2, xe2, xn2;
-      load_row<double, T, G>(n, ext, path, valid, a2, e2, n2);
-      double c2;
-      bool ok2 = group_solve<double, G>(n, a2, e2, n2, xe2, xn2, c2);
-      if (redo) {
-        xE = mk<T>((T)xe2.x, (T)xe2.y);
-        xN = mk<T>((T)xn2.x, (T)xn2.y);
-        ok = ok2;
-        if (lane == 0 && n_fp64) atomicAdd(n_fp64, 1);
-      }
-    }
-  }
-  if (!valid) return;   // no shuffles below
+  fin = group_all<G>(fin && finite(rhsE) && finite(rhsN));
+  T dcol[G];
+  equilibrate<T, G>(a, rhsE, rhsN, dcol);
+  const bool ok = group_solve<T, G>(n, a, rhsE, rhsN, xE, xN, cond, prow) && fin;
+  const T dj = pick_s<T, G>(dcol, lane);
+  xE = mk<T>(xE.x * dj, xE.y * dj);
+  xN = mk<T>(xN.x * dj, xN.y * dj);
+  return ok;
+}
 
+// Step control of one path (all lanes of its group), given the directions:
+// accept/reject, then the next prediction.  TS is the state precision.
+template <typename TS, int G>
+__device__ __forceinline__ void update_path(int n, int64_t path, int32_t status, bool ok, cx<TS> xE,
+                                            cx<TS> xN, const hpt_paths& S, const hpt_params& prm) {
+  const int lane = threadIdx.x & (G - 1);
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   const bool mine = lane < n;
   const size_t vi = (size_t)path * n + lane;
-  cx<T> y = mine ? ld<T>(S.y, vi) : mk<T>(0, 0);
+  cx<TS> y = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
   bool solfin = !mine || (finite(xE) && finite(xN));
-  // group reductions (only the group's own lanes reach here: all lanes of an
-  // active group are valid together)
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   solfin = (__ballot_sync(gmask, solfin) & gmask) == gmask;
-  T ny = mine ? cabs_t(y) : T(0), nd = mine ? cabs_t(xN) : T(0);
+  TS ny = mine ? cabs_t(y) : TS(0), nd = mine ? cabs_t(xN) : TS(0);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
-    ny = fmax(ny, __shfl_xor_sync(gmask, ny, o, G));
-    nd = fmax(nd, __shfl_xor_sync(gmask, nd, o, G));
+    ny = t_max(ny, __shfl_xor_sync(gmask, ny, o, G));
+    nd = t_max(nd, __shfl_xor_sync(gmask, nd, o, G));
   }
   const bool bad = !(ok && solfin);
   double tau = S.tau[path], dtau = S.dtau[path], tauacc = S.tau_acc[path];
   int32_t steps = S.steps[path] + 1, accepts = S.accepts[path], rejects = S.rejects[path],
           streak = S.streak[path];
-  const T err = nd / fmax(T(1), ny);
-  const bool accept = !bad && err <= (T)prm.tol_accept;
-  cx<T> yacc = mine ? ld<T>(S.y_acc, vi) : mk<T>(0, 0);
-  cx<T> dEacc = mine ? ld<T>(S.dE_acc, vi) : mk<T>(0, 0);
+  const TS err = nd / t_max(TS(1), ny);
+  const bool accept = !bad && err <= (TS)prm.tol_accept;
+  cx<TS> yacc = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
+  cx<TS> dEacc = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
   bool predict = true;
   if (accept) {
-    yacc = mk<T>(y.x + xN.x, y.y + xN.y);
+    yacc = mk<TS>(y.x + xN.x, y.y + xN.y);
     dEacc = xE;
     tauacc = tau;
     accepts += 1;
@@ -293,8 +336,8 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
       status = HPT_PATH_CONVERGED;
       predict = false;
     } else {
-      const T m = mine ? cabs_t(yacc) : T(1);
-      bool div = mine && (!(m < (T)prm.div_bound) || !(m > (T)(1.0 / prm.div_bound)));
+      const TS m = mine ? cabs_t(yacc) : TS(1);
+      bool div = mine && (!(m < (TS)prm.div_bound) || !(m > (TS)(1.0 / prm.div_bound)));
       div = (__ballot_sync(gmask, div) & gmask) != 0u;
       if (div) {
         status = HPT_PATH_DIVERGED;
@@ -312,7 +355,7 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
       if (bad) {
         status = HPT_PATH_SINGULAR;
       } else {
-        y = mk<T>(y.x + xN.x, y.y + xN.y);
+        y = mk<TS>(y.x + xN.x, y.y + xN.y);
         yacc = y;
         if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
       }
@@ -326,14 +369,14 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
   }
   if (predict) {
     const double h = fmin(dtau, -tauacc);
-    y = mk<T>(yacc.x + (T)h * dEacc.x, yacc.y + (T)h * dEacc.y);
+    y = mk<TS>(yacc.x + (TS)h * dEacc.x, yacc.y + (TS)h * dEacc.y);
     tau = tauacc + h;
     if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
   }
   if (mine) {
-    st<T>(S.y, vi, y);
-    st<T>(S.y_acc, vi, yacc);
-    st<T>(S.dE_acc, vi, dEacc);
+    st<TS>(S.y, vi, y);
+    st<TS>(S.y_acc, vi, yacc);
+    st<TS>(S.dE_acc, vi, dEacc);
   }
   if (lane == 0) {
     S.tau[path] = tau;
@@ -347,6 +390,58 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
   }
 }
 
+// One Euler-Newton step per ACTIVE path: consolidated solve, then the step
+// control.  T is the state and solve precision.  FP32 solves whose pivot
+// ratio (after equilibration) exceeds prm.cond_max are not applied here: the
+// path goes to redo_list and is solved again in FP64 by redo_fp64_kernel.
+template <typename T, int G>
+__global__ void __launch_bounds__(128)
+solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
+                    int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list) {
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  bool valid = path < p;
+  const int32_t status = valid ? S.status[path] : -1;
+  valid = valid && status == HPT_PATH_ACTIVE;
+  if (!__any_sync(0xffffffffu, valid)) return;   // warp-uniform exit
+  __shared__ __align__(16) cx<T> prow_buf[128 / G][G + 2];
+  cx<T> xE, xN;
+  T cond;
+  const bool ok = path_solve<T, T, G>(n, ext, path, valid, prow_buf[threadIdx.x / G], xE, xN, cond);
+  if (!valid) return;   // group-uniform; only group-masked shuffles below
+  if (sizeof(T) == 4 && redo_list && ok && !(cond <= (T)prm.cond_max)) {
+    if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = path;
+    return;
+  }
+  update_path<T, G>(n, path, status, ok, xE, xN, S, prm);
+}
+
+// FP64 re-solve of the paths listed by the FP32 kernel (same FP32 Jacobian,
+// FP64 factorisation), then their step control in the FP32 state.
+template <int G>
+__global__ void __launch_bounds__(128)
+redo_fp64_kernel(int n, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
+                 const int32_t* __restrict__ redo_count, const int64_t* __restrict__ redo_list) {
+  __shared__ __align__(16) cx<double> prow_buf[128 / G][G + 2];
+  const int count = *redo_count;
+  const int groups_per_warp = 32 / G;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int g = (threadIdx.x & 31) / G;
+  for (int64_t base = warp_id * groups_per_warp; base < count; base += nwarps * groups_per_warp) {
+    const int64_t i = base + g;
+    const bool valid = i < count;
+    const int64_t path = valid ? redo_list[i] : 0;
+    cx<double> xE, xN;
+    double cond;
+    const bool ok = path_solve<double, float, G>(n, ext, path, valid, prow_buf[threadIdx.x / G], xE, xN, cond);
+    if (valid)
+      update_path<float, G>(n, path, S.status[path], ok, mk<float>((float)xE.x, (float)xE.y),
+                            mk<float>((float)xN.x, (float)xN.y), S, prm);
+    __syncwarp();
+  }
+}
+
 // Newton polish update at t = 1 (FP64): x += dN until |dN|/max(1,|x|) <= tol.
 template <int G>
 __global__ void __launch_bounds__(128)
@@ -356,10 +451,10 @@ newton_kernel(int n, int64_t p, const void* __restrict__ ext, double2* __restric
   const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const bool valid = path < p && done[path] == 0;
   if (!__any_sync(0xffffffffu, valid)) return;
-  cx<double> a[G], rE, rN, xE, xN;
-  load_row<double, double, G>(n, ext, path, valid, a, rE, rN);
+  __shared__ __align__(16) cx<double> prow_buf[128 / G][G + 2];
+  cx<double> xE, xN;
   double cond;
-  bool ok = group_solve<double, G>(n, a, rE, rN, xE, xN, cond);
+  bool ok = path_solve<double, double, G>(n, ext, path, valid, prow_buf[threadIdx.x / G], xE, xN, cond);
   if (!valid) return;
   const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   const bool mine = lane < n;
@@ -410,7 +505,8 @@ adjoint_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t*
   rE = have ? ld<double>(gx, (size_t)path * n + lane) : mk<double>(0, 0);
   rN = mk<double>(0, 0);
   double cond;
-  bool ok = group_solve<double, G>(n, a, rE, rN, lam, dummy, cond);
+  __shared__ __align__(16) cx<double> prow_buf[128 / G][G + 2];
+  bool ok = group_solve<double, G>(n, a, rE, rN, lam, dummy, cond, prow_buf[threadIdx.x / G]);
   if (have) {
     const double2 v = x[(size_t)path * n + lane];
     zsh[grp][lane] = make_double2(log(hypot(v.x, v.y)), atan2(v.y, v.x));
@@ -516,16 +612,28 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
   const bool dbl = s->prec == HPT_FP64;
   const int G = a.n <= 8 ? 8 : (a.n <= 16 ? 16 : 32);
   const unsigned nb = blocks_for(a.p * G, 128);
-  int pi = prof_begin(s, dbl ? "solve_update_fp64" : "solve_update_fp32", st);
   if (dbl) {
-    if (G == 8) solve_update_kernel<double, 8><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr);
-    else if (G == 16) solve_update_kernel<double, 16><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr);
-    else solve_update_kernel<double, 32><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr);
-  } else {
-    if (G == 8) solve_update_kernel<float, 8><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr);
-    else if (G == 16) solve_update_kernel<float, 16><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr);
-    else solve_update_kernel<float, 32><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr);
+    int pi = prof_begin(s, "solve_update_fp64", st);
+    if (G == 8) solve_update_kernel<double, 8><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr, nullptr);
+    else if (G == 16) solve_update_kernel<double, 16><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr, nullptr);
+    else solve_update_kernel<double, 32><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr, nullptr);
+    prof_end(s, pi, st);
+    return cudaGetLastError();
   }
+  cudaError_t e = cudaMemsetAsync(a.redo_count, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  int pi = prof_begin(s, "solve_update_fp32", st);
+  if (G == 8) solve_update_kernel<float, 8><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  else if (G == 16) solve_update_kernel<float, 16><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  else solve_update_kernel<float, 32><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  prof_end(s, pi, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // FP64 re-solves: a fixed grid that loops over the device-side list
+  unsigned rb = blocks_for(std::min<int64_t>(a.p, 8192) * G, 128);
+  pi = prof_begin(s, "redo_fp64", st);
+  if (G == 8) redo_fp64_kernel<8><<<rb, 128, 0, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  else if (G == 16) redo_fp64_kernel<16><<<rb, 128, 0, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  else redo_fp64_kernel<32><<<rb, 128, 0, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
   prof_end(s, pi, st);
   return cudaGetLastError();
 }

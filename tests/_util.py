@@ -62,3 +62,20 @@ def eval_case(name):
         alpha = W.random_alpha(24, 24, -2, 2)
         return s, {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
     raise KeyError(name)
+
+
+def planted_case(cfg, min_det, max_det=400000):
+    """First attempt of a planted-cell workload whose pair matrix has
+    min_det <= |det V| <= max_det and passes the cell test:
+    (system, pairs, t-exponent dict, |det V|)."""
+    for att in range(200):
+        s, pairs = cfg(att)
+        d = abs(cells.det_int(cells.pair_matrix(s, pairs)))
+        if not (min_det <= d <= max_det):
+            continue
+        try:
+            te = cells.t_exponents(s, {"kind": "pairs", "pairs": pairs})
+        except (cells.NotACell, cells.NonGeneric):
+            continue
+        return s, pairs, te, d
+    raise RuntimeError("no planted cell found")
