@@ -200,6 +200,27 @@ hpt_status hpt_paths_init(hpt_system sys, int64_t p, const void* y0_dev, const h
 hpt_status hpt_step(hpt_system sys, int64_t p, const hpt_paths* state, int32_t nsteps,
                     const hpt_params* params, void* stream);
 
+/* The step of hpt_step with no device-memory allocation.  The paper has no
+ * counterpart of this entry point.  Its scratch (the extended Jacobians of
+ * the p paths and the FP64 re-solve list) comes from a 32 MiB array compiled
+ * into the library (a file-scope __device__ array that every GPU loading the
+ * library holds until the process exits) instead of from cudaMalloc.  It is
+ * for callers that must not allocate device memory while they run:
+ * applications that give all device memory to their own allocator or pool and
+ * forbid libraries from allocating behind it, code with a fixed device-memory
+ * budget, and loops that cannot afford the device synchronisation of
+ * cudaMalloc/cudaFree.  The caller still owns the state buffers.
+ * Limit: p <= (32 MiB - 512) / (n (n+2) c + 8) paths, c = 16 bytes (HPT_FP64)
+ * or 8 (HPT_MIXED); for n = 16 that is 7,269 (FP64) or 14,512 (mixed) paths.
+ * Larger p returns HPT_ERANGE (split the batch).  The first call on a device
+ * looks up the array's device address with cudaGetSymbolAddress (with that
+ * device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the one array: calls whose GPU work
+ * overlaps (other streams, other host threads) race and corrupt each other.
+ * Same arguments, results and error behaviour as hpt_step otherwise. */
+hpt_status hpt_step_static(hpt_system sys, int64_t p, const hpt_paths* state, int32_t nsteps,
+                           const hpt_params* params, void* stream);
+
 /* Whole tracks: start points y0_dev[p*n] complex128 at tau0 -> tau = 0, then an
  * FP64 Newton polish at t = 1 of the converged paths.  Writes x_out_dev[p*n]
  * complex128, status_dev[p], steps_dev[p].  Synchronises the stream. */

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA err
 
 EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lift_exponents",
            "hpt_create_system", "hpt_destroy", "hpt_get_info", "hpt_get_texp", "hpt_eval",
-           "hpt_paths_init", "hpt_step", "hpt_track", "hpt_polish", "hpt_adjoint",
+           "hpt_paths_init", "hpt_step", "hpt_step_static", "hpt_track", "hpt_polish", "hpt_adjoint",
            "hpt_device_error", "hpt_profile_enable", "hpt_profile_read"]
 
 
@@ -80,6 +80,7 @@ for _name, _args in {
     "hpt_eval": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
     "hpt_paths_init": [_VP, _I64, _VP, _VP, _VP, _VP],
     "hpt_step": [_VP, _I64, _VP, _I32, _VP, _VP],
+    "hpt_step_static": [_VP, _I64, _VP, _I32, _VP, _VP],
     "hpt_track": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
     "hpt_polish": [_VP, _I64, _VP, _VP, _VP, _VP],
     "hpt_adjoint": [_VP, _I64, _VP, _VP, _VP, _VP],
@@ -263,6 +264,16 @@ class System:
         c = state._c()
         _check(_lib.hpt_step(self._h, state.p, ctypes.byref(c), int(nsteps), ctypes.byref(params),
                              _stream(stream)), "hpt_step")
+        return state
+
+    def step_static(self, state, nsteps=1, params=None, stream=None):
+        """hpt_step without device-memory allocation: scratch from the library's
+        fixed 32 MiB array (see hpt_step_static in include/hpt.h for the path
+        limit and the sharing rules)."""
+        params = params or Params()
+        c = state._c()
+        _check(_lib.hpt_step_static(self._h, state.p, ctypes.byref(c), int(nsteps), ctypes.byref(params),
+                                    _stream(stream)), "hpt_step_static")
         return state
 
     def track(self, y0, params=None, stream=None):
