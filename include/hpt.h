@@ -210,8 +210,9 @@ hpt_status hpt_step(hpt_system sys, int64_t p, const hpt_paths* state, int32_t n
  * forbid libraries from allocating behind it, code with a fixed device-memory
  * budget, and loops that cannot afford the device synchronisation of
  * cudaMalloc/cudaFree.  The caller still owns the state buffers.
- * Limit: p <= (32 MiB - 512) / (n (n+2) c + 8) paths, c = 16 bytes (HPT_FP64)
- * or 8 (HPT_MIXED); for n = 16 that is 7,269 (FP64) or 14,512 (mixed) paths.
+ * Limit: p <= (32 MiB - 511 - 127 n (n+2) c) / (n (n+2) c + 8) paths, c = 16
+ * bytes (HPT_FP64) or 8 (HPT_MIXED); for n = 16 that is 7,142 (FP64) or 14,386
+ * (mixed) paths.
  * Larger p returns HPT_ERANGE (split the batch).  The first call on a device
  * looks up the array's device address with cudaGetSymbolAddress (with that
  * device current) and caches it; make that first call before any stream

@@ -60,7 +60,7 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
   const int n = s->n;
   const int64_t chunk = std::min<int64_t>(p, kChunk);
   // scratch: extended Jacobian of a chunk, then the FP64 re-solve list
-  const size_t ext_bytes = ((size_t)chunk * n * (n + 2) * csize(s) + 255) / 256 * 256;
+  const size_t ext_bytes = (ext_entries(chunk, n) * csize(s) + 255) / 256 * 256;
   hpt_status rc = ensure_scratch(s, ext_bytes + 256 + (size_t)chunk * sizeof(int64_t));
   if (rc) return rc;
   int32_t* redo_count = (int32_t*)((char*)s->d_scratch + ext_bytes);
@@ -93,7 +93,7 @@ hpt_status polish_impl(hpt_system s, int64_t p, void* x, int32_t* done, const hp
                        cudaStream_t st) {
   const int n = s->n;
   const int64_t chunk = std::min<int64_t>(p, kChunk);
-  hpt_status rc = ensure_scratch(s, (size_t)chunk * n * (n + 2) * 16);
+  hpt_status rc = ensure_scratch(s, ext_entries(chunk, n) * 16);
   if (rc) return rc;
   for (int it = 0; it < prm.polish_iters; ++it) {
     for (int64_t q0 = 0; q0 < p; q0 += chunk) {
@@ -262,7 +262,7 @@ hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, v
   if (!x || !gx) { set_error("x or gx is NULL"); return HPT_EINVAL; }
   const int n = s->n;
   const int64_t chunk = std::min<int64_t>(p, 8192);
-  const size_t ext_bytes = ((size_t)chunk * n * (n + 2) * 16 + 255) / 256 * 256;
+  const size_t ext_bytes = (ext_entries(chunk, n) * 16 + 255) / 256 * 256;
   if ((rc = ensure_scratch(s, ext_bytes + (size_t)chunk * s->M * 16))) return rc;
   void* contrib = (char*)s->d_scratch + ext_bytes;
   for (int64_t q0 = 0; q0 < p; q0 += chunk) {

@@ -96,16 +96,16 @@ eval_fp64_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_
     if (path >= p) continue;
     // op. 3 of Algorithm 2: D_y h_k = D_z h_k diag(e^{-z})
     if (ext) {
-      double2* row = ext + ((size_t)path * n + k) * np2;
 #pragma unroll
       for (int u = 0; u < NMAX; ++u) {
         if (u < n) {
           const double2 iy = iys[u][lane];
-          row[u] = make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
+          ext[ext_index(path, k, u, n)] =
+              make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
         }
       }
-      row[n] = accT;
-      row[n + 1] = accH;
+      ext[ext_index(path, k, n, n)] = accT;
+      ext[ext_index(path, k, n + 1, n)] = accH;
     }
     if (oHy) {
       double2* row = oHy + ((size_t)path * n + k) * n;

@@ -261,7 +261,7 @@ static MixedLayout mixed_layout(int n, int max_m) {
   L.off_blo = L.off_bhi + L.NJ * L.KC * 2;
   L.off_texp = L.off_blo + L.NJ * L.KC * 2;
   L.chunk_bytes = round_up(L.off_texp + L.MP * 4, 128);
-  int cols = 2 * L.MP + L.NJ, t = 32;
+  int cols = 4 * L.MP + L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
   while (t < cols) t *= 2;
   L.tmem_cols = t;
   return L;

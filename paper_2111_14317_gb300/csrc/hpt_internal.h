@@ -29,7 +29,7 @@ struct MixedLayout {
   int KC = 0;   // 2 MP
   int off_bexp = 0, off_bhi = 0, off_blo = 0, off_texp = 0;
   int chunk_bytes = 0;
-  int tmem_cols = 0;     // power of two >= 2 MP + NJ
+  int tmem_cols = 0;     // power of two >= 4 MP + NJ
   int smem_bytes = 0;    // dynamic shared memory of the eval kernel
 };
 
@@ -40,6 +40,16 @@ struct MixedLayout {
 inline int canon_offset(int r, int k, int K) {
   return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
+
+// Index of entry (path, k, u) of the extended Jacobian scratch, u < n+2:
+// tiles of 128 paths, inside a tile entry (k, u) of all 128 paths is
+// contiguous, so the 128 threads of a tile write (and the lane groups of the
+// solve read) whole sectors.  The scratch holds ceil(p/128)*128 paths.
+__host__ __device__ inline size_t ext_index(int64_t path, int k, int u, int n) {
+  return ((size_t)(path >> 7) * (size_t)(n * (n + 2)) + (size_t)k * (n + 2) + (size_t)u) * 128 +
+         (size_t)(path & 127);
+}
+inline size_t ext_entries(int64_t p, int n) { return (size_t)((p + 127) / 128) * 128 * n * (n + 2); }
 
 struct KernelStat {
   std::string name;
@@ -99,8 +109,9 @@ int prof_begin(hpt_system s, const char* name, cudaStream_t st);
 void prof_end(hpt_system s, int idx, cudaStream_t st);
 
 // Kernel launchers (return cudaSuccess or the launch error).
-// Output layout: either the extended Jacobian ext[p][n][n+2] (row k =
-// [dH_k/dy_0..dH_k/dy_{n-1}, dH_k/dtau, H_k]) or the user layout of hpt_eval.
+// Output layout: either the extended Jacobian (row k = [dH_k/dy_0..
+// dH_k/dy_{n-1}, dH_k/dtau, H_k], stored at ext_index) or the user layout of
+// hpt_eval.
 struct EvalOut {
   void* ext = nullptr;       // extended Jacobian (step scratch)
   void* H = nullptr;         // user layout

@@ -138,7 +138,11 @@ constexpr float kTwoPiHi = 6.28318548202514648f;
 constexpr float kTwoPiLo = -1.74845553e-07f;
 constexpr float kInvTwoPi = 0.159154943091895336f;
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int kEvalThreads = 256;   // two warpgroups over the 128 TMEM lanes
+
+// Barriers in shared memory: [0], [1] constant buffers; [2], [3] exponent
+// accumulators W[0], W[1]; [4] coefficient accumulator J.
+__global__ void __launch_bounds__(kEvalThreads, 2)
 eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
                   const uint8_t* __restrict__ chunks, float2* __restrict__ ext, float2* __restrict__ oH,
                   float2* __restrict__ oHy, float2* __restrict__ oHt, int32_t* __restrict__ err) {
@@ -149,20 +153,21 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   float2* sInvY = (float2*)(sm + P.s_invy);        // [n][128]
   uint8_t* sAcHi = sm + P.s_achi;
   uint8_t* sAcLo = sm + P.s_aclo;
-  uint64_t* bars = (uint64_t*)(sm + P.s_bar);      // [0],[1] const buffers, [2] mma
-  uint32_t* tslot = (uint32_t*)(sm + P.s_bar + 32);
-  int* sAbort = (int*)(sm + P.s_bar + 36);
+  uint64_t* bars = (uint64_t*)(sm + P.s_bar);
+  uint32_t* tslot = (uint32_t*)(sm + P.s_bar + 64);
+  int* sAbort = (int*)(sm + P.s_bar + 68);
 
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & 127;          // point of the tile = TMEM lane
+  const int half = tid >> 7;          // warpgroup: splits the column chunks
   const int n = P.n;
   const int my_tiles = (P.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   if (my_tiles <= 0) return;
   const int g_total = my_tiles * n;
+  const bool lookahead = P.nbuf == 2;
 
   if (tid == 0) {
-    mbar_init(su32(&bars[0]), 1);
-    mbar_init(su32(&bars[1]), 1);
-    mbar_init(su32(&bars[2]), 1);
+    for (int i = 0; i < 5; ++i) mbar_init(su32(&bars[i]), 1);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -175,81 +180,89 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  const uint32_t t_wre = tbase, t_wim = tbase + P.MP, t_j = tbase + 2 * P.MP;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t t_j = tbase + 4 * P.MP;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 
-  // constant images for the first nbuf equations
-  if (tid == 0) {
-    for (int g = 0; g < P.nbuf && g < g_total; ++g)
-      bulk_load(su32(sm + (g ? P.s_const1 : P.s_const0)), chunks + (size_t)(g % n) * P.chunk_bytes, P.chunk_bytes, su32(&bars[g]));
-  }
-  uint32_t mma_phase = 0;
-  int g = 0;
+  auto cbuf = [&](int g) -> uint8_t* { return sm + ((P.nbuf == 2 && (g & 1)) ? P.s_const1 : P.s_const0); };
+  auto cpar = [&](int g) -> uint32_t { return (uint32_t)(P.nbuf == 2 ? (g >> 1) : g) & 1u; };
   const uint32_t idx_x = idesc_bf16(128, P.MP), idx_c = idesc_bf16(128, P.NJ);
   const int kx_steps = P.KX / 16, kc_steps = P.KC / 16;
   const uint32_t sbo_x = P.KX * 16, sbo_c = P.KC * 16;
 
+  // exponent GEMM of work item g (equation g % n) into W[g & 1]; thread 0 only
+  auto issue_exp = [&](int g) -> bool {
+    if (!mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g))) return false;
+    tc_fence_after();
+    const uint32_t cb = su32(cbuf(g));
+    const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * P.MP);
+    for (int s = 0; s < kx_steps; ++s) {
+      const uint64_t bd = smem_desc(cb + P.off_bexp + s * 256, 128, sbo_x);
+      mma_bf16(tw, smem_desc(su32(sAre) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
+      mma_bf16(tw + P.MP, smem_desc(su32(sAim) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
+    }
+    mma_commit(su32(&bars[2 + (g & 1)]));
+    return true;
+  };
+
+  // constant images for the first nbuf work items
+  if (tid == 0) {
+    for (int g = 0; g < P.nbuf && g < g_total; ++g)
+      bulk_load(su32(cbuf(g)), chunks + (size_t)(g % n) * P.chunk_bytes, P.chunk_bytes, su32(&bars[g]));
+  }
+  int g = 0;
+
   for (int it = 0; it < my_tiles; ++it) {
     const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-    const int64_t path = (int64_t)tile * 128 + tid;
+    const int64_t path = (int64_t)tile * 128 + row;
     const bool live = path < P.p;
-    // ---- op. 1: z = log y, three-way BF16 split, 1/y
-    double tv = (live && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);
+    // ---- op. 1: z = log y, three-way BF16 split, 1/y (variables split by half)
+    const double tv = (live && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);
     const double tau = tau_is_t ? log(tv) : tv;
     const float tau_d = (float)(tau * (double)P.inv_D);
     const float t_inv = (float)(tau_is_t ? 1.0 / tv : exp(-tau));
-    for (int j = 0; j < n; ++j) {
+    for (int j = half; j < n; j += 2) {
       float2 v = live ? y[path * n + j] : make_float2(1.f, 0.f);
       const float zr = logf(hypotf(v.x, v.y)), zi = atan2f(v.y, v.x);
       const float r2 = v.x * v.x + v.y * v.y;
-      sInvY[j * 128 + tid] = make_float2(v.x / r2, -v.y / r2);
+      sInvY[j * 128 + row] = make_float2(v.x / r2, -v.y / r2);
       float rem_r = zr, rem_i = zi;
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
         const uint16_t hr = bf16_rn(rem_r), hi = bf16_rn(rem_i);
-        *(uint16_t*)(sAre + canon(tid, s * n + j, P.KX)) = hr;
-        *(uint16_t*)(sAim + canon(tid, s * n + j, P.KX)) = hi;
+        *(uint16_t*)(sAre + canon(row, s * n + j, P.KX)) = hr;
+        *(uint16_t*)(sAim + canon(row, s * n + j, P.KX)) = hi;
         rem_r -= bf16_f(hr);
         rem_i -= bf16_f(hi);
       }
     }
-    for (int q = 3 * n; q < P.KX; ++q) {
-      *(uint16_t*)(sAre + canon(tid, q, P.KX)) = 0;
-      *(uint16_t*)(sAim + canon(tid, q, P.KX)) = 0;
+    for (int q = 3 * n + half; q < P.KX; q += 2) {
+      *(uint16_t*)(sAre + canon(row, q, P.KX)) = 0;
+      *(uint16_t*)(sAim + canon(row, q, P.KX)) = 0;
     }
     proxy_fence();
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && lookahead && !issue_exp(g)) atomicExch(sAbort, 1);
 
     for (int k = 0; k < n; ++k, ++g) {
-      const int buf = P.nbuf == 2 ? (g & 1) : 0;
-      const uint32_t use = P.nbuf == 2 ? (uint32_t)(g >> 1) : (uint32_t)g;   // uses of this buffer so far
-      // ---- op. 2a: W = Z A_k (exponent GEMM)
-      bool ok = mbar_wait(su32(&bars[buf]), use & 1u);
-      if (!ok) atomicExch(sAbort, 1);
-      __syncthreads();
-      if (*sAbort) goto teardown;
+      // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
+      // GEMM of equation k+1 is issued now and runs under this epilogue
       if (tid == 0) {
-        tc_fence_after();
-        const uint32_t cb = su32(sm + (buf ? P.s_const1 : P.s_const0));
-        for (int s = 0; s < kx_steps; ++s) {
-          const uint64_t bd = smem_desc(cb + P.off_bexp + s * 256, 128, sbo_x);
-          mma_bf16(t_wre, smem_desc(su32(sAre) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
-          mma_bf16(t_wim, smem_desc(su32(sAim) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
-        }
-        mma_commit(su32(&bars[2]));
+        const bool ok1 = lookahead ? (k + 1 < n ? issue_exp(g + 1) : true) : issue_exp(g);
+        if (!ok1) atomicExch(sAbort, 1);
       }
-      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[2]), mma_phase));
-      mma_phase ^= 1;
+      bool ok = mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g));   // e of equation k visible
+      ok = __all_sync(0xffffffffu, ok && mbar_wait(su32(&bars[2 + (g & 1)]), (uint32_t)(g >> 1) & 1u));
       if (!ok) atomicExch(sAbort, 1);
       tc_fence_after();
       // ---- complex exponential, BF16 hi/lo split into the op. 2b A operand
       {
-        const float* texp = (const float*)(sm + (buf ? P.s_const1 : P.s_const0) + P.off_texp);
-        for (int c0 = 0; c0 < P.MP; c0 += 16) {
+        const float* texp = (const float*)(cbuf(g) + P.off_texp);
+        const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * P.MP) + lane_base;
+        for (int c0 = 16 * half; c0 < P.MP; c0 += 32) {
           uint32_t wre[16], wim[16];
-          tmem_ld16(t_wre + lane_base + c0, wre);
-          tmem_ld16(t_wim + lane_base + c0, wim);
+          tmem_ld16(tw + c0, wre);
+          tmem_ld16(tw + P.MP + c0, wim);
           tmem_wait_ld();
           uint32_t hr[8], hi_[8], lr[8], li[8];
 #pragma unroll
@@ -267,21 +280,24 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
               er[u] = m * cs;
               ei[u] = m * sn;
             }
-            const uint16_t h0 = bf16_rn(er[0]), h1 = bf16_rn(er[1]);
-            const uint16_t g0 = bf16_rn(ei[0]), g1 = bf16_rn(ei[1]);
-            hr[q / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
-            hi_[q / 2] = (uint32_t)g0 | ((uint32_t)g1 << 16);
-            lr[q / 2] = (uint32_t)bf16_rn(er[0] - bf16_f(h0)) | ((uint32_t)bf16_rn(er[1] - bf16_f(h1)) << 16);
-            li[q / 2] = (uint32_t)bf16_rn(ei[0] - bf16_f(g0)) | ((uint32_t)bf16_rn(ei[1] - bf16_f(g1)) << 16);
+            const __nv_bfloat162 hre = __floats2bfloat162_rn(er[0], er[1]);
+            const __nv_bfloat162 him = __floats2bfloat162_rn(ei[0], ei[1]);
+            const float2 fre = __bfloat1622float2(hre), fim = __bfloat1622float2(him);
+            const __nv_bfloat162 lre = __floats2bfloat162_rn(er[0] - fre.x, er[1] - fre.y);
+            const __nv_bfloat162 lim = __floats2bfloat162_rn(ei[0] - fim.x, ei[1] - fim.y);
+            hr[q / 2] = *(const uint32_t*)&hre;
+            hi_[q / 2] = *(const uint32_t*)&him;
+            lr[q / 2] = *(const uint32_t*)&lre;
+            li[q / 2] = *(const uint32_t*)&lim;
           }
           // Re E at K = c0.., Im E at K = MP + c0..; 16 values = two core columns
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int kre = c0 + 8 * h, kim = P.MP + c0 + 8 * h;
-            *(uint4*)(sAcHi + canon(tid, kre, P.KC)) = make_uint4(hr[4 * h], hr[4 * h + 1], hr[4 * h + 2], hr[4 * h + 3]);
-            *(uint4*)(sAcLo + canon(tid, kre, P.KC)) = make_uint4(lr[4 * h], lr[4 * h + 1], lr[4 * h + 2], lr[4 * h + 3]);
-            *(uint4*)(sAcHi + canon(tid, kim, P.KC)) = make_uint4(hi_[4 * h], hi_[4 * h + 1], hi_[4 * h + 2], hi_[4 * h + 3]);
-            *(uint4*)(sAcLo + canon(tid, kim, P.KC)) = make_uint4(li[4 * h], li[4 * h + 1], li[4 * h + 2], li[4 * h + 3]);
+            *(uint4*)(sAcHi + canon(row, kre, P.KC)) = make_uint4(hr[4 * h], hr[4 * h + 1], hr[4 * h + 2], hr[4 * h + 3]);
+            *(uint4*)(sAcLo + canon(row, kre, P.KC)) = make_uint4(lr[4 * h], lr[4 * h + 1], lr[4 * h + 2], lr[4 * h + 3]);
+            *(uint4*)(sAcHi + canon(row, kim, P.KC)) = make_uint4(hi_[4 * h], hi_[4 * h + 1], hi_[4 * h + 2], hi_[4 * h + 3]);
+            *(uint4*)(sAcLo + canon(row, kim, P.KC)) = make_uint4(li[4 * h], li[4 * h + 1], li[4 * h + 2], li[4 * h + 3]);
           }
         }
       }
@@ -292,7 +308,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       // ---- op. 2b: [D_z h | D_tau h | h] = E_k B_k^T, split passes
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t cb = su32(sm + (buf ? P.s_const1 : P.s_const0));
+        const uint32_t cb = su32(cbuf(g));
         for (int s = 0; s < kc_steps; ++s) {
           const uint64_t ah = smem_desc(su32(sAcHi) + s * 256, 128, sbo_c);
           const uint64_t al = smem_desc(su32(sAcLo) + s * 256, 128, sbo_c);
@@ -302,21 +318,20 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
           mma_bf16(t_j, ah, bl, idx_c, 1);
           mma_bf16(t_j, al, bh, idx_c, 1);
         }
-        mma_commit(su32(&bars[2]));
+        mma_commit(su32(&bars[4]));
       }
-      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[2]), mma_phase));
-      mma_phase ^= 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[4]), (uint32_t)g & 1u));
       if (!ok) atomicExch(sAbort, 1);
       tc_fence_after();
-      // both GEMMs of equation k are done: the constant buffer is free
+      // both GEMMs of equation k are done: its constant buffer is free
       if (tid == 0 && ok && g + P.nbuf < g_total) {
         proxy_fence();
-        bulk_load(su32(sm + (buf ? P.s_const1 : P.s_const0)), chunks + (size_t)((g + P.nbuf) % n) * P.chunk_bytes,
-                  P.chunk_bytes, su32(&bars[buf]));
+        bulk_load(su32(cbuf(g)), chunks + (size_t)((g + P.nbuf) % n) * P.chunk_bytes, P.chunk_bytes,
+                  su32(&bars[P.nbuf == 2 ? (g & 1) : 0]));
       }
-      // ---- op. 3: scale to y-coordinates and write row k
+      // ---- op. 3: scale to y-coordinates and write row k (column chunks split by half)
       if (ok) {
-        for (int c0 = 0; c0 < P.NJ; c0 += 16) {
+        for (int c0 = 16 * half; c0 < P.NJ; c0 += 32) {
           uint32_t jr[16];
           tmem_ld16(t_j + lane_base + c0, jr);
           tmem_wait_ld();
@@ -326,15 +341,15 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
             const int u = c0 / 2 + q;
             const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
             if (u < n) {
-              const float2 iy = sInvY[u * 128 + tid];
+              const float2 iy = sInvY[u * 128 + row];
               const float2 hy = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
-              if (ext) ext[((size_t)path * n + k) * (n + 2) + u] = hy;
+              if (ext) ext[ext_index(path, k, u, n)] = hy;
               if (oHy) oHy[((size_t)path * n + k) * n + u] = hy;
             } else if (u == n) {
-              if (ext) ext[((size_t)path * n + k) * (n + 2) + n] = v;
+              if (ext) ext[ext_index(path, k, n, n)] = v;
               if (oHt) oHt[(size_t)path * n + k] = make_float2(v.x * t_inv, v.y * t_inv);
             } else if (u == n + 1) {
-              if (ext) ext[((size_t)path * n + k) * (n + 2) + n + 1] = v;
+              if (ext) ext[ext_index(path, k, n + 1, n)] = v;
               if (oH) oH[(size_t)path * n + k] = v;
             }
           }
@@ -350,11 +365,10 @@ teardown:
   if (*sAbort) {
     if (tid == 0) {
       atomicExch(err, 1);
-      // let copies still in flight land before the CTA's shared memory goes away
-      for (int q = g; q < g + P.nbuf && q < g_total; ++q) {
-        const int b = P.nbuf == 2 ? (q & 1) : 0;
-        mbar_wait(su32(&bars[b]), (uint32_t)(P.nbuf == 2 ? (q >> 1) : q) & 1u);
-      }
+      // let copies and MMAs still in flight land before the CTA's resources go away
+      for (int q = g; q < g + P.nbuf && q < g_total; ++q) mbar_wait(su32(&bars[P.nbuf == 2 ? (q & 1) : 0]), cpar(q));
+      mbar_wait(su32(&bars[2 + (g & 1)]), (uint32_t)(g >> 1) & 1u);
+      mbar_wait(su32(&bars[2 + ((g + 1) & 1)]), (uint32_t)((g + 1) >> 1) & 1u);
     }
   }
   tc_fence_before();
@@ -399,7 +413,7 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
   a.s_const0 = take(L.chunk_bytes);
   const int off_single = off;
   a.s_const1 = take(L.chunk_bytes);
-  a.s_bar = take(64);
+  a.s_bar = take(128);
   int smem = off + 1024;   // slack for aligning the dynamic base
   a.inv_D = (float)(1.0 / (double)s->D);
   a.p = p;
@@ -422,7 +436,7 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
   if (smem > max_smem) {   // large shapes: one constant buffer, no prefetch
     off = off_single;
     a.s_const1 = a.s_const0;
-    a.s_bar = take(64);
+    a.s_bar = take(128);
     smem = off + 1024;
     a.nbuf = 1;
   }
@@ -434,7 +448,7 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
   int64_t grid = (int64_t)g_num_sms * per_sm;
   if (grid > ntiles) grid = ntiles;
   int pi = prof_begin(s, "eval_mixed_tc", st);
-  eval_mixed_kernel<<<(unsigned)grid, 128, smem, st>>>(a, (const float2*)y, tin, tau_is_t, s->d_chunks,
+  eval_mixed_kernel<<<(unsigned)grid, kEvalThreads, smem, st>>>(a, (const float2*)y, tin, tau_is_t, s->d_chunks,
                                                        (float2*)out.ext, (float2*)out.H, (float2*)out.Hy,
                                                        (float2*)out.Ht, s->d_err);
   prof_end(s, pi, st);

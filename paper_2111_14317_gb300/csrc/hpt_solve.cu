@@ -2,16 +2,18 @@
 // per-path step control, plus the small kernels around them (state init,
 // active count, Newton polish at t = 1, implicit-function adjoint).
 //
-// Solve mapping: a group of G lanes owns one path; lane r holds row r of
-// [H_y | H_tau | H] in registers.  Gaussian elimination with partial pivoting
-// (pivot = largest |.|^2, ties to the lowest row, as LAPACK's getrf) selects a
-// pivot lane per column with a butterfly arg-max, broadcasts the pivot row by
-// shuffles and eliminates the remaining rows in place; rows are never moved,
-// the column -> pivot-lane map is kept instead.  Back substitution runs
-// column-wise: the owner of column j divides, broadcasts x_j, and every row
-// pivoting an earlier column updates its right-hand side.  Two right-hand
-// sides [-H_tau, -H] give the Euler direction dE and the Newton direction dN
-// from one factorisation.
+// Solve mapping: a group of G lanes owns one path and every lane holds R rows
+// of [H_y | -H_tau | -H] in registers (rows lane, lane + G, ...), n <= G R.
+// The rows are equilibrated by exact powers of two, then Gaussian elimination
+// with partial pivoting runs over a run-time column loop.  Rows are "shifted":
+// after column j is eliminated every live row moves one register to the left,
+// so the current column is always register 0 and the loop body uses static
+// register indices only.  The pivot (largest |.|^2; ties to the lowest row, as
+// LAPACK's getrf) comes from one packed integer max per butterfly level; its
+// owner writes the pivot row, relative to column j, into row j of the group's
+// shared-memory factor U, from where every lane reads it.  Back substitution
+// works column by column on U.  Two right-hand sides [-H_tau, -H] give the
+// Euler direction dE and the Newton direction dN from one factorisation.
 #include <math.h>
 
 #include <algorithm>
@@ -34,17 +36,21 @@ __device__ __forceinline__ cx<T> mk(T a, T b) {
   return r;
 }
 template <typename T>
-__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-template <typename T>
 __device__ __forceinline__ cx<T> csub_mul(cx<T> acc, cx<T> a, cx<T> b) {  // acc - a b
   return mk<T>(acc.x - (a.x * b.x - a.y * b.y), acc.y - (a.x * b.y + a.y * b.x));
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) {
+  return mk<T>(a.x * s, a.y * s);
 }
 template <typename T>
 __device__ __forceinline__ cx<T> cdiv(cx<T> a, cx<T> b) {
   const T d = b.x * b.x + b.y * b.y;
   return mk<T>((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cmul_conj_scale(cx<T> a, cx<T> b, T r) {   // a conj(b) r
+  return mk<T>((a.x * b.x + a.y * b.y) * r, (a.y * b.x - a.x * b.y) * r);
 }
 template <typename T>
 __device__ __forceinline__ T abs2(cx<T> a) {
@@ -58,19 +64,6 @@ template <typename T, int G>
 __device__ __forceinline__ cx<T> shfl(cx<T> v, int src) {
   return mk<T>(__shfl_sync(0xffffffffu, v.x, src, G), __shfl_sync(0xffffffffu, v.y, src, G));
 }
-template <int G>
-__device__ __forceinline__ bool group_all(bool v) {
-  unsigned m = __ballot_sync(0xffffffffu, v);
-  const int lane = threadIdx.x & 31;
-  const unsigned seg = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  return (m & seg) == seg;
-}
-template <typename T, int G>
-__device__ __forceinline__ T group_max(T v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o, G));
-  return v;
-}
 
 __device__ __forceinline__ float t_hypot(float a, float b) { return hypotf(a, b); }
 __device__ __forceinline__ double t_hypot(double a, double b) { return hypot(a, b); }
@@ -80,153 +73,37 @@ __device__ __forceinline__ float t_min(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double t_min(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float t_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double t_sqrt(double a) { return sqrt(a); }
-// 2^-e for m in [2^(e-1), 2^e): an exact power-of-two scale bringing m to [1/2, 1)
+__device__ __forceinline__ float t_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double t_abs(double a) { return fabs(a); }
+// 2^-e for m in [2^(e-1), 2^e): an exact power-of-two scale bringing m to
+// [1/2, 1), read off the exponent field (1 for zero, subnormal, inf, NaN).
 __device__ __forceinline__ float pow2_inv(float m) {
-  int e;
-  frexpf(m, &e);
-  return (m > 0.f && isfinite(m)) ? ldexpf(1.f, -e) : 1.f;
+  const unsigned b = (__float_as_uint(m) >> 23) & 0xffu;
+  return (b == 0u || b == 0xffu) ? 1.f : __uint_as_float((253u - min(b, 252u)) << 23);
 }
 __device__ __forceinline__ double pow2_inv(double m) {
-  int e;
-  frexp(m, &e);
-  return (m > 0.0 && isfinite(m)) ? ldexp(1.0, -e) : 1.0;
+  const unsigned long long b = ((unsigned long long)__double_as_longlong(m) >> 52) & 0x7ffull;
+  return (b == 0ull || b == 0x7ffull) ? 1.0
+                                      : __longlong_as_double((long long)((2045ull - min(b, 2044ull)) << 52));
 }
-
 template <typename T>
 __device__ __forceinline__ T cabs_t(cx<T> a) {
   return t_hypot(a.x, a.y);
 }
 template <typename T>
 __device__ __forceinline__ T cmag(cx<T> a) {   // max(|re|, |im|): a cheap magnitude for scaling
-  return t_max(fabs(a.x), fabs(a.y));
+  return t_max(t_abs(a.x), t_abs(a.y));
 }
 
-// Entry j of a register row without dynamic indexing.
-template <typename T, int G>
-__device__ __forceinline__ cx<T> pick(const cx<T> (&a)[G], int j) {
-  cx<T> r = a[0];
-#pragma unroll
-  for (int c = 1; c < G; ++c)
-    if (c == j) r = a[c];
-  return r;
-}
-
-template <typename T, int G>
-__device__ __forceinline__ T pick_s(const T (&a)[G], int j) {
-  T r = a[0];
-#pragma unroll
-  for (int c = 1; c < G; ++c)
-    if (c == j) r = a[c];
-  return r;
-}
-
-// Pivot key: the magnitude |a_jj|^2 rounded to float with the low five
-// mantissa bits replaced by (31 - row), so that one integer max over the
-// group picks the largest magnitude, ties to the lowest row.  Rows already
-// used as pivots get key 0 and are never picked.
+// Pivot key: |a|^2 rounded to float with the low five mantissa bits replaced
+// by (31 - row), so that one integer max picks the largest magnitude, ties to
+// the lowest row.  Rows already used as pivots get key 0.
 template <typename T>
-__device__ __forceinline__ unsigned pivot_key(T v, bool used, int lane) {
+__device__ __forceinline__ unsigned pivot_key(T v, bool used, int row) {
   if (used) return 0u;
   float f = (float)v;
   if (!(f == f)) f = 0.f;   // NaN rows stay eligible; the pivot test flags them
-  return (__float_as_uint(f) & ~31u) | (unsigned)(31 - lane);
-}
-
-// Two-sided equilibration by exact powers of two: every row, then every
-// column of [a] is brought to magnitude [1/2, 1).  The solution of the scaled
-// system is x = diag(dcol) x'; pivots then reflect the matrix's conditioning
-// rather than the scales of y and t^s in its rows and columns.
-template <typename T, int G>
-__device__ __forceinline__ void equilibrate(cx<T> (&a)[G], cx<T>& rhsE, cx<T>& rhsN, T (&dcol)[G]) {
-  T m = T(0);
-#pragma unroll
-  for (int c = 0; c < G; ++c) m = t_max(m, cmag(a[c]));
-  const T dr = pow2_inv(m);
-#pragma unroll
-  for (int c = 0; c < G; ++c) a[c] = mk<T>(a[c].x * dr, a[c].y * dr);
-  rhsE = mk<T>(rhsE.x * dr, rhsE.y * dr);
-  rhsN = mk<T>(rhsN.x * dr, rhsN.y * dr);
-#pragma unroll
-  for (int c = 0; c < G; ++c) {
-    T mc = cmag(a[c]);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) mc = t_max(mc, __shfl_xor_sync(0xffffffffu, mc, o, G));
-    dcol[c] = pow2_inv(mc);
-    a[c] = mk<T>(a[c].x * dcol[c], a[c].y * dcol[c]);
-  }
-}
-
-// Solves rows [a | rhsE | rhsN] of an n x n system held one row per lane
-// (n <= G) with partial pivoting.  prow is this group's shared-memory pivot
-// row buffer (G + 2 entries, 16-byte aligned).  On return lane j (< n) holds
-// xE, xN = solution component j.  Returns false (group-uniform) when a pivot
-// is zero or not finite; cond receives max |u_jj| / min |u_jj|.
-template <typename T, int G>
-__device__ bool group_solve(int n, cx<T> (&a)[G], cx<T>& rhsE, cx<T>& rhsN, cx<T>& xE,
-                            cx<T>& xN, T& cond, cx<T>* prow) {
-  const int lane = threadIdx.x & (G - 1);
-  const int gbase = (threadIdx.x & 31) & ~(G - 1);
-  bool used = lane >= n;
-  int my_col = G;
-  bool ok = true;
-  T pmax = 0, pmin = 0;
-#pragma unroll 1
-  for (int j = 0; j < n; ++j) {
-    const cx<T> aj = pick<T, G>(a, j);
-    unsigned key = pivot_key<T>(abs2(aj), used, lane);
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o, G));
-    const int bl = 31 - (int)(key & 31u);
-    const bool was_used = used;
-    if (lane == bl) {
-#pragma unroll
-      for (int c = 0; c < G; ++c) prow[c] = a[c];
-      prow[G] = rhsE;
-      prow[G + 1] = rhsN;
-      used = true;
-      my_col = j;
-    }
-    __syncwarp();
-    const cx<T> pj = prow[j];
-    const T p2 = abs2(pj);
-    if (!(p2 > T(0)) || !isfinite(p2)) ok = false;
-    const T pa = t_sqrt(p2);
-    if (j == 0) { pmax = pa; pmin = pa; }
-    else { pmax = t_max(pmax, pa); pmin = t_min(pmin, pa); }
-    if (!was_used && lane != bl) {
-      const cx<T> l = cdiv(aj, pj);
-#pragma unroll
-      for (int c = 1; c < G; ++c)
-        if (c > j) a[c] = csub_mul(a[c], l, prow[c]);
-      rhsE = csub_mul(rhsE, l, prow[G]);
-      rhsN = csub_mul(rhsN, l, prow[G + 1]);
-    }
-    __syncwarp();
-  }
-  xE = mk<T>(0, 0);
-  xN = mk<T>(0, 0);
-#pragma unroll 1
-  for (int j = n - 1; j >= 0; --j) {
-    // the lane that pivoted column j
-    const unsigned b = __ballot_sync(0xffffffffu, my_col == j);
-    const unsigned seg = (G == 32) ? b : ((b >> gbase) & ((1u << G) - 1u));
-    const int owner = seg ? (__ffs(seg) - 1) : 0;
-    const cx<T> aj = pick<T, G>(a, j);
-    cx<T> ve = mk<T>(0, 0), vn = mk<T>(0, 0);
-    if (lane == owner) {
-      ve = cdiv(rhsE, aj);
-      vn = cdiv(rhsN, aj);
-    }
-    ve = shfl<T, G>(ve, owner);
-    vn = shfl<T, G>(vn, owner);
-    if (lane == j) { xE = ve; xN = vn; }
-    if (my_col < j) {
-      rhsE = csub_mul(rhsE, aj, ve);
-      rhsN = csub_mul(rhsN, aj, vn);
-    }
-  }
-  cond = pmin > T(0) ? pmax / pmin : T(INFINITY);
-  return ok;
+  return (__float_as_uint(f) & ~31u) | (unsigned)(31 - row);
 }
 
 template <typename T>
@@ -239,7 +116,6 @@ template <>
 struct cplx_t<float> {
   typedef float2 type;
 };
-
 template <typename T>
 __device__ __forceinline__ cx<T> ld(const void* base, size_t idx) {
   const typename cplx_t<T>::type v = ((const typename cplx_t<T>::type*)base)[idx];
@@ -253,65 +129,257 @@ __device__ __forceinline__ void st(void* base, size_t idx, cx<T> v) {
   ((typename cplx_t<T>::type*)base)[idx] = w;
 }
 
-// Loads row `lane` of path `path` from the extended Jacobian (T-precision
-// storage S) into the solve registers.
-template <typename T, typename S, int G>
-__device__ __forceinline__ void load_row(int n, const void* ext, int64_t path, bool valid, cx<T> (&a)[G],
-                                         cx<T>& rhsE, cx<T>& rhsN) {
-  const int lane = threadIdx.x & (G - 1);
-  const bool have = valid && lane < n;
-  const size_t base = ((size_t)path * n + lane) * (n + 2);
-#pragma unroll
-  for (int c = 0; c < G; ++c) {
-    a[c] = mk<T>(0, 0);
-    if (have && c < n) {
-      cx<S> v = ld<S>(ext, base + c);
-      a[c] = mk<T>((T)v.x, (T)v.y);
-    }
-  }
-  rhsE = mk<T>(0, 0);
-  rhsN = mk<T>(0, 0);
-  if (have) {
-    cx<S> ht = ld<S>(ext, base + n), h = ld<S>(ext, base + n + 1);
-    rhsE = mk<T>(-(T)ht.x, -(T)ht.y);
-    rhsN = mk<T>(-(T)h.x, -(T)h.y);
-  }
+// Shared memory of one group: U (NC rows of LD complex; LD even keeps rows
+// 16-byte aligned, LD - 1 odd keeps the column reads of the back substitution
+// on distinct banks) then the column scales (NC reals), padded so that
+// consecutive groups start 8 banks apart.
+template <typename T, int NC>
+struct GroupSmem {
+  static constexpr int LD = NC + 4;
+  static constexpr int raw_words = (NC * LD * 2 * (int)sizeof(T) + NC * (int)sizeof(T)) / 4;
+  static constexpr int words = (raw_words + 31) / 32 * 32 + 8;
+  static constexpr int bytes = words * 4;
+};
+
+constexpr int kSolveThreads = 128;
+
+// Rows of one path for a group: lane l holds rows l + G s, s < R, as
+// a[s][0..NC) plus the two right-hand sides.
+template <typename T, int G, int R>
+struct PathRows {
+  static constexpr int NC = G * R;
+  cx<T> a[R][NC];
+  cx<T> bE[R], bN[R];
+};
+
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+  return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
 }
 
-// Equilibrated solve of one path's [H_y | -H_tau | -H]; the solution is
-// returned unscaled.  Precision T, extended Jacobian stored in precision S.
-template <typename T, typename S, int G>
-__device__ __forceinline__ bool path_solve(int n, const void* ext, int64_t path, bool valid, cx<T>* prow,
-                                           cx<T>& xE, cx<T>& xN, T& cond) {
+// Loads the rows of [H_y | -H_tau | -H] (adjoint = false) or of
+// [J^H | g | 0] (adjoint = true, J = H_y, g from gx) for one path; returns
+// whether every entry is finite (group-uniform).
+template <typename T, typename S, int G, int R>
+__device__ __forceinline__ bool load_rows(int n, const void* ext, int64_t path, bool valid, bool adjoint,
+                                          const double2* gx, PathRows<T, G, R>& P) {
+  constexpr int NC = G * R;
   const int lane = threadIdx.x & (G - 1);
-  cx<T> a[G], rhsE, rhsN;
-  load_row<T, S, G>(n, ext, path, valid, a, rhsE, rhsN);
-  bool fin = true;
+  T chk = T(0);
 #pragma unroll
-  for (int c = 0; c < G; ++c) fin = fin && finite(a[c]);
-  fin = group_all<G>(fin && finite(rhsE) && finite(rhsN));
-  T dcol[G];
-  equilibrate<T, G>(a, rhsE, rhsN, dcol);
-  const bool ok = group_solve<T, G>(n, a, rhsE, rhsN, xE, xN, cond, prow) && fin;
-  const T dj = pick_s<T, G>(dcol, lane);
-  xE = mk<T>(xE.x * dj, xE.y * dj);
-  xN = mk<T>(xN.x * dj, xN.y * dj);
+  for (int s = 0; s < R; ++s) {
+    const int r = lane + G * s;
+    const bool have = valid && r < n;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      P.a[s][c] = mk<T>(0, 0);
+      if (have && c < n) {
+        cx<S> v = adjoint ? ld<S>(ext, ext_index(path, c, r, n)) : ld<S>(ext, ext_index(path, r, c, n));
+        P.a[s][c] = adjoint ? mk<T>((T)v.x, -(T)v.y) : mk<T>((T)v.x, (T)v.y);
+        chk += t_abs(P.a[s][c].x) + t_abs(P.a[s][c].y);
+      }
+    }
+    P.bE[s] = mk<T>(0, 0);
+    P.bN[s] = mk<T>(0, 0);
+    if (have) {
+      if (adjoint) {
+        const double2 g = gx[(size_t)path * n + r];
+        P.bE[s] = mk<T>((T)g.x, (T)g.y);
+      } else {
+        const cx<S> ht = ld<S>(ext, ext_index(path, r, n, n));
+        const cx<S> h = ld<S>(ext, ext_index(path, r, n + 1, n));
+        P.bE[s] = mk<T>(-(T)ht.x, -(T)ht.y);
+        P.bN[s] = mk<T>(-(T)h.x, -(T)h.y);
+      }
+      chk += t_abs(P.bE[s].x) + t_abs(P.bE[s].y) + t_abs(P.bN[s].x) + t_abs(P.bN[s].y);
+    }
+  }
+  // a sum of magnitudes is finite iff every entry is
+  const unsigned ball = __ballot_sync(0xffffffffu, isfinite(chk));
+  const unsigned seg = group_mask<G>();
+  return (ball & seg) == seg;
+}
+
+// Solves the path held in P (n <= G R) with equilibration and partial
+// pivoting.  Returns false (group-uniform) when a pivot is zero or not
+// finite; cond receives max |u_jj| / min |u_jj|.  On return lane l holds
+// solution components l + G s in xE[s], xN[s].  sm is the group's shared
+// memory (GroupSmem).
+template <typename T, int G, int R>
+__device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (&xE)[R], cx<T> (&xN)[R], T& cond,
+                            unsigned char* sm) {
+  constexpr int NC = G * R, LD = GroupSmem<T, NC>::LD;
+  cx<T>* U = (cx<T>*)sm;
+  T* dcol = (T*)(sm + NC * LD * sizeof(cx<T>));
+  const int lane = threadIdx.x & (G - 1);
+
+  // equilibration: rows, then columns, by exact powers of two
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    T m = T(0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) m = t_max(m, cmag(P.a[s][c]));
+    const T dr = pow2_inv(m);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) P.a[s][c] = cscale(P.a[s][c], dr);
+    P.bE[s] = cscale(P.bE[s], dr);
+    P.bN[s] = cscale(P.bN[s], dr);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (c < n) {
+      T m = T(0);
+#pragma unroll
+      for (int s = 0; s < R; ++s) m = t_max(m, cmag(P.a[s][c]));
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) m = t_max(m, __shfl_xor_sync(0xffffffffu, m, o, G));
+      const T d = pow2_inv(m);
+#pragma unroll
+      for (int s = 0; s < R; ++s) P.a[s][c] = cscale(P.a[s][c], d);
+      if (lane == 0) dcol[c] = d;
+    }
+  }
+
+  bool used[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) used[s] = lane + G * s >= n;
+  bool ok = true;
+  T pmax = 0, pmin = 0;
+#pragma unroll 1
+  for (int j = 0; j < n; ++j) {
+    unsigned key = 0u;
+#pragma unroll
+    for (int s = 0; s < R; ++s) key = max(key, pivot_key<T>(abs2(P.a[s][0]), used[s], lane + G * s));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o, G));
+    const int br = 31 - (int)(key & 31u);
+    if (lane == (br & (G - 1))) {
+      // the owner's slot chosen entry by entry (a per-slot conditional store
+      // would be turned into a dynamically indexed, local-memory row)
+      const int bs = br / G;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        cx<T> v = P.a[0][c];
+#pragma unroll
+        for (int s = 1; s < R; ++s) v = (bs == s) ? P.a[s][c] : v;
+        U[j * LD + c] = v;
+      }
+      cx<T> e = P.bE[0], f = P.bN[0];
+#pragma unroll
+      for (int s = 1; s < R; ++s) {
+        e = (bs == s) ? P.bE[s] : e;
+        f = (bs == s) ? P.bN[s] : f;
+      }
+      U[j * LD + NC] = e;
+      U[j * LD + NC + 1] = f;
+#pragma unroll
+      for (int s = 0; s < R; ++s) used[s] = used[s] || (bs == s);
+    }
+    __syncwarp();
+    const cx<T> pj = U[j * LD];
+    const T p2 = abs2(pj);
+    if (!(p2 > T(0)) || !isfinite(p2)) ok = false;
+    const T pa = t_sqrt(p2);
+    pmax = j == 0 ? pa : t_max(pmax, pa);
+    pmin = j == 0 ? pa : t_min(pmin, pa);
+    const T rp = T(1) / p2;   // one reciprocal per pivot, shared by all rows
+    // multipliers; rows already used get 0, so the unpredicated update below
+    // only shifts them (their values are no longer read)
+    cx<T> l[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) l[s] = used[s] ? mk<T>(0, 0) : cmul_conj_scale(P.a[s][0], pj, rp);
+    // shifted update: a[c-1] = a[c] - l u_{j, j+c} over the live width
+    const int lim = n - 1 - j;
+#pragma unroll
+    for (int c = 1; c < NC; ++c) {
+      if (c <= lim) {   // uniform over the group
+        const cx<T> u = U[j * LD + c];
+#pragma unroll
+        for (int s = 0; s < R; ++s) P.a[s][c - 1] = csub_mul(P.a[s][c], l[s], u);
+      }
+    }
+    const cx<T> uE = U[j * LD + NC], uN = U[j * LD + NC + 1];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      P.bE[s] = csub_mul(P.bE[s], l[s], uE);
+      P.bN[s] = csub_mul(P.bN[s], l[s], uN);
+    }
+  }
+  __syncwarp();
+  // back substitution on U (row i holds u_{i, i+c} at c, then the two
+  // right-hand sides); lane l carries the right-hand sides of rows l + G s
+  cx<T> rE[R], rN[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int i = lane + G * s;
+    rE[s] = i < n ? U[i * LD + NC] : mk<T>(0, 0);
+    rN[s] = i < n ? U[i * LD + NC + 1] : mk<T>(0, 0);
+    xE[s] = mk<T>(0, 0);
+    xN[s] = mk<T>(0, 0);
+  }
+#pragma unroll 1
+  for (int j = n - 1; j >= 0; --j) {
+    const cx<T> ujj = U[j * LD];
+    const int js = j / G;
+    cx<T> vE = rE[0], vN = rN[0];
+#pragma unroll
+    for (int s = 1; s < R; ++s)
+      if (s == js) { vE = rE[s]; vN = rN[s]; }
+    vE = shfl<T, G>(vE, j & (G - 1));
+    vN = shfl<T, G>(vN, j & (G - 1));
+    const T ru = T(1) / abs2(ujj);
+    const cx<T> xe = cmul_conj_scale(vE, ujj, ru), xn = cmul_conj_scale(vN, ujj, ru);
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const int i = lane + G * s;
+      if (i == j) { xE[s] = xe; xN[s] = xn; }
+      if (i < j) {
+        const cx<T> u = U[i * LD + (j - i)];
+        rE[s] = csub_mul(rE[s], u, xe);
+        rN[s] = csub_mul(rN[s], u, xn);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int i = lane + G * s;
+    if (i < n) {
+      const T d = dcol[i];
+      xE[s] = cscale(xE[s], d);
+      xN[s] = cscale(xN[s], d);
+    }
+  }
+  __syncwarp();   // the group's shared memory is reused by its next solve
+  cond = pmin > T(0) ? pmax / pmin : T(INFINITY);
   return ok;
 }
 
 // Step control of one path (all lanes of its group), given the directions:
-// accept/reject, then the next prediction.  TS is the state precision.
-template <typename TS, int G>
-__device__ __forceinline__ void update_path(int n, int64_t path, int32_t status, bool ok, cx<TS> xE,
-                                            cx<TS> xN, const hpt_paths& S, const hpt_params& prm) {
+// accept/reject, then the next prediction.  TS is the state precision; lane l
+// handles the variables l + G s.
+template <typename TS, int G, int R>
+__device__ __forceinline__ void update_path(int n, int64_t path, int32_t status, bool ok, const cx<TS> (&xE)[R],
+                                            const cx<TS> (&xN)[R], const hpt_paths& S, const hpt_params& prm) {
   const int lane = threadIdx.x & (G - 1);
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-  const bool mine = lane < n;
-  const size_t vi = (size_t)path * n + lane;
-  cx<TS> y = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
-  bool solfin = !mine || (finite(xE) && finite(xN));
+  const unsigned gmask = group_mask<G>();
+  cx<TS> y[R], yacc[R], dEacc[R];
+  bool solfin = true;
+  TS ny = TS(0), nd = TS(0);
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int j = lane + G * s;
+    const bool mine = j < n;
+    const size_t vi = (size_t)path * n + j;
+    y[s] = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
+    yacc[s] = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
+    dEacc[s] = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
+    if (mine) {
+      solfin = solfin && finite(xE[s]) && finite(xN[s]);
+      ny = t_max(ny, cabs_t(y[s]));
+      nd = t_max(nd, cabs_t(xN[s]));
+    }
+  }
   solfin = (__ballot_sync(gmask, solfin) & gmask) == gmask;
-  TS ny = mine ? cabs_t(y) : TS(0), nd = mine ? cabs_t(xN) : TS(0);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
     ny = t_max(ny, __shfl_xor_sync(gmask, ny, o, G));
@@ -323,12 +391,13 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
           streak = S.streak[path];
   const TS err = nd / t_max(TS(1), ny);
   const bool accept = !bad && err <= (TS)prm.tol_accept;
-  cx<TS> yacc = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
-  cx<TS> dEacc = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
   bool predict = true;
   if (accept) {
-    yacc = mk<TS>(y.x + xN.x, y.y + xN.y);
-    dEacc = xE;
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      yacc[s] = mk<TS>(y[s].x + xN[s].x, y[s].y + xN[s].y);
+      dEacc[s] = xE[s];
+    }
     tauacc = tau;
     accepts += 1;
     streak += 1;
@@ -336,8 +405,14 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
       status = HPT_PATH_CONVERGED;
       predict = false;
     } else {
-      const TS m = mine ? cabs_t(yacc) : TS(1);
-      bool div = mine && (!(m < (TS)prm.div_bound) || !(m > (TS)(1.0 / prm.div_bound)));
+      bool div = false;
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        if (lane + G * s < n) {
+          const TS m = cabs_t(yacc[s]);
+          div = div || !(m < (TS)prm.div_bound) || !(m > (TS)(1.0 / prm.div_bound));
+        }
+      }
       div = (__ballot_sync(gmask, div) & gmask) != 0u;
       if (div) {
         status = HPT_PATH_DIVERGED;
@@ -355,8 +430,11 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
       if (bad) {
         status = HPT_PATH_SINGULAR;
       } else {
-        y = mk<TS>(y.x + xN.x, y.y + xN.y);
-        yacc = y;
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+          y[s] = mk<TS>(y[s].x + xN[s].x, y[s].y + xN[s].y);
+          yacc[s] = y[s];
+        }
         if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
       }
     } else {
@@ -369,14 +447,20 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
   }
   if (predict) {
     const double h = fmin(dtau, -tauacc);
-    y = mk<TS>(yacc.x + (TS)h * dEacc.x, yacc.y + (TS)h * dEacc.y);
+#pragma unroll
+    for (int s = 0; s < R; ++s) y[s] = mk<TS>(yacc[s].x + (TS)h * dEacc[s].x, yacc[s].y + (TS)h * dEacc[s].y);
     tau = tauacc + h;
     if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
   }
-  if (mine) {
-    st<TS>(S.y, vi, y);
-    st<TS>(S.y_acc, vi, yacc);
-    st<TS>(S.dE_acc, vi, dEacc);
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int j = lane + G * s;
+    if (j < n) {
+      const size_t vi = (size_t)path * n + j;
+      st<TS>(S.y, vi, y[s]);
+      st<TS>(S.y_acc, vi, yacc[s]);
+      st<TS>(S.dE_acc, vi, dEacc[s]);
+    }
   }
   if (lane == 0) {
     S.tau[path] = tau;
@@ -394,142 +478,168 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
 // control.  T is the state and solve precision.  FP32 solves whose pivot
 // ratio (after equilibration) exceeds prm.cond_max are not applied here: the
 // path goes to redo_list and is solved again in FP64 by redo_fp64_kernel.
-template <typename T, int G>
-__global__ void __launch_bounds__(128)
+template <typename T, int G, int R>
+__global__ void __launch_bounds__(kSolveThreads)
 solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
                     int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (G - 1);
   const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   bool valid = path < p;
   const int32_t status = valid ? S.status[path] : -1;
   valid = valid && status == HPT_PATH_ACTIVE;
   if (!__any_sync(0xffffffffu, valid)) return;   // warp-uniform exit
-  __shared__ __align__(16) cx<T> prow_buf[128 / G][G + 2];
-  cx<T> xE, xN;
+  PathRows<T, G, R> P;
+  const bool fin = load_rows<T, T, G, R>(n, ext, path, valid, false, nullptr, P);
+  cx<T> xE[R], xN[R];
   T cond;
-  const bool ok = path_solve<T, T, G>(n, ext, path, valid, prow_buf[threadIdx.x / G], xE, xN, cond);
+  const bool ok =
+      group_solve<T, G, R>(n, P, xE, xN, cond, smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes) && fin;
   if (!valid) return;   // group-uniform; only group-masked shuffles below
   if (sizeof(T) == 4 && redo_list && ok && !(cond <= (T)prm.cond_max)) {
     if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = path;
     return;
   }
-  update_path<T, G>(n, path, status, ok, xE, xN, S, prm);
+  update_path<T, G, R>(n, path, status, ok, xE, xN, S, prm);
 }
 
 // FP64 re-solve of the paths listed by the FP32 kernel (same FP32 Jacobian,
 // FP64 factorisation), then their step control in the FP32 state.
-template <int G>
-__global__ void __launch_bounds__(128)
+template <int G, int R>
+__global__ void __launch_bounds__(kSolveThreads)
 redo_fp64_kernel(int n, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
                  const int32_t* __restrict__ redo_count, const int64_t* __restrict__ redo_list) {
-  __shared__ __align__(16) cx<double> prow_buf[128 / G][G + 2];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int count = *redo_count;
-  const int groups_per_warp = 32 / G;
+  constexpr int per_warp = 32 / G;
   const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
   const int g = (threadIdx.x & 31) / G;
-  for (int64_t base = warp_id * groups_per_warp; base < count; base += nwarps * groups_per_warp) {
+  unsigned char* sm = smem + (threadIdx.x / G) * GroupSmem<double, G * R>::bytes;
+  for (int64_t base = warp_id * per_warp; base < count; base += nwarps * per_warp) {
     const int64_t i = base + g;
     const bool valid = i < count;
     const int64_t path = valid ? redo_list[i] : 0;
-    cx<double> xE, xN;
+    PathRows<double, G, R> P;
+    const bool fin = load_rows<double, float, G, R>(n, ext, path, valid, false, nullptr, P);
+    cx<double> xE[R], xN[R];
     double cond;
-    const bool ok = path_solve<double, float, G>(n, ext, path, valid, prow_buf[threadIdx.x / G], xE, xN, cond);
-    if (valid)
-      update_path<float, G>(n, path, S.status[path], ok, mk<float>((float)xE.x, (float)xE.y),
-                            mk<float>((float)xN.x, (float)xN.y), S, prm);
+    const bool ok = group_solve<double, G, R>(n, P, xE, xN, cond, sm) && fin;
+    if (valid) {
+      cx<float> fE[R], fN[R];
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        fE[s] = mk<float>((float)xE[s].x, (float)xE[s].y);
+        fN[s] = mk<float>((float)xN[s].x, (float)xN[s].y);
+      }
+      update_path<float, G, R>(n, path, S.status[path], ok, fE, fN, S, prm);
+    }
     __syncwarp();
   }
 }
 
 // Newton polish update at t = 1 (FP64): x += dN until |dN|/max(1,|x|) <= tol.
-template <int G>
-__global__ void __launch_bounds__(128)
+template <int G, int R>
+__global__ void __launch_bounds__(kSolveThreads)
 newton_kernel(int n, int64_t p, const void* __restrict__ ext, double2* __restrict__ x,
               int32_t* __restrict__ done, double tol) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (G - 1);
   const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const bool valid = path < p && done[path] == 0;
   if (!__any_sync(0xffffffffu, valid)) return;
-  __shared__ __align__(16) cx<double> prow_buf[128 / G][G + 2];
-  cx<double> xE, xN;
+  PathRows<double, G, R> P;
+  const bool fin = load_rows<double, double, G, R>(n, ext, path, valid, false, nullptr, P);
+  cx<double> xE[R], xN[R];
   double cond;
-  bool ok = path_solve<double, double, G>(n, ext, path, valid, prow_buf[threadIdx.x / G], xE, xN, cond);
+  const bool ok =
+      group_solve<double, G, R>(n, P, xE, xN, cond, smem + (threadIdx.x / G) * GroupSmem<double, G * R>::bytes) &&
+      fin;
   if (!valid) return;
-  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-  const bool mine = lane < n;
-  const size_t vi = (size_t)path * n + lane;
-  cx<double> y = mine ? ld<double>(x, vi) : mk<double>(0, 0);
-  bool fin = !mine || finite(xN);
-  fin = (__ballot_sync(gmask, fin) & gmask) == gmask;
-  if (!(ok && fin)) {
+  const unsigned gmask = group_mask<G>();
+  bool sfin = true;
+  double ny = 0.0, nd = 0.0;
+  cx<double> y[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int j = lane + G * s;
+    y[s] = j < n ? ld<double>(x, (size_t)path * n + j) : mk<double>(0, 0);
+    if (j < n) {
+      sfin = sfin && finite(xN[s]);
+      y[s] = mk<double>(y[s].x + xN[s].x, y[s].y + xN[s].y);
+      ny = fmax(ny, cabs_t(y[s]));
+      nd = fmax(nd, cabs_t(xN[s]));
+    }
+  }
+  sfin = (__ballot_sync(gmask, sfin) & gmask) == gmask;
+  if (!(ok && sfin)) {
     if (lane == 0) done[path] = 2;
     return;
   }
-  y = mk<double>(y.x + xN.x, y.y + xN.y);
-  double ny = mine ? cabs_t(y) : 0.0, nd = mine ? cabs_t(xN) : 0.0;
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
     ny = fmax(ny, __shfl_xor_sync(gmask, ny, o, G));
     nd = fmax(nd, __shfl_xor_sync(gmask, nd, o, G));
   }
-  if (mine) st<double>(x, vi, y);
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int j = lane + G * s;
+    if (j < n) st<double>(x, (size_t)path * n + j, y[s]);
+  }
   if (lane == 0 && nd / fmax(1.0, ny) <= tol) done[path] = 1;
 }
 
 // Adjoint, part 1: per solution, lambda from J^H lambda = gx (J from the
 // extended Jacobian at t = 1), then contrib[q][i] = -lambda_k conj(x^{a_i})
 // for every monomial i of equation k (monomials by exp of <a, log x>).
-template <int G>
-__global__ void __launch_bounds__(128)
+template <int G, int R>
+__global__ void __launch_bounds__(kSolveThreads)
 adjoint_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t* __restrict__ off,
                const double* __restrict__ ahat, int M, const void* __restrict__ ext,
                const double2* __restrict__ x, const double2* __restrict__ gx,
                double2* __restrict__ contrib) {
-  __shared__ double2 zsh[128 / G][G];
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double2 zsh[kSolveThreads / G][G * R];
   const int lane = threadIdx.x & (G - 1);
   const int grp = threadIdx.x / G;
   const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const bool valid = path < p;
-  cx<double> a[G], rE, rN, lam, dummy;
-  const bool have = valid && lane < n;
-  // row `lane` of J^H = conj of column `lane` of J
-#pragma unroll
-  for (int c = 0; c < G; ++c) {
-    a[c] = mk<double>(0, 0);
-    if (have && c < n) {
-      cx<double> v = ld<double>(ext, ((size_t)path * n + c) * (n + 2) + lane);
-      a[c] = mk<double>(v.x, -v.y);
-    }
-  }
-  rE = have ? ld<double>(gx, (size_t)path * n + lane) : mk<double>(0, 0);
-  rN = mk<double>(0, 0);
+  PathRows<double, G, R> P;
+  const bool fin = load_rows<double, double, G, R>(n, ext, path, valid, true, gx, P);
+  cx<double> lam[R], dummy[R];
   double cond;
-  __shared__ __align__(16) cx<double> prow_buf[128 / G][G + 2];
-  bool ok = group_solve<double, G>(n, a, rE, rN, lam, dummy, cond, prow_buf[threadIdx.x / G]);
-  if (have) {
-    const double2 v = x[(size_t)path * n + lane];
-    zsh[grp][lane] = make_double2(log(hypot(v.x, v.y)), atan2(v.y, v.x));
-  }
-  __syncwarp();
-  __syncthreads();
-  if (!have) return;
-  const int k = lane;
-  for (int i = off[k]; i < off[k] + msz[k]; ++i) {
-    const double* ai = ahat + (size_t)i * (n + 1);
-    double wr = 0.0, wi = 0.0;
-    for (int j = 0; j < n; ++j) {
-      wr = fma(ai[j], zsh[grp][j].x, wr);
-      wi = fma(ai[j], zsh[grp][j].y, wi);
+  const bool ok =
+      group_solve<double, G, R>(n, P, lam, dummy, cond, smem + grp * GroupSmem<double, G * R>::bytes) && fin;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int j = lane + G * s;
+    if (valid && j < n) {
+      const double2 v = x[(size_t)path * n + j];
+      zsh[grp][j] = make_double2(log(hypot(v.x, v.y)), atan2(v.y, v.x));
     }
-    double sn, cs;
-    sincos(wi, &sn, &cs);
-    const double m = exp(wr);
-    // -lambda_k * conj(m (cs + i sn))
-    const double mr = m * cs, mi = -m * sn;
-    double2 v = make_double2(-(lam.x * mr - lam.y * mi), -(lam.x * mi + lam.y * mr));
-    if (!ok) v = make_double2(NAN, NAN);
-    contrib[(size_t)path * M + i] = v;
+  }
+  __syncthreads();
+  if (!valid) return;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int k = lane + G * s;
+    if (k >= n) continue;
+    for (int i = off[k]; i < off[k] + msz[k]; ++i) {
+      const double* ai = ahat + (size_t)i * (n + 1);
+      double wr = 0.0, wi = 0.0;
+      for (int j = 0; j < n; ++j) {
+        wr = fma(ai[j], zsh[grp][j].x, wr);
+        wi = fma(ai[j], zsh[grp][j].y, wi);
+      }
+      double sn, cs;
+      sincos(wi, &sn, &cs);
+      const double m = exp(wr);
+      // -lambda_k * conj(m (cs + i sn))
+      const double mr = m * cs, mi = -m * sn;
+      double2 v = make_double2(-(lam[s].x * mr - lam[s].y * mi), -(lam[s].x * mi + lam[s].y * mr));
+      if (!ok) v = make_double2(NAN, NAN);
+      contrib[(size_t)path * M + i] = v;
+    }
   }
 }
 
@@ -605,67 +715,112 @@ __global__ void init_done_kernel(int64_t p, const int32_t* __restrict__ status, 
 
 inline unsigned blocks_for(int64_t threads, int bs) { return (unsigned)((threads + bs - 1) / bs); }
 
+// Lane-group shape for n: (G, R) = (8, 1) for n <= 8, (8, 2) for n <= 16,
+// (32, 1) for n <= 32.
+inline int shape_of(int n) { return n <= 8 ? 0 : (n <= 16 ? 1 : 2); }
+
+template <typename K>
+cudaError_t set_smem(K kernel, int bytes) {
+  return bytes > 48 * 1024 ? cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                           : cudaSuccess;
+}
+
+template <typename T, int G, int R>
+cudaError_t launch_solve_shape(const StepArgs& a, int32_t* rc, int64_t* rl, cudaStream_t st) {
+  const int smem = (kSolveThreads / G) * GroupSmem<T, G * R>::bytes;
+  cudaError_t e = set_smem(solve_update_kernel<T, G, R>, smem);
+  if (e != cudaSuccess) return e;
+  solve_update_kernel<T, G, R><<<blocks_for(a.p * G, kSolveThreads), kSolveThreads, smem, st>>>(
+      a.n, a.p, a.ext, a.st, a.prm, rc, rl);
+  return cudaGetLastError();
+}
+
+template <int G, int R>
+cudaError_t launch_redo_shape(const StepArgs& a, cudaStream_t st) {
+  const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
+  cudaError_t e = set_smem(redo_fp64_kernel<G, R>, smem);
+  if (e != cudaSuccess) return e;
+  const unsigned nb = blocks_for(std::min<int64_t>(a.p, 8192) * G, kSolveThreads);
+  redo_fp64_kernel<G, R><<<nb, kSolveThreads, smem, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  return cudaGetLastError();
+}
+
+template <int G, int R>
+cudaError_t launch_newton_shape(int n, int64_t p, const void* ext, void* x, int32_t* done, double tol,
+                                cudaStream_t st) {
+  const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
+  cudaError_t e = set_smem(newton_kernel<G, R>, smem);
+  if (e != cudaSuccess) return e;
+  newton_kernel<G, R><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(n, p, ext, (double2*)x,
+                                                                                      done, tol);
+  return cudaGetLastError();
+}
+
+template <int G, int R>
+cudaError_t launch_adjoint_shape(hpt_system s, int64_t p, const void* ext, const void* x, const void* gx,
+                                 void* contrib, cudaStream_t st) {
+  const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
+  cudaError_t e = set_smem(adjoint_kernel<G, R>, smem);
+  if (e != cudaSuccess) return e;
+  adjoint_kernel<G, R><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(
+      s->n, p, s->d_msz, s->d_off, s->d_ahat, s->M, ext, (const double2*)x, (const double2*)gx,
+      (double2*)contrib);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st) {
   if (a.p <= 0) return cudaSuccess;
-  const bool dbl = s->prec == HPT_FP64;
-  const int G = a.n <= 8 ? 8 : (a.n <= 16 ? 16 : 32);
-  const unsigned nb = blocks_for(a.p * G, 128);
-  if (dbl) {
+  const int shape = shape_of(a.n);
+  cudaError_t e;
+  if (s->prec == HPT_FP64) {
     int pi = prof_begin(s, "solve_update_fp64", st);
-    if (G == 8) solve_update_kernel<double, 8><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr, nullptr);
-    else if (G == 16) solve_update_kernel<double, 16><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr, nullptr);
-    else solve_update_kernel<double, 32><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, nullptr, nullptr);
+    e = shape == 0 ? launch_solve_shape<double, 8, 1>(a, nullptr, nullptr, st)
+      : shape == 1 ? launch_solve_shape<double, 8, 2>(a, nullptr, nullptr, st)
+                   : launch_solve_shape<double, 32, 1>(a, nullptr, nullptr, st);
     prof_end(s, pi, st);
-    return cudaGetLastError();
+    return e;
   }
-  cudaError_t e = cudaMemsetAsync(a.redo_count, 0, sizeof(int32_t), st);
+  e = cudaMemsetAsync(a.redo_count, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   int pi = prof_begin(s, "solve_update_fp32", st);
-  if (G == 8) solve_update_kernel<float, 8><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
-  else if (G == 16) solve_update_kernel<float, 16><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
-  else solve_update_kernel<float, 32><<<nb, 128, 0, st>>>(a.n, a.p, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  e = shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
+    : shape == 1 ? launch_solve_shape<float, 8, 2>(a, a.redo_count, a.redo_list, st)
+                 : launch_solve_shape<float, 32, 1>(a, a.redo_count, a.redo_list, st);
   prof_end(s, pi, st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (e != cudaSuccess) return e;
   // FP64 re-solves: a fixed grid that loops over the device-side list
-  unsigned rb = blocks_for(std::min<int64_t>(a.p, 8192) * G, 128);
   pi = prof_begin(s, "redo_fp64", st);
-  if (G == 8) redo_fp64_kernel<8><<<rb, 128, 0, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
-  else if (G == 16) redo_fp64_kernel<16><<<rb, 128, 0, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
-  else redo_fp64_kernel<32><<<rb, 128, 0, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  e = shape == 0 ? launch_redo_shape<8, 1>(a, st)
+    : shape == 1 ? launch_redo_shape<8, 2>(a, st)
+                 : launch_redo_shape<32, 1>(a, st);
   prof_end(s, pi, st);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void* x, int32_t* done,
                                  double tol, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
-  const int G = s->n <= 8 ? 8 : (s->n <= 16 ? 16 : 32);
-  const unsigned nb = blocks_for(p * G, 128);
+  const int shape = shape_of(s->n);
   int pi = prof_begin(s, "newton_fp64", st);
-  if (G == 8) newton_kernel<8><<<nb, 128, 0, st>>>(s->n, p, ext, (double2*)x, done, tol);
-  else if (G == 16) newton_kernel<16><<<nb, 128, 0, st>>>(s->n, p, ext, (double2*)x, done, tol);
-  else newton_kernel<32><<<nb, 128, 0, st>>>(s->n, p, ext, (double2*)x, done, tol);
+  cudaError_t e = shape == 0 ? launch_newton_shape<8, 1>(s->n, p, ext, x, done, tol, st)
+                : shape == 1 ? launch_newton_shape<8, 2>(s->n, p, ext, x, done, tol, st)
+                             : launch_newton_shape<32, 1>(s->n, p, ext, x, done, tol, st);
   prof_end(s, pi, st);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void* x, const void* gx,
                            void* partial, int64_t nblk, void* gc, cudaStream_t st) {
   (void)nblk;
   if (p <= 0) return cudaSuccess;
-  const int G = s->n <= 8 ? 8 : (s->n <= 16 ? 16 : 32);
-  const unsigned nb = blocks_for(p * G, 128);
+  const int shape = shape_of(s->n);
   int pi = prof_begin(s, "adjoint_fp64", st);
-  if (G == 8)
-    adjoint_kernel<8><<<nb, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, s->M, ext, (const double2*)x, (const double2*)gx, (double2*)partial);
-  else if (G == 16)
-    adjoint_kernel<16><<<nb, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, s->M, ext, (const double2*)x, (const double2*)gx, (double2*)partial);
-  else
-    adjoint_kernel<32><<<nb, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, s->M, ext, (const double2*)x, (const double2*)gx, (double2*)partial);
+  cudaError_t e = shape == 0 ? launch_adjoint_shape<8, 1>(s, p, ext, x, gx, partial, st)
+                : shape == 1 ? launch_adjoint_shape<8, 2>(s, p, ext, x, gx, partial, st)
+                             : launch_adjoint_shape<32, 1>(s, p, ext, x, gx, partial, st);
   prof_end(s, pi, st);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   pi = prof_begin(s, "adjoint_sum", st);
   sum_columns_kernel<<<blocks_for(s->M, 128), 128, 0, st>>>(p, s->M, (const double2*)partial, (double2*)gc);

@@ -60,9 +60,11 @@ extern "C" hpt_status hpt_step_static(hpt_system s, int64_t p, const hpt_paths* 
   if (!prm || !S || p < 0 || nsteps < 0) { set_error("bad params, state, p or nsteps"); return HPT_EINVAL; }
   const int n = s->n;
   const size_t cs = s->prec == HPT_FP64 ? 16 : 8;
-  // layout: [re-solve counter, 256 B][re-solve list, p int64][extended Jacobian]
+  // layout: [re-solve counter, 256 B][re-solve list, p int64][extended
+  // Jacobian of ceil(p/128)*128 paths]; max_p bounds 511 + 8p + (p+127) B
   const size_t per_path = (size_t)n * (n + 2) * cs + sizeof(int64_t);
-  const int64_t max_p = (int64_t)((kStaticScratchBytes - 512) / per_path);
+  const size_t jac = (size_t)n * (n + 2) * cs;
+  const int64_t max_p = (int64_t)((kStaticScratchBytes - 511 - 127 * jac) / per_path);
   if (p > max_p) {
     set_error("hpt_step_static: p=%lld exceeds the static scratch limit of %lld paths for n=%d "
               "(%zu bytes per path in %zu bytes)", (long long)p, (long long)max_p, n, per_path,

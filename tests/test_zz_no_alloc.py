@@ -58,8 +58,8 @@ def test_static_step_rejects_oversized_batch(hpt):
     s = W.config2(1)
     cl, _ = cells.mixed_cells(s)
     h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": cl[0]["pairs"]}, 0)
-    per_path = 4 * 6 * 16 + 8
-    limit = ((32 << 20) - 512) // per_path
+    jac = 4 * 6 * 16
+    limit = ((32 << 20) - 511 - 127 * jac) // (jac + 8)
     st = hpt.PathState(limit + 1, 4, 0)       # a real state of the refused size
     with pytest.raises(hpt.HptError) as err:
         h.step_static(st, 1)
