@@ -250,21 +250,29 @@ def diagonalize(V):
 def binomial_solutions(V, b, limit=None):
     """All solutions y in (C*)^n of prod_j y_j^{V[k][j]} = b_k, k = 0..n-1.
 
-    With U V W = diag(d): zeta = W^{-1} log y satisfies
-    d_j zeta_j = (U log b)_j + 2 pi i m_j, m_j = 0..|d_j|-1, and log y =
-    W zeta.  There are |det V| solutions.
+    With U V W = diag(d) (U, W unimodular), V^{-1} = W diag(1/d) U, and the
+    solutions are log y = V^{-1} log b + 2 pi i W diag(1/d) m for
+    m_j = 0..|d_j|-1: |det V| of them.  The first term comes from a linear
+    solve with V itself (numpy.linalg.solve); the rational vector
+    W diag(1/d) m is reduced modulo 1 exactly (integers), since only its
+    fractional part changes y.  (Forming W zeta in floating point instead
+    cancels badly when W has large entries.)
     """
     n = len(V)
     U, d, W = diagonalize(V)
     logb = np.log(np.asarray(b, dtype=np.complex128))
-    Ulogb = np.array(U, dtype=np.float64) @ logb
-    Wm = np.array(W, dtype=np.float64)
+    z0 = np.linalg.solve(np.array(V, dtype=np.float64), logb)
+    L = 1
+    for dj in d:
+        L = _lcm(L, abs(int(dj)))
     sols = []
     for m in itertools.product(*[range(abs(dj)) for dj in d]):
         if limit is not None and len(sols) >= limit:
             break
-        zeta = np.array([(Ulogb[j] + 2j * np.pi * m[j]) / d[j] for j in range(n)])
-        sols.append(np.exp(Wm @ zeta))
+        # numerators over L of (W diag(1/d) m)_r, reduced mod L
+        num = [sum(int(W[r][j]) * int(m[j]) * (L // int(d[j])) for j in range(n)) % L for r in range(n)]
+        frac = np.array([v / L for v in num])
+        sols.append(np.exp(z0 + 2j * np.pi * frac))
     return np.array(sols, dtype=np.complex128).reshape(len(sols), n)
 
 

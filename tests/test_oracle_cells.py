@@ -166,3 +166,20 @@ def test_start_points_solve_the_cell_system(oracle_mod):
         H, _, _ = osys.eval(y0, np.full(len(y0), -1e4))
         SH, _, _ = osys.scale(y0, np.full(len(y0), -1e4))
         assert np.max(np.abs(H) / SH) < 1e-13
+
+
+def test_start_points_large_determinant():
+    """A planted n=8 cell with |det V| ~ 1e5, whose unimodular factors have
+    entries ~1e8: the start points still solve y^V = b to rounding level."""
+    import _util
+    s, pairs, _, d = _util.planted_case(W.config5, 4096)
+    V = np.array(cells.pair_matrix(s, pairs))
+    off = s.offsets
+    b = np.array([-s.coeffs[off[k] + pairs[k][0]] / s.coeffs[off[k] + pairs[k][1]] for k in range(s.n)])
+    y = cells.start_points(s, pairs, limit=2000)
+    res = np.abs(np.prod(y[:, None, :] ** V[None, :, :], axis=2) / b[None, :] - 1).max()
+    assert res < 1e-12
+    # distinct points
+    dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
+    np.fill_diagonal(dd, np.inf)
+    assert dd.min() > 1e-8
