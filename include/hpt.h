@@ -162,6 +162,32 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* support_sizes, const int
                               const int64_t* lifting, const hpt_cell* cell, int64_t* texp,
                               int64_t* denom, int64_t* alpha_num, int64_t* beta_num);
 
+/* Host-only start points of a cell of kind PAIRS: the solutions in (C*)^n of
+ * the binomial start system H(y, t=0) = 0, i.e. c_{k,p0} y^{a_{k,p0}} +
+ * c_{k,p1} y^{a_{k,p1}} = 0 (Section 2 leaves this step to Huber and
+ * Sturmfels).  With V_k = a_{k,p1} - a_{k,p0}, b_k = -c_{k,p0}/c_{k,p1} and an
+ * integer diagonal form U V W = diag(d) (U, W unimodular), the |det V|
+ * solutions are y = exp(W zeta), zeta_j = ((U log b)_j + 2 pi i m_j) / d_j,
+ * m_j = 0..|d_j|-1.  Writes solutions first..first+count-1 (mixed-radix order
+ * of m, last coordinate fastest) to y0[count*n] complex128 (interleaved) and
+ * |det V| to *total (may be NULL).  HPT_ENOTCELL for a singular pair matrix,
+ * HPT_ERANGE on integer overflow or a range beyond |det V|. */
+hpt_status hpt_binomial_start(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
+                              const double* coeffs, const int32_t* pairs, int64_t first, int64_t count,
+                              double* y0, int64_t* total);
+
+/* Host-only start points of a PAIRS cell for chosen lattice vectors: for each
+ * k (kvec[count*n] int64, row q = k of solution q) writes y = exp(z) with
+ * V z = log b + 2 pi i k (log b principal, V and b as in hpt_binomial_start)
+ * to y0[count*n] complex128.  Every solution of the start system is of this
+ * form; k and k' give the same solution exactly when k - k' lies in V Z^n.
+ * Floating-point (FP64 LU with partial pivoting), so it serves any |det V|,
+ * where hpt_binomial_start's exact enumeration needs |det V| < 2^62.
+ * HPT_ENOTCELL for a singular pair matrix. */
+hpt_status hpt_binomial_points(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
+                               const double* coeffs, const int32_t* pairs, int64_t count, const int64_t* kvec,
+                               double* y0);
+
 /* Algorithm 1 (Initialize): exact bookkeeping as hpt_lift_exponents, then one
  * upload of the constants (A with the t-exponent row, B_k for every k, and for
  * HPT_MIXED their split-BF16 operand images) to the current device.
@@ -252,6 +278,61 @@ hpt_status hpt_device_error(hpt_system sys);
 hpt_status hpt_profile_enable(hpt_system sys, int32_t enable);
 hpt_status hpt_profile_read(hpt_system sys, int32_t cap, const char** names, int64_t* launches,
                             double* ms, int32_t* count);
+
+/* ---- Batching form: many systems of different sizes in one tracker ----
+ *
+ * Problem (d) of Section 1 asks for parallelism at several levels; Section 5
+ * batches the points of one system.  A batch goes one level up: the paths of
+ * many HPT_MIXED systems (n may differ) advance together.  Every step is one
+ * launch of the mixed evaluation kernel over all live paths of all systems
+ * (each 128-path tile belongs to one system and reads that system's
+ * constants), one FP32 solve launch per lane-group shape (n <= 8, <= 16,
+ * <= 32) and one FP64 re-solve launch.  After every round of K steps the live
+ * paths are compacted on the device (finished paths leave the launches) and
+ * the position count comes back to the host, which stops when it is 0.  A
+ * round (K steps + compaction + count read-back) is a captured CUDA graph,
+ * replayed.  Converged paths get the FP64 polish of hpt_track per system.
+ */
+typedef struct hpt_batch_s* hpt_batch;
+
+typedef struct {
+  int32_t steps_per_round;    /* K: steps between compactions (1..256) */
+  int32_t eval_ctas_per_sm;   /* resident evaluation CTAs per SM: 1 or 2 (capped by tensor memory) */
+} hpt_batch_tuning;
+
+/* Groups nsys (>= 1) HPT_MIXED system handles of the current device (their
+ * constant images are copied; the handles must outlive the batch, whose
+ * polish uses them).  Default tuning: K = 16, 2 CTAs/SM where they fit.
+ * HPT_ENOTSUP if a handle is HPT_FP64. */
+hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* out);
+hpt_status hpt_batch_destroy(hpt_batch b);
+hpt_status hpt_batch_get_tuning(hpt_batch b, hpt_batch_tuning* t);
+hpt_status hpt_batch_set_tuning(hpt_batch b, const hpt_batch_tuning* t);
+
+/* Tracks paths[s] (host array, >= 0) paths of every system s from t = 0 to
+ * t = 1 and polishes the converged ones, as hpt_track does for one system.
+ * y0: device complex128 start points, system 0's paths[0] x n_0 values, then
+ * system 1's, ... (concatenated, path-major).  x_out: device complex128 in
+ * the same layout; status_out, steps_out: device int32 per path in the same
+ * order (either may be NULL).  The batch owns its state and scratch (grown
+ * on demand, kept for the next call).  Work is ordered after earlier work on
+ * `stream`; returns after it is done. */
+hpt_status hpt_batch_track(hpt_batch b, const int64_t* paths, const void* y0, const hpt_params* prm,
+                           void* x_out, int32_t* status_out, int32_t* steps_out, void* stream);
+
+/* The project's autotuner: runs hpt_batch_track once per candidate tuning
+ * (K in {4, 8, 16, 32} x eval CTAs/SM in {1, 2} where 2 fits) on the given
+ * problem and keeps the fastest as the batch's tuning.  Writes the chosen
+ * tuning to *best, and, where not NULL, each candidate's tuning and
+ * milliseconds to cand[] / ms[] (capacity *ncand in, count out). */
+hpt_status hpt_batch_autotune(hpt_batch b, const int64_t* paths, const void* y0, const hpt_params* prm,
+                              void* x_out, void* stream, hpt_batch_tuning* best, hpt_batch_tuning* cand,
+                              double* ms, int32_t* ncand);
+
+/* Counters of the last hpt_batch_track: rounds (graph replays), positions
+ * evaluated summed over steps (live paths + tile padding), and the number of
+ * kernels one round launches. */
+hpt_status hpt_batch_stats(hpt_batch b, int64_t* rounds, int64_t* position_steps, int32_t* kernels_per_round);
 
 #ifdef __cplusplus
 }

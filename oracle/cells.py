@@ -287,6 +287,31 @@ def start_points(sysm, pairs, limit=None):
     return binomial_solutions(V, b, limit)
 
 
+def binomial_points(V, b, ks):
+    """The solutions log y = V^{-1} (log b + 2 pi i k) of the binomial system
+    prod_j y_j^{V[k][j]} = b_k for the integer vectors k (rows of ks): every
+    solution has this form, and k, k' give the same y exactly when k - k' is
+    in V Z^n.  A plain linear solve per k (numpy.linalg.solve), usable at any
+    |det V|."""
+    Vf = np.array(V, dtype=np.float64)
+    logb = np.log(np.asarray(b, dtype=np.complex128))
+    ks = np.asarray(ks, dtype=np.int64).reshape(-1, len(V))
+    out = np.empty(ks.shape, dtype=np.complex128)
+    for i, k in enumerate(ks):
+        out[i] = np.exp(np.linalg.solve(Vf, logb + 2j * np.pi * k))
+    return out
+
+
+def start_points_at(sysm, pairs, ks):
+    """Start points of the cell's binomial start system for chosen lattice
+    vectors k (see binomial_points)."""
+    off = sysm.offsets
+    V = pair_matrix(sysm, pairs)
+    b = [-sysm.coeffs[off[k] + int(pairs[k][0])] / sysm.coeffs[off[k] + int(pairs[k][1])]
+         for k in range(sysm.n)]
+    return binomial_points(V, b, ks)
+
+
 def tau0(e, D, eps0=1e-10):
     """tau0 = ln(eps0) / s_min, s_min = min over e > 0 of e / D."""
     pos = [v for v in e if v > 0]

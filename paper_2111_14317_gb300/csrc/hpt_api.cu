@@ -16,23 +16,6 @@ constexpr int64_t kChunk = 65536;
 
 inline size_t csize(const hpt_system s) { return s->prec == HPT_FP64 ? 16 : 8; }
 
-hpt_status cuda_fail(cudaError_t e, const char* what) {
-  set_error("%s: %s", what, cudaGetErrorString(e));
-  return e == cudaErrorMemoryAllocation ? HPT_ENOMEM : HPT_ECUDA;
-}
-
-hpt_status check_params(const hpt_params* prm) {
-  if (!prm) { set_error("params is NULL"); return HPT_EINVAL; }
-  if (!(prm->tol_accept > 0) || !(prm->dtau_init > 0) || !(prm->dtau_min > 0) ||
-      !(prm->dtau_max >= prm->dtau_min) || !(prm->grow >= 1) || !(prm->shrink > 0 && prm->shrink < 1) ||
-      prm->grow_after < 1 || prm->max_steps < 1 || !(prm->div_bound > 1) || !(prm->polish_tol > 0) ||
-      prm->polish_iters < 0) {
-    set_error("params out of range");
-    return HPT_EINVAL;
-  }
-  return HPT_OK;
-}
-
 hpt_paths offset_paths(const hpt_paths& S, int64_t q0, int n, size_t cs) {
   hpt_paths o = S;
   o.y = (char*)S.y + q0 * n * cs;
@@ -91,24 +74,50 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
 
 hpt_status polish_impl(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm,
                        cudaStream_t st) {
-  const int n = s->n;
   const int64_t chunk = std::min<int64_t>(p, kChunk);
-  hpt_status rc = ensure_scratch(s, ext_entries(chunk, n) * 16);
+  hpt_status rc = ensure_scratch(s, ext_entries(chunk, s->n) * 16);
   if (rc) return rc;
+  return polish_paths(s, p, x, done, prm, s->d_scratch, chunk, st);
+}
+
+}  // namespace
+
+hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm, void* ext,
+                        int64_t chunk, cudaStream_t st) {
+  const int n = s->n;
   for (int it = 0; it < prm.polish_iters; ++it) {
     for (int64_t q0 = 0; q0 < p; q0 += chunk) {
       const int64_t cnt = std::min(chunk, p - q0);
       EvalOut out;
-      out.ext = s->d_scratch;
+      out.ext = ext;
       void* xq = (char*)x + q0 * n * 16;
       cudaError_t e = launch_eval_fp64(s, cnt, xq, nullptr, 0, out, st);
       if (e != cudaSuccess) return cuda_fail(e, "polish evaluation launch");
-      e = launch_newton_update(s, cnt, s->d_scratch, xq, done + q0, prm.polish_tol, st);
+      e = launch_newton_update(s, cnt, ext, xq, done + q0, prm.polish_tol, st);
       if (e != cudaSuccess) return cuda_fail(e, "polish update launch");
     }
   }
   return HPT_OK;
 }
+
+hpt_status check_params(const hpt_params* prm) {
+  if (!prm) { set_error("params is NULL"); return HPT_EINVAL; }
+  if (!(prm->tol_accept > 0) || !(prm->dtau_init > 0) || !(prm->dtau_min > 0) ||
+      !(prm->dtau_max >= prm->dtau_min) || !(prm->grow >= 1) || !(prm->shrink > 0 && prm->shrink < 1) ||
+      prm->grow_after < 1 || prm->max_steps < 1 || !(prm->div_bound > 1) || !(prm->polish_tol > 0) ||
+      prm->polish_iters < 0) {
+    set_error("params out of range");
+    return HPT_EINVAL;
+  }
+  return HPT_OK;
+}
+
+hpt_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? HPT_ENOMEM : HPT_ECUDA;
+}
+
+namespace {
 
 hpt_status check_sys(hpt_system s) {
   if (!s) { set_error("NULL handle"); return HPT_EINVAL; }

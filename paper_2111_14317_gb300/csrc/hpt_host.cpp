@@ -70,6 +70,84 @@ static bool rdiv(const Rat& a, const Rat& b, Rat& out) {
   return rmul(a, inv, out);
 }
 
+// ------------------------------------------------------------ modular determinant
+// Exact nonsingularity test of an integer matrix: det V is computed modulo
+// primes below 2^62 until their product exceeds Hadamard's bound prod_k
+// |row_k|_2 >= |det V|; then det V = 0 exactly when every residue is 0.
+typedef unsigned __int128 u128;
+
+static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
+static uint64_t powmod(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1;
+  for (a %= p; e; e >>= 1, a = mulmod(a, a, p))
+    if (e & 1) r = mulmod(r, a, p);
+  return r;
+}
+// Miller-Rabin with the first twelve primes as bases: exact below 3.3e24.
+static bool is_prime64(uint64_t n) {
+  static const uint64_t bases[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (n < 2) return false;
+  for (uint64_t b : bases)
+    if (n % b == 0) return n == b;
+  uint64_t d = n - 1;
+  int r = 0;
+  while (!(d & 1)) { d >>= 1; ++r; }
+  for (uint64_t b : bases) {
+    uint64_t x = powmod(b, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool comp = true;
+    for (int i = 1; i < r && comp; ++i) {
+      x = mulmod(x, x, n);
+      if (x == n - 1) comp = false;
+    }
+    if (comp) return false;
+  }
+  return true;
+}
+static uint64_t det_mod(int n, const std::vector<int64_t>& V, uint64_t p) {
+  std::vector<uint64_t> A((size_t)n * n);
+  for (int i = 0; i < n * n; ++i) {
+    const int64_t v = V[i] % (int64_t)p;
+    A[i] = (uint64_t)(v < 0 ? v + (int64_t)p : v);
+  }
+  uint64_t det = 1;
+  for (int j = 0; j < n; ++j) {
+    int piv = -1;
+    for (int i = j; i < n && piv < 0; ++i)
+      if (A[i * n + j]) piv = i;
+    if (piv < 0) return 0;
+    if (piv != j) {
+      for (int c = 0; c < n; ++c) std::swap(A[piv * n + c], A[j * n + c]);
+      det = (p - det) % p;
+    }
+    det = mulmod(det, A[j * n + j], p);
+    const uint64_t inv = powmod(A[j * n + j], p - 2, p);
+    for (int i = j + 1; i < n; ++i) {
+      const uint64_t f = mulmod(A[i * n + j], inv, p);
+      if (!f) continue;
+      for (int c = j; c < n; ++c) A[i * n + c] = (A[i * n + c] + p - mulmod(f, A[j * n + c], p)) % p;
+    }
+  }
+  return det;
+}
+// HPT_OK (nonsingular), HPT_ENOTCELL (singular).
+static hpt_status nonsingular_exact(int n, const std::vector<int64_t>& V) {
+  double log2_bound = 1.0;
+  for (int k = 0; k < n; ++k) {
+    double r2 = 0;
+    for (int j = 0; j < n; ++j) r2 += (double)V[k * n + j] * (double)V[k * n + j];
+    if (r2 == 0) return HPT_ENOTCELL;
+    log2_bound += 0.5 * log2(r2);
+  }
+  double covered = 0;
+  for (uint64_t cand = ((uint64_t)1 << 62) - 1; covered <= log2_bound; cand -= 2) {
+    if (!is_prime64(cand)) continue;
+    if (det_mod(n, V, cand) != 0) return HPT_OK;
+    covered += log2((double)cand);
+  }
+  return HPT_ENOTCELL;
+}
+
 // Solves V x = rhs exactly (Gauss-Jordan over the rationals).  Returns
 // HPT_OK, HPT_ENOTCELL (singular) or HPT_ERANGE.
 static hpt_status solve_exact(int n, const std::vector<int64_t>& V, const std::vector<int64_t>& rhs,
@@ -152,7 +230,16 @@ static hpt_status lift(int32_t n, const int32_t* msz, const int32_t* exps, const
       rhs[k] = lifting[off[k] + p0[k]] - lifting[off[k] + p1[k]];
     }
     std::vector<Rat> alpha;
-    rc = solve_exact(n, V, rhs, alpha);
+    bool zero_rhs = true;
+    for (int k = 0; k < n; ++k) zero_rhs = zero_rhs && rhs[k] == 0;
+    if (zero_rhs) {
+      // equal lifting values on every pair: the inner normal is 0 whatever
+      // the size of V, and only its nonsingularity needs checking
+      rc = nonsingular_exact(n, V);
+      alpha.assign(n, Rat());
+    } else {
+      rc = solve_exact(n, V, rhs, alpha);
+    }
     if (rc == HPT_ENOTCELL) { set_error("pair matrix is singular"); return rc; }
     if (rc) { set_error("overflow solving for alpha"); return rc; }
     i128 D = 1;
@@ -317,6 +404,234 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* msz, const int32_t* exps
   if (denom) *denom = L.D;
   if (alpha_num) memcpy(alpha_num, L.alpha.data(), n * sizeof(int64_t));
   if (beta_num) memcpy(beta_num, L.beta.data(), n * sizeof(int64_t));
+  return HPT_OK;
+}
+
+hpt_status hpt_binomial_start(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,
+                               const int32_t* pairs, int64_t first, int64_t count, double* y0,
+                               int64_t* total) {
+  int32_t M;
+  hpt_status rc = check_shape(n, msz, &M);
+  if (rc) return rc;
+  if (!exps || !coeffs || !pairs || first < 0 || count < 0 || (count > 0 && !y0)) {
+    set_error("bad arguments");
+    return HPT_EINVAL;
+  }
+  std::vector<int32_t> off(n);
+  for (int k = 0, acc = 0; k < n; ++k) { off[k] = acc; acc += msz[k]; }
+  // V_k = a_{k,p1} - a_{k,p0};  b_k = -c_{k,p0} / c_{k,p1}
+  std::vector<i128> A((size_t)n * n), U((size_t)n * n, 0), W((size_t)n * n, 0);
+  std::vector<double> br(n), bi(n);
+  for (int k = 0; k < n; ++k) {
+    const int p0 = pairs[2 * k], p1 = pairs[2 * k + 1];
+    if (p0 < 0 || p1 < 0 || p0 >= msz[k] || p1 >= msz[k] || p0 == p1) { set_error("bad pair"); return HPT_EINVAL; }
+    for (int j = 0; j < n; ++j)
+      A[k * n + j] = (i128)exps[(size_t)(off[k] + p1) * n + j] - exps[(size_t)(off[k] + p0) * n + j];
+    const double c0r = coeffs[2 * (off[k] + p0)], c0i = coeffs[2 * (off[k] + p0) + 1];
+    const double c1r = coeffs[2 * (off[k] + p1)], c1i = coeffs[2 * (off[k] + p1) + 1];
+    const double d = c1r * c1r + c1i * c1i;
+    if (!(d > 0)) { set_error("zero coefficient in the cell"); return HPT_EINVAL; }
+    br[k] = -(c0r * c1r + c0i * c1i) / d;
+    bi[k] = -(c0i * c1r - c0r * c1i) / d;
+    U[k * n + k] = 1;
+    W[k * n + k] = 1;
+  }
+  // integer diagonal form U V W = diag(dd): repeated pivot-and-reduce with
+  // the smallest nonzero entry of the trailing block as pivot
+  auto big = [](i128 v) { return v >= kLim || v <= -kLim; };
+  for (int t = 0; t < n; ++t) {
+    for (int guard = 0;; ++guard) {
+      if (guard > 100000) { set_error("diagonal form did not converge"); return HPT_ERANGE; }
+      int pi = -1, pj = -1;
+      i128 best = 0;
+      for (int i = t; i < n; ++i)
+        for (int j = t; j < n; ++j) {
+          const i128 v = iabs(A[i * n + j]);
+          if (v != 0 && (pi < 0 || v < best)) { best = v; pi = i; pj = j; }
+        }
+      if (pi < 0) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
+      if (pi != t)
+        for (int c = 0; c < n; ++c) { std::swap(A[pi * n + c], A[t * n + c]); std::swap(U[pi * n + c], U[t * n + c]); }
+      if (pj != t)
+        for (int r = 0; r < n; ++r) { std::swap(A[r * n + pj], A[r * n + t]); std::swap(W[r * n + pj], W[r * n + t]); }
+      bool done = true;
+      const i128 piv = A[t * n + t];
+      for (int i = t + 1; i < n; ++i) {
+        const i128 q = A[i * n + t] / piv;
+        if (q)
+          for (int c = 0; c < n; ++c) {
+            A[i * n + c] -= q * A[t * n + c];
+            U[i * n + c] -= q * U[t * n + c];
+            if (big(A[i * n + c]) || big(U[i * n + c])) { set_error("overflow in the diagonal form"); return HPT_ERANGE; }
+          }
+        if (A[i * n + t] != 0) done = false;
+      }
+      for (int j = t + 1; j < n; ++j) {
+        const i128 q = A[t * n + j] / piv;
+        if (q)
+          for (int r = 0; r < n; ++r) {
+            A[r * n + j] -= q * A[r * n + t];
+            W[r * n + j] -= q * W[r * n + t];
+            if (big(A[r * n + j]) || big(W[r * n + j])) { set_error("overflow in the diagonal form"); return HPT_ERANGE; }
+          }
+        if (A[t * n + j] != 0) done = false;
+      }
+      if (done) break;
+    }
+  }
+  std::vector<int64_t> dd(n);
+  i128 tot = 1;
+  for (int j = 0; j < n; ++j) {
+    dd[j] = (int64_t)iabs(A[j * n + j]);
+    tot *= dd[j];
+    if (tot >= kLim) { set_error("too many start solutions"); return HPT_ERANGE; }
+  }
+  if (total) *total = (int64_t)tot;
+  if (first + count > (int64_t)tot) { set_error("solutions %lld..%lld requested of %lld", (long long)first, (long long)(first + count), (long long)tot); return HPT_ERANGE; }
+  // log y = V^{-1} log b + 2 pi i W diag(1/d) m: the first term by Gaussian
+  // elimination with partial pivoting on the original V; the second is a
+  // rational vector, reduced modulo 1 exactly (only its fractional part
+  // changes y), because forming W zeta in floating point cancels badly when
+  // the unimodular W has large entries.
+  std::vector<double> Vd((size_t)n * n), zr0(n), zi0(n);
+  for (int k = 0; k < n; ++k) {
+    for (int j = 0; j < n; ++j)
+      Vd[k * n + j] = (double)exps[(size_t)(off[k] + pairs[2 * k + 1]) * n + j] -
+                      (double)exps[(size_t)(off[k] + pairs[2 * k]) * n + j];
+    zr0[k] = 0.5 * log(br[k] * br[k] + bi[k] * bi[k]);
+    zi0[k] = atan2(bi[k], br[k]);
+  }
+  for (int j = 0; j < n; ++j) {
+    int piv = j;
+    for (int i = j + 1; i < n; ++i)
+      if (fabs(Vd[i * n + j]) > fabs(Vd[piv * n + j])) piv = i;
+    if (Vd[piv * n + j] == 0.0) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
+    if (piv != j) {
+      for (int c = 0; c < n; ++c) std::swap(Vd[piv * n + c], Vd[j * n + c]);
+      std::swap(zr0[piv], zr0[j]);
+      std::swap(zi0[piv], zi0[j]);
+    }
+    for (int i = j + 1; i < n; ++i) {
+      const double f = Vd[i * n + j] / Vd[j * n + j];
+      for (int c = j; c < n; ++c) Vd[i * n + c] -= f * Vd[j * n + c];
+      zr0[i] -= f * zr0[j];
+      zi0[i] -= f * zi0[j];
+    }
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    double sr = zr0[j], si = zi0[j];
+    for (int c = j + 1; c < n; ++c) { sr -= Vd[j * n + c] * zr0[c]; si -= Vd[j * n + c] * zi0[c]; }
+    zr0[j] = sr / Vd[j * n + j];
+    zi0[j] = si / Vd[j * n + j];
+  }
+  i128 L = 1;
+  for (int j = 0; j < n; ++j) {
+    const i128 g = igcd(L, dd[j]);
+    L = L / g * dd[j];
+    if (L >= kLim) { set_error("common denominator overflow"); return HPT_ERANGE; }
+  }
+  // W entries reduced mod L keep the products below 2^126
+  std::vector<i128> Wm((size_t)n * n);
+  for (int i = 0; i < n * n; ++i) Wm[i] = ((W[i] % L) + L) % L;
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<int64_t> m(n);
+  for (int64_t q = 0; q < count; ++q) {
+    int64_t idx = first + q;   // mixed radix, last coordinate fastest
+    for (int j = n - 1; j >= 0; --j) { m[j] = idx % dd[j]; idx /= dd[j]; }
+    for (int r = 0; r < n; ++r) {
+      i128 num = 0;
+      for (int j = 0; j < n; ++j) {
+        if (!m[j]) continue;
+        // sign of d_j: W diag(1/d) uses the signed pivot
+        const i128 dj = A[j * n + j];
+        const i128 scale = L / (dj < 0 ? -dj : dj);
+        i128 t = (Wm[r * n + j] * (i128)m[j]) % L;
+        t = (t * scale) % L;
+        if (dj < 0) t = (L - t) % L;
+        num = (num + t) % L;
+      }
+      const double frac = (double)num / (double)L;
+      const double mag = exp(zr0[r]);
+      const double ang = zi0[r] + two_pi * frac;
+      y0[(q * n + r) * 2] = mag * cos(ang);
+      y0[(q * n + r) * 2 + 1] = mag * sin(ang);
+    }
+  }
+  return HPT_OK;
+}
+
+hpt_status hpt_binomial_points(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,
+                                const int32_t* pairs, int64_t count, const int64_t* kvec, double* y0) {
+  int32_t M;
+  hpt_status rc = check_shape(n, msz, &M);
+  if (rc) return rc;
+  if (!exps || !coeffs || !pairs || count < 0 || (count > 0 && (!kvec || !y0))) {
+    set_error("bad arguments");
+    return HPT_EINVAL;
+  }
+  std::vector<int32_t> off(n);
+  for (int k = 0, acc = 0; k < n; ++k) { off[k] = acc; acc += msz[k]; }
+  // V_k = a_{k,p1} - a_{k,p0}, log b_k (principal) with b_k = -c_{k,p0}/c_{k,p1}
+  std::vector<double> V((size_t)n * n), lr(n), li(n);
+  double vmax = 0;
+  for (int k = 0; k < n; ++k) {
+    const int p0 = pairs[2 * k], p1 = pairs[2 * k + 1];
+    if (p0 < 0 || p1 < 0 || p0 >= msz[k] || p1 >= msz[k] || p0 == p1) { set_error("bad pair"); return HPT_EINVAL; }
+    for (int j = 0; j < n; ++j) {
+      V[k * n + j] = (double)exps[(size_t)(off[k] + p1) * n + j] - (double)exps[(size_t)(off[k] + p0) * n + j];
+      vmax = std::max(vmax, fabs(V[k * n + j]));
+    }
+    const double c0r = coeffs[2 * (off[k] + p0)], c0i = coeffs[2 * (off[k] + p0) + 1];
+    const double c1r = coeffs[2 * (off[k] + p1)], c1i = coeffs[2 * (off[k] + p1) + 1];
+    const double d = c1r * c1r + c1i * c1i;
+    if (!(d > 0)) { set_error("zero coefficient in the cell"); return HPT_EINVAL; }
+    const double br = -(c0r * c1r + c0i * c1i) / d, bi = -(c0i * c1r - c0r * c1i) / d;
+    lr[k] = 0.5 * log(br * br + bi * bi);
+    li[k] = atan2(bi, br);
+  }
+  // LU with partial pivoting of V (kept for every right-hand side)
+  std::vector<int> perm(n);
+  for (int j = 0; j < n; ++j) perm[j] = j;
+  for (int j = 0; j < n; ++j) {
+    int piv = j;
+    for (int i = j + 1; i < n; ++i)
+      if (fabs(V[i * n + j]) > fabs(V[piv * n + j])) piv = i;
+    if (!(fabs(V[piv * n + j]) > 1e-9 * vmax)) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
+    if (piv != j) {
+      for (int c = 0; c < n; ++c) std::swap(V[piv * n + c], V[j * n + c]);
+      std::swap(perm[piv], perm[j]);
+    }
+    for (int i = j + 1; i < n; ++i) {
+      const double f = V[i * n + j] / V[j * n + j];
+      V[i * n + j] = f;
+      for (int c = j + 1; c < n; ++c) V[i * n + c] -= f * V[j * n + c];
+    }
+  }
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> zr(n), zi(n);
+  for (int64_t q = 0; q < count; ++q) {
+    const int64_t* kq = kvec + q * n;
+    for (int j = 0; j < n; ++j) {
+      zr[j] = lr[perm[j]];
+      zi[j] = li[perm[j]] + two_pi * (double)kq[perm[j]];
+    }
+    for (int j = 0; j < n; ++j)
+      for (int i = j + 1; i < n; ++i) {
+        zr[i] -= V[i * n + j] * zr[j];
+        zi[i] -= V[i * n + j] * zi[j];
+      }
+    for (int j = n - 1; j >= 0; --j) {
+      double sr = zr[j], si = zi[j];
+      for (int c = j + 1; c < n; ++c) { sr -= V[j * n + c] * zr[c]; si -= V[j * n + c] * zi[c]; }
+      zr[j] = sr / V[j * n + j];
+      zi[j] = si / V[j * n + j];
+    }
+    for (int r = 0; r < n; ++r) {
+      const double mag = exp(zr[r]);
+      y0[(q * n + r) * 2] = mag * cos(zi[r]);
+      y0[(q * n + r) * 2 + 1] = mag * sin(zi[r]);
+    }
+  }
   return HPT_OK;
 }
 
@@ -585,7 +900,7 @@ static cudaEvent_t pool_event(hpt_system s) {
 }
 
 int prof_begin(hpt_system s, const char* name, cudaStream_t st) {
-  if (!s->profiling) return -1;
+  if (!s || !s->profiling) return -1;
   int idx = -1;
   for (size_t i = 0; i < s->stats.size(); ++i)
     if (s->stats[i].name == name) idx = (int)i;

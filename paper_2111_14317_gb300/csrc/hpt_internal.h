@@ -33,6 +33,17 @@ struct MixedLayout {
   int smem_bytes = 0;    // dynamic shared memory of the eval kernel
 };
 
+// One system's operand shapes as the mixed evaluation kernel reads them
+// (from its launch arguments for a single system, from a device table per
+// tile for many systems).
+struct MixedSys {
+  int n, MP, KX, NJ, KC;
+  int chunk_bytes, off_bexp, off_bhi, off_blo, off_texp;
+  float inv_D;
+  int pad_;
+  int64_t chunk_off;   // byte offset of the system's constant images
+};
+
 // Byte offset of element (r, k) of an R x K bf16 operand in the canonical
 // K-major no-swizzle layout used by the tensor-core descriptors: 8-row x
 // 16-byte core matrices, K-adjacent cores 128 bytes apart (leading byte
@@ -50,6 +61,24 @@ __host__ __device__ inline size_t ext_index(int64_t path, int k, int u, int n) {
          (size_t)(path & 127);
 }
 inline size_t ext_entries(int64_t p, int n) { return (size_t)((p + 127) / 128) * 128 * n * (n + 2); }
+
+// Positions of a launch and the paths behind them.  With every pointer null a
+// launch covers one system: position q is path q, every path has n
+// variables.  A many-systems launch walks a list of positions padded per
+// system to whole 128-position tiles (entry -1 = padding), so every tile
+// belongs to one system; tile_sys gives it, sys_n its size, vofs the offset of
+// a path's first variable in the concatenated state.  The extended Jacobian
+// scratch is indexed by position with the bucket's largest n (nmax).
+struct PathMap {
+  const int64_t* list = nullptr;
+  const int32_t* tile_sys = nullptr;
+  const int32_t* sys_n = nullptr;
+  const int64_t* vofs = nullptr;
+  const int32_t* npos = nullptr;   // device-side position count (null: the host count)
+  int nmax = 0;
+  const int32_t* pos_begin = nullptr;   // device-side first position (null: 0); a multiple of 128
+  const struct MixedSys* sys_tab = nullptr;   // mixed evaluation: per-system operand shapes
+};
 
 struct KernelStat {
   std::string name;
@@ -127,10 +156,22 @@ cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const doubl
 // Mixed tensor-core evaluation, complex64 in and out.
 cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const double* tau,
                               int tau_is_t, const EvalOut& out, cudaStream_t st);
+// The same over a position map of many systems: pm.sys_tab describes each
+// system, chunks holds every system's constant images, maxs the largest of
+// each operand dimension (it sizes shared memory; maxs.n = pm.nmax) and
+// tmem_cols the largest tensor-memory need.  p bounds the positions;
+// ctas_per_sm 0 picks the default.  Writes the extended Jacobian only.
+cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tmem_cols, const uint8_t* chunks,
+                                  int64_t p, const void* y, const double* tau, const PathMap& pm, void* ext,
+                                  int32_t* err, int ctas_per_sm, cudaStream_t st);
+// Resident eval CTAs per SM the tensor memory allows for tmem_cols (1 or 2).
+int eval_mixed_max_ctas(int tmem_cols);
+MixedSys mixed_sys_of(const hpt_system s);
 
 struct StepArgs {
   int n;
-  int64_t p;
+  int64_t p;                       // positions (an upper bound when map.npos is set)
+  PathMap map;
   const void* ext;           // extended Jacobian of every path
   hpt_paths st;
   hpt_params prm;
@@ -142,6 +183,13 @@ struct StepArgs {
 // Consolidated solve + update + step control.  T = double for HPT_FP64,
 // float for HPT_MIXED.
 cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st);
+// Many-systems pieces of the mixed step: the FP32 solve of one lane-group
+// shape (shape_of(n)) over the map's position range, appending FP64
+// re-solves to a.redo_list (the caller zeroes a.redo_count once per step),
+// and the FP64 re-solve of the whole list with a shape that covers a.map.nmax.
+int solve_shape_of(int n);
+cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st);
+cudaError_t launch_redo_fp64_shape(int shape, const StepArgs& a, cudaStream_t st);
 
 // Newton update at t = 1 for the polish: x += dN where the relative
 // correction is still above tol; done[q] set once it is below.
@@ -153,6 +201,14 @@ cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void*
 cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void* x,
                            const void* gx, void* partial, int64_t nblk, void* gc,
                            cudaStream_t st);
+
+// FP64 Newton polish at t = 1 of p solutions x (complex128) whose done flag
+// is 0, polish_iters rounds over chunks of `chunk` paths; ext holds the
+// extended Jacobian of a chunk (FP64).
+hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm, void* ext,
+                        int64_t chunk, cudaStream_t st);
+hpt_status check_params(const hpt_params* prm);
+hpt_status cuda_fail(cudaError_t e, const char* what);
 
 // State init / conversion helpers.
 cudaError_t launch_paths_init(hpt_system s, int64_t p, const void* y0, double tau0,

@@ -27,19 +27,19 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "hpt_internal.h"
 
 namespace hpt {
 namespace {
 
 struct MixedArgs {
-  int n, MP, KX, NJ, KC;
-  int chunk_bytes, off_bexp, off_bhi, off_blo, off_texp;
+  MixedSys sys;   // the system of a single-system launch
   int tmem_cols;
   int nbuf;   // constant-image buffers: 2 (prefetch next equation) or 1
   // shared-memory carve-up (bytes from the 1024-aligned base)
   int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_bar;
-  float inv_D;
   int64_t p;
   int ntiles;
 };
@@ -145,7 +145,7 @@ constexpr int kEvalThreads = 256;   // two warpgroups over the 128 TMEM lanes
 __global__ void __launch_bounds__(kEvalThreads, 2)
 eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
                   const uint8_t* __restrict__ chunks, float2* __restrict__ ext, float2* __restrict__ oH,
-                  float2* __restrict__ oHy, float2* __restrict__ oHt, int32_t* __restrict__ err) {
+                  float2* __restrict__ oHy, float2* __restrict__ oHt, int32_t* __restrict__ err, PathMap pm) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sAre = sm + P.s_are;
@@ -160,11 +160,14 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & 127;          // point of the tile = TMEM lane
   const int half = tid >> 7;          // warpgroup: splits the column chunks
-  const int n = P.n;
-  const int my_tiles = (P.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int ntiles = pm.npos ? (*pm.npos + 127) / 128 : P.ntiles;
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   if (my_tiles <= 0) return;
-  const int g_total = my_tiles * n;
   const bool lookahead = P.nbuf == 2;
+  const int nmax = pm.nmax ? pm.nmax : P.sys.n;
+  // work items are (tile, equation) pairs; a tile's system fixes the shapes
+  auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
+  auto sys_of = [&](int tile) { return pm.tile_sys ? pm.tile_sys[tile] : 0; };
 
   if (tid == 0) {
     for (int i = 0; i < 5; ++i) mbar_init(su32(&bars[i]), 1);
@@ -180,48 +183,63 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  const uint32_t t_j = tbase + 4 * P.MP;
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 
   auto cbuf = [&](int g) -> uint8_t* { return sm + ((P.nbuf == 2 && (g & 1)) ? P.s_const1 : P.s_const0); };
   auto cpar = [&](int g) -> uint32_t { return (uint32_t)(P.nbuf == 2 ? (g >> 1) : g) & 1u; };
-  const uint32_t idx_x = idesc_bf16(128, P.MP), idx_c = idesc_bf16(128, P.NJ);
-  const int kx_steps = P.KX / 16, kc_steps = P.KC / 16;
-  const uint32_t sbo_x = P.KX * 16, sbo_c = P.KC * 16;
 
-  // exponent GEMM of work item g (equation g % n) into W[g & 1]; thread 0 only
-  auto issue_exp = [&](int g) -> bool {
+  // exponent GEMM of work item g (an equation of system S) into W[g & 1];
+  // thread 0 only
+  auto issue_exp = [&](int g, const MixedSys& S) -> bool {
     if (!mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g))) return false;
     tc_fence_after();
     const uint32_t cb = su32(cbuf(g));
-    const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * P.MP);
-    for (int s = 0; s < kx_steps; ++s) {
-      const uint64_t bd = smem_desc(cb + P.off_bexp + s * 256, 128, sbo_x);
+    const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * S.MP);
+    const uint32_t idx_x = idesc_bf16(128, S.MP), sbo_x = S.KX * 16;
+    for (int s = 0; s < S.KX / 16; ++s) {
+      const uint64_t bd = smem_desc(cb + S.off_bexp + s * 256, 128, sbo_x);
       mma_bf16(tw, smem_desc(su32(sAre) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
-      mma_bf16(tw + P.MP, smem_desc(su32(sAim) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
+      mma_bf16(tw + S.MP, smem_desc(su32(sAim) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
     }
     mma_commit(su32(&bars[2 + (g & 1)]));
     return true;
   };
 
-  // constant images for the first nbuf work items
-  if (tid == 0) {
-    for (int g = 0; g < P.nbuf && g < g_total; ++g)
-      bulk_load(su32(cbuf(g)), chunks + (size_t)(g % n) * P.chunk_bytes, P.chunk_bytes, su32(&bars[g]));
-  }
+  // constant images for the first nbuf work items; (lit, lk) is the next
+  // item to load, `issued` the number of items loaded so far (thread 0)
+  int lit = 0, lk = 0, issued = 0;
+  auto load_next = [&]() {
+    if (lit >= my_tiles) return;
+    const int ls = sys_of(tile_of(lit));
+    const int ln = pm.sys_tab ? pm.sys_tab[ls].n : P.sys.n;
+    const int lbytes = pm.sys_tab ? pm.sys_tab[ls].chunk_bytes : P.sys.chunk_bytes;
+    const int64_t loff = pm.sys_tab ? pm.sys_tab[ls].chunk_off : P.sys.chunk_off;
+    bulk_load(su32(cbuf(issued)), chunks + loff + (size_t)lk * lbytes, lbytes,
+              su32(&bars[P.nbuf == 2 ? (issued & 1) : 0]));
+    ++issued;
+    if (++lk >= ln) { lk = 0; ++lit; }
+  };
+  if (tid == 0)
+    for (int q = 0; q < P.nbuf; ++q) load_next();
   int g = 0;
 
   for (int it = 0; it < my_tiles; ++it) {
-    const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-    const int64_t path = (int64_t)tile * 128 + row;
-    const bool live = path < P.p;
+    const int tile = tile_of(it);
+    const MixedSys S = pm.sys_tab ? pm.sys_tab[sys_of(tile)] : P.sys;
+    const int n = S.n;
+    const uint32_t t_j = tbase + 4 * S.MP;
+    const int64_t pos = (int64_t)tile * 128 + row;   // position of this row
+    const int64_t path = pm.list ? pm.list[pos] : pos;
+    const bool live = pm.list ? path >= 0 : pos < P.p;
+    const size_t vbase = !live ? 0 : (pm.vofs ? (size_t)pm.vofs[path] : (size_t)path * n);
+    const float inv_D = S.inv_D;
     // ---- op. 1: z = log y, three-way BF16 split, 1/y (variables split by half)
     const double tv = (live && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);
     const double tau = tau_is_t ? log(tv) : tv;
-    const float tau_d = (float)(tau * (double)P.inv_D);
+    const float tau_d = (float)(tau * (double)inv_D);
     const float t_inv = (float)(tau_is_t ? 1.0 / tv : exp(-tau));
     for (int j = half; j < n; j += 2) {
-      float2 v = live ? y[path * n + j] : make_float2(1.f, 0.f);
+      float2 v = live ? y[vbase + j] : make_float2(1.f, 0.f);
       const float zr = logf(hypotf(v.x, v.y)), zi = atan2f(v.y, v.x);
       const float r2 = v.x * v.x + v.y * v.y;
       sInvY[j * 128 + row] = make_float2(v.x / r2, -v.y / r2);
@@ -229,26 +247,26 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
         const uint16_t hr = bf16_rn(rem_r), hi = bf16_rn(rem_i);
-        *(uint16_t*)(sAre + canon(row, s * n + j, P.KX)) = hr;
-        *(uint16_t*)(sAim + canon(row, s * n + j, P.KX)) = hi;
+        *(uint16_t*)(sAre + canon(row, s * n + j, S.KX)) = hr;
+        *(uint16_t*)(sAim + canon(row, s * n + j, S.KX)) = hi;
         rem_r -= bf16_f(hr);
         rem_i -= bf16_f(hi);
       }
     }
-    for (int q = 3 * n + half; q < P.KX; q += 2) {
-      *(uint16_t*)(sAre + canon(row, q, P.KX)) = 0;
-      *(uint16_t*)(sAim + canon(row, q, P.KX)) = 0;
+    for (int q = 3 * n + half; q < S.KX; q += 2) {
+      *(uint16_t*)(sAre + canon(row, q, S.KX)) = 0;
+      *(uint16_t*)(sAim + canon(row, q, S.KX)) = 0;
     }
     proxy_fence();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0 && lookahead && !issue_exp(g)) atomicExch(sAbort, 1);
+    if (tid == 0 && lookahead && !issue_exp(g, S)) atomicExch(sAbort, 1);
 
     for (int k = 0; k < n; ++k, ++g) {
       // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
       // GEMM of equation k+1 is issued now and runs under this epilogue
       if (tid == 0) {
-        const bool ok1 = lookahead ? (k + 1 < n ? issue_exp(g + 1) : true) : issue_exp(g);
+        const bool ok1 = lookahead ? (k + 1 < n ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
         if (!ok1) atomicExch(sAbort, 1);
       }
       bool ok = mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g));   // e of equation k visible
@@ -257,12 +275,12 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       tc_fence_after();
       // ---- complex exponential, BF16 hi/lo split into the op. 2b A operand
       {
-        const float* texp = (const float*)(cbuf(g) + P.off_texp);
-        const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * P.MP) + lane_base;
-        for (int c0 = 16 * half; c0 < P.MP; c0 += 32) {
+        const float* texp = (const float*)(cbuf(g) + S.off_texp);
+        const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * S.MP) + lane_base;
+        for (int c0 = 16 * half; c0 < S.MP; c0 += 32) {
           uint32_t wre[16], wim[16];
           tmem_ld16(tw + c0, wre);
-          tmem_ld16(tw + P.MP + c0, wim);
+          tmem_ld16(tw + S.MP + c0, wim);
           tmem_wait_ld();
           uint32_t hr[8], hi_[8], lr[8], li[8];
 #pragma unroll
@@ -293,11 +311,11 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
           // Re E at K = c0.., Im E at K = MP + c0..; 16 values = two core columns
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const int kre = c0 + 8 * h, kim = P.MP + c0 + 8 * h;
-            *(uint4*)(sAcHi + canon(row, kre, P.KC)) = make_uint4(hr[4 * h], hr[4 * h + 1], hr[4 * h + 2], hr[4 * h + 3]);
-            *(uint4*)(sAcLo + canon(row, kre, P.KC)) = make_uint4(lr[4 * h], lr[4 * h + 1], lr[4 * h + 2], lr[4 * h + 3]);
-            *(uint4*)(sAcHi + canon(row, kim, P.KC)) = make_uint4(hi_[4 * h], hi_[4 * h + 1], hi_[4 * h + 2], hi_[4 * h + 3]);
-            *(uint4*)(sAcLo + canon(row, kim, P.KC)) = make_uint4(li[4 * h], li[4 * h + 1], li[4 * h + 2], li[4 * h + 3]);
+            const int kre = c0 + 8 * h, kim = S.MP + c0 + 8 * h;
+            *(uint4*)(sAcHi + canon(row, kre, S.KC)) = make_uint4(hr[4 * h], hr[4 * h + 1], hr[4 * h + 2], hr[4 * h + 3]);
+            *(uint4*)(sAcLo + canon(row, kre, S.KC)) = make_uint4(lr[4 * h], lr[4 * h + 1], lr[4 * h + 2], lr[4 * h + 3]);
+            *(uint4*)(sAcHi + canon(row, kim, S.KC)) = make_uint4(hi_[4 * h], hi_[4 * h + 1], hi_[4 * h + 2], hi_[4 * h + 3]);
+            *(uint4*)(sAcLo + canon(row, kim, S.KC)) = make_uint4(li[4 * h], li[4 * h + 1], li[4 * h + 2], li[4 * h + 3]);
           }
         }
       }
@@ -309,11 +327,12 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       if (tid == 0) {
         tc_fence_after();
         const uint32_t cb = su32(cbuf(g));
-        for (int s = 0; s < kc_steps; ++s) {
+        const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
+        for (int s = 0; s < S.KC / 16; ++s) {
           const uint64_t ah = smem_desc(su32(sAcHi) + s * 256, 128, sbo_c);
           const uint64_t al = smem_desc(su32(sAcLo) + s * 256, 128, sbo_c);
-          const uint64_t bh = smem_desc(cb + P.off_bhi + s * 256, 128, sbo_c);
-          const uint64_t bl = smem_desc(cb + P.off_blo + s * 256, 128, sbo_c);
+          const uint64_t bh = smem_desc(cb + S.off_bhi + s * 256, 128, sbo_c);
+          const uint64_t bl = smem_desc(cb + S.off_blo + s * 256, 128, sbo_c);
           mma_bf16(t_j, ah, bh, idx_c, s > 0);
           mma_bf16(t_j, ah, bl, idx_c, 1);
           mma_bf16(t_j, al, bh, idx_c, 1);
@@ -324,14 +343,13 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       if (!ok) atomicExch(sAbort, 1);
       tc_fence_after();
       // both GEMMs of equation k are done: its constant buffer is free
-      if (tid == 0 && ok && g + P.nbuf < g_total) {
+      if (tid == 0 && ok) {
         proxy_fence();
-        bulk_load(su32(cbuf(g)), chunks + (size_t)((g + P.nbuf) % n) * P.chunk_bytes, P.chunk_bytes,
-                  su32(&bars[P.nbuf == 2 ? (g & 1) : 0]));
+        load_next();   // item g + nbuf into this buffer
       }
       // ---- op. 3: scale to y-coordinates and write row k (column chunks split by half)
       if (ok) {
-        for (int c0 = 16 * half; c0 < P.NJ; c0 += 32) {
+        for (int c0 = 16 * half; c0 < S.NJ; c0 += 32) {
           uint32_t jr[16];
           tmem_ld16(t_j + lane_base + c0, jr);
           tmem_wait_ld();
@@ -343,13 +361,13 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
             if (u < n) {
               const float2 iy = sInvY[u * 128 + row];
               const float2 hy = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
-              if (ext) ext[ext_index(path, k, u, n)] = hy;
+              if (ext) ext[ext_index(pos, k, u, nmax)] = hy;
               if (oHy) oHy[((size_t)path * n + k) * n + u] = hy;
             } else if (u == n) {
-              if (ext) ext[ext_index(path, k, n, n)] = v;
+              if (ext) ext[ext_index(pos, k, n, nmax)] = v;
               if (oHt) oHt[(size_t)path * n + k] = make_float2(v.x * t_inv, v.y * t_inv);
             } else if (u == n + 1) {
-              if (ext) ext[ext_index(path, k, n + 1, n)] = v;
+              if (ext) ext[ext_index(pos, k, n + 1, nmax)] = v;
               if (oH) oH[(size_t)path * n + k] = v;
             }
           }
@@ -366,7 +384,7 @@ teardown:
     if (tid == 0) {
       atomicExch(err, 1);
       // let copies and MMAs still in flight land before the CTA's resources go away
-      for (int q = g; q < g + P.nbuf && q < g_total; ++q) mbar_wait(su32(&bars[P.nbuf == 2 ? (q & 1) : 0]), cpar(q));
+      for (int q = g; q < issued; ++q) mbar_wait(su32(&bars[P.nbuf == 2 ? (q & 1) : 0]), cpar(q));
       mbar_wait(su32(&bars[2 + (g & 1)]), (uint32_t)(g >> 1) & 1u);
       mbar_wait(su32(&bars[2 + ((g + 1) & 1)]), (uint32_t)((g + 1) >> 1) & 1u);
     }
@@ -381,51 +399,43 @@ teardown:
 
 int g_num_sms = 0;
 
-}  // namespace
-
-cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const double* tin, int tau_is_t,
-                              const EvalOut& out, cudaStream_t st) {
-  if (p <= 0) return cudaSuccess;
-  const MixedLayout& L = s->ml;
-  MixedArgs a;
-  a.n = s->n;
-  a.MP = L.MP;
-  a.KX = L.KX;
-  a.NJ = L.NJ;
-  a.KC = L.KC;
-  a.chunk_bytes = L.chunk_bytes;
-  a.off_bexp = L.off_bexp;
-  a.off_bhi = L.off_bhi;
-  a.off_blo = L.off_blo;
-  a.off_texp = L.off_texp;
-  a.tmem_cols = L.tmem_cols;
-  int off = 0;
-  auto take = [&](int bytes) {
-    int o = off;
-    off += (bytes + 1023) / 1024 * 1024;
-    return o;
-  };
-  a.s_are = take(128 * L.KX * 2);
-  a.s_aim = take(128 * L.KX * 2);
-  a.s_invy = take(128 * s->n * 8);
-  a.s_achi = take(128 * L.KC * 2);
-  a.s_aclo = take(128 * L.KC * 2);
-  a.s_const0 = take(L.chunk_bytes);
-  const int off_single = off;
-  a.s_const1 = take(L.chunk_bytes);
-  a.s_bar = take(128);
-  int smem = off + 1024;   // slack for aligning the dynamic base
-  a.inv_D = (float)(1.0 / (double)s->D);
-  a.p = p;
-  const int64_t ntiles = (p + 127) / 128;
-  if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
-  a.ntiles = (int)ntiles;
+int num_sms() {
   if (!g_num_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 1;
   }
+  return g_num_sms;
+}
+
+// Shared-memory carve-up for the largest shapes of a launch (maxs), the
+// single-system arguments (sys) and the grid; then the launch.
+cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& maxs, int tmem_cols, int64_t p,
+                        int64_t ntiles, const uint8_t* chunks, const void* y, const double* tin, int tau_is_t,
+                        const EvalOut& out, int32_t* err, const PathMap& pm, int ctas_per_sm, cudaStream_t st) {
+  MixedArgs a;
+  a.sys = sys;
+  a.tmem_cols = tmem_cols;
+  int off = 0;
+  auto take = [&](int bytes) {
+    int o = off;
+    off += (bytes + 1023) / 1024 * 1024;
+    return o;
+  };
+  a.s_are = take(128 * maxs.KX * 2);
+  a.s_aim = take(128 * maxs.KX * 2);
+  a.s_invy = take(128 * maxs.n * 8);
+  a.s_achi = take(128 * maxs.KC * 2);
+  a.s_aclo = take(128 * maxs.KC * 2);
+  a.s_const0 = take(maxs.chunk_bytes);
+  const int off_single = off;
+  a.s_const1 = take(maxs.chunk_bytes);
+  a.s_bar = take(128);
+  int smem = off + 1024;   // slack for aligning the dynamic base
+  a.p = p;
+  if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
+  a.ntiles = (int)ntiles;
   int max_smem = 0;
   {
     int dev = 0;
@@ -444,15 +454,60 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
   cudaError_t e = cudaFuncSetAttribute(eval_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // resident CTAs per SM are bounded by tensor memory (512 columns)
-  const int per_sm = 512 / L.tmem_cols >= 2 ? 2 : 1;
-  int64_t grid = (int64_t)g_num_sms * per_sm;
+  const int max_per_sm = eval_mixed_max_ctas(tmem_cols);
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, max_per_sm) : max_per_sm;
+  int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > ntiles) grid = ntiles;
-  int pi = prof_begin(s, "eval_mixed_tc", st);
-  eval_mixed_kernel<<<(unsigned)grid, kEvalThreads, smem, st>>>(a, (const float2*)y, tin, tau_is_t, s->d_chunks,
-                                                       (float2*)out.ext, (float2*)out.H, (float2*)out.Hy,
-                                                       (float2*)out.Ht, s->d_err);
-  prof_end(s, pi, st);
+  if (grid < 1) return cudaSuccess;
+  int pi = prof_begin(prof, "eval_mixed_tc", st);
+  eval_mixed_kernel<<<(unsigned)grid, kEvalThreads, smem, st>>>(a, (const float2*)y, tin, tau_is_t, chunks,
+                                                               (float2*)out.ext, (float2*)out.H, (float2*)out.Hy,
+                                                               (float2*)out.Ht, err, pm);
+  prof_end(prof, pi, st);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }
+
+MixedSys mixed_sys_of(const hpt_system s) {
+  const MixedLayout& L = s->ml;
+  MixedSys m;
+  m.n = s->n;
+  m.MP = L.MP;
+  m.KX = L.KX;
+  m.NJ = L.NJ;
+  m.KC = L.KC;
+  m.chunk_bytes = L.chunk_bytes;
+  m.off_bexp = L.off_bexp;
+  m.off_bhi = L.off_bhi;
+  m.off_blo = L.off_blo;
+  m.off_texp = L.off_texp;
+  m.inv_D = (float)(1.0 / (double)s->D);
+  m.pad_ = 0;
+  m.chunk_off = 0;
+  return m;
+}
+
+cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const double* tin, int tau_is_t,
+                              const EvalOut& out, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  const MixedSys m = mixed_sys_of(s);
+  return launch_core(s, m, m, s->ml.tmem_cols, p, (p + 127) / 128, s->d_chunks, y, tin, tau_is_t, out, s->d_err,
+                     PathMap(), 0, st);
+}
+
+cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tmem_cols, const uint8_t* chunks,
+                                  int64_t p, const void* y, const double* tau, const PathMap& pm, void* ext,
+                                  int32_t* err, int ctas_per_sm, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  if (!pm.list || !pm.tile_sys || !pm.vofs || !pm.npos || !pm.sys_tab || pm.nmax != maxs.n)
+    return cudaErrorInvalidValue;
+  EvalOut out;
+  out.ext = ext;
+  return launch_core(prof, maxs, maxs, tmem_cols, p, (p + 127) / 128, chunks, y, tau, 0, out, err, pm,
+                     ctas_per_sm, st);
 }
 
 }  // namespace hpt

@@ -161,8 +161,8 @@ __device__ __forceinline__ unsigned group_mask() {
 // [J^H | g | 0] (adjoint = true, J = H_y, g from gx) for one path; returns
 // whether every entry is finite (group-uniform).
 template <typename T, typename S, int G, int R>
-__device__ __forceinline__ bool load_rows(int n, const void* ext, int64_t path, bool valid, bool adjoint,
-                                          const double2* gx, PathRows<T, G, R>& P) {
+__device__ __forceinline__ bool load_rows(int n, int nmax, const void* ext, int64_t q, size_t vbase, bool valid,
+                                          bool adjoint, const double2* gx, PathRows<T, G, R>& P) {
   constexpr int NC = G * R;
   const int lane = threadIdx.x & (G - 1);
   T chk = T(0);
@@ -174,7 +174,7 @@ __device__ __forceinline__ bool load_rows(int n, const void* ext, int64_t path, 
     for (int c = 0; c < NC; ++c) {
       P.a[s][c] = mk<T>(0, 0);
       if (have && c < n) {
-        cx<S> v = adjoint ? ld<S>(ext, ext_index(path, c, r, n)) : ld<S>(ext, ext_index(path, r, c, n));
+        cx<S> v = adjoint ? ld<S>(ext, ext_index(q, c, r, nmax)) : ld<S>(ext, ext_index(q, r, c, nmax));
         P.a[s][c] = adjoint ? mk<T>((T)v.x, -(T)v.y) : mk<T>((T)v.x, (T)v.y);
         chk += t_abs(P.a[s][c].x) + t_abs(P.a[s][c].y);
       }
@@ -183,11 +183,11 @@ __device__ __forceinline__ bool load_rows(int n, const void* ext, int64_t path, 
     P.bN[s] = mk<T>(0, 0);
     if (have) {
       if (adjoint) {
-        const double2 g = gx[(size_t)path * n + r];
+        const double2 g = gx[vbase + r];
         P.bE[s] = mk<T>((T)g.x, (T)g.y);
       } else {
-        const cx<S> ht = ld<S>(ext, ext_index(path, r, n, n));
-        const cx<S> h = ld<S>(ext, ext_index(path, r, n + 1, n));
+        const cx<S> ht = ld<S>(ext, ext_index(q, r, n, nmax));
+        const cx<S> h = ld<S>(ext, ext_index(q, r, n + 1, nmax));
         P.bE[s] = mk<T>(-(T)ht.x, -(T)ht.y);
         P.bN[s] = mk<T>(-(T)h.x, -(T)h.y);
       }
@@ -358,8 +358,9 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
 // accept/reject, then the next prediction.  TS is the state precision; lane l
 // handles the variables l + G s.
 template <typename TS, int G, int R>
-__device__ __forceinline__ void update_path(int n, int64_t path, int32_t status, bool ok, const cx<TS> (&xE)[R],
-                                            const cx<TS> (&xN)[R], const hpt_paths& S, const hpt_params& prm) {
+__device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, int32_t status, bool ok,
+                                            const cx<TS> (&xE)[R], const cx<TS> (&xN)[R], const hpt_paths& S,
+                                            const hpt_params& prm) {
   const int lane = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
   cx<TS> y[R], yacc[R], dEacc[R];
@@ -369,7 +370,7 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
   for (int s = 0; s < R; ++s) {
     const int j = lane + G * s;
     const bool mine = j < n;
-    const size_t vi = (size_t)path * n + j;
+    const size_t vi = vbase + j;
     y[s] = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
     yacc[s] = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
     dEacc[s] = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
@@ -456,7 +457,7 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
   for (int s = 0; s < R; ++s) {
     const int j = lane + G * s;
     if (j < n) {
-      const size_t vi = (size_t)path * n + j;
+      const size_t vi = vbase + j;
       st<TS>(S.y, vi, y[s]);
       st<TS>(S.y_acc, vi, yacc[s]);
       st<TS>(S.dE_acc, vi, dEacc[s]);
@@ -474,41 +475,68 @@ __device__ __forceinline__ void update_path(int n, int64_t path, int32_t status,
   }
 }
 
+__device__ __forceinline__ int64_t pm_path(const PathMap& m, int64_t q) { return m.list ? m.list[q] : q; }
+__device__ __forceinline__ int pm_n(const PathMap& m, int64_t q, int n) {
+  return m.sys_n ? m.sys_n[m.tile_sys[q >> 7]] : n;
+}
+__device__ __forceinline__ size_t pm_vbase(const PathMap& m, int64_t path, int n) {
+  return m.vofs ? (size_t)m.vofs[path] : (size_t)path * n;
+}
+__device__ __forceinline__ int64_t pm_count(const PathMap& m, int64_t p) { return m.npos ? (int64_t)*m.npos : p; }
+__device__ __forceinline__ int64_t pm_begin(const PathMap& m) { return m.pos_begin ? (int64_t)*m.pos_begin : 0; }
+
 // One Euler-Newton step per ACTIVE path: consolidated solve, then the step
 // control.  T is the state and solve precision.  FP32 solves whose pivot
 // ratio (after equilibration) exceeds prm.cond_max are not applied here: the
-// path goes to redo_list and is solved again in FP64 by redo_fp64_kernel.
+// position goes to redo_list and is solved again in FP64 by redo_fp64_kernel.
+// Persistent: the warps loop over the positions (32/G consecutive positions
+// per warp, always inside one 128-position tile, so n is warp-uniform).
 template <typename T, int G, int R>
 __global__ void __launch_bounds__(kSolveThreads)
-solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
-                    int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list) {
+solve_update_kernel(int n0, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
+                    int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list, PathMap pm) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int per_warp = 32 / G;
   const int lane = threadIdx.x & (G - 1);
-  const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  bool valid = path < p;
-  const int32_t status = valid ? S.status[path] : -1;
-  valid = valid && status == HPT_PATH_ACTIVE;
-  if (!__any_sync(0xffffffffu, valid)) return;   // warp-uniform exit
-  PathRows<T, G, R> P;
-  const bool fin = load_rows<T, T, G, R>(n, ext, path, valid, false, nullptr, P);
-  cx<T> xE[R], xN[R];
-  T cond;
-  const bool ok =
-      group_solve<T, G, R>(n, P, xE, xN, cond, smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes) && fin;
-  if (!valid) return;   // group-uniform; only group-masked shuffles below
-  if (sizeof(T) == 4 && redo_list && ok && !(cond <= (T)prm.cond_max)) {
-    if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = path;
-    return;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int g = (threadIdx.x & 31) / G;
+  unsigned char* sm = smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes;
+  const int64_t npos = pm_count(pm, p);
+  const int nmax = pm.nmax;
+  for (int64_t base = pm_begin(pm) + warp_id * per_warp; base < npos; base += nwarps * per_warp) {
+    const int64_t q = base + g;
+    const int n = pm_n(pm, base, n0);
+    const int64_t path = q < npos ? pm_path(pm, q) : -1;
+    const int32_t status = path >= 0 ? S.status[path] : -1;
+    const bool valid = status == HPT_PATH_ACTIVE;
+    if (!__any_sync(0xffffffffu, valid)) continue;   // warp-uniform skip
+    const size_t vbase = valid ? pm_vbase(pm, path, n) : 0;
+    PathRows<T, G, R> P;
+    const bool fin = load_rows<T, T, G, R>(n, nmax, ext, q, vbase, valid, false, nullptr, P);
+    cx<T> xE[R], xN[R];
+    T cond;
+    const bool ok = group_solve<T, G, R>(n, P, xE, xN, cond, sm) && fin;
+    if (valid) {   // group-uniform; only group-masked shuffles below
+      if (sizeof(T) == 4 && redo_list && ok && !(cond <= (T)prm.cond_max)) {
+        if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = q;
+      } else {
+        update_path<T, G, R>(n, path, vbase, status, ok, xE, xN, S, prm);
+      }
+    }
+    __syncwarp();
   }
-  update_path<T, G, R>(n, path, status, ok, xE, xN, S, prm);
 }
 
-// FP64 re-solve of the paths listed by the FP32 kernel (same FP32 Jacobian,
-// FP64 factorisation), then their step control in the FP32 state.
+// FP64 re-solve of the positions listed by the FP32 kernel (same FP32
+// Jacobian, FP64 factorisation), then their step control in the FP32 state.
+// Entries of the list sit next to any other, so n may differ between the
+// groups of a warp: the warp solves with the largest n of its groups and a
+// smaller system gets identity rows for the unknowns it does not have.
 template <int G, int R>
 __global__ void __launch_bounds__(kSolveThreads)
-redo_fp64_kernel(int n, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
-                 const int32_t* __restrict__ redo_count, const int64_t* __restrict__ redo_list) {
+redo_fp64_kernel(int n0, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
+                 const int32_t* __restrict__ redo_count, const int64_t* __restrict__ redo_list, PathMap pm) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int count = *redo_count;
   constexpr int per_warp = 32 / G;
@@ -519,12 +547,29 @@ redo_fp64_kernel(int n, const void* __restrict__ ext, hpt_paths S, hpt_params pr
   for (int64_t base = warp_id * per_warp; base < count; base += nwarps * per_warp) {
     const int64_t i = base + g;
     const bool valid = i < count;
-    const int64_t path = valid ? redo_list[i] : 0;
+    const int64_t q = valid ? redo_list[i] : 0;
+    const int64_t path = valid ? pm_path(pm, q) : 0;
+    const int n = valid ? pm_n(pm, q, n0) : 0;
+    int nw = n;   // the warp's largest n: group_solve needs a warp-uniform size
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nw = max(nw, __shfl_xor_sync(0xffffffffu, nw, o));
+    const size_t vbase = valid ? pm_vbase(pm, path, n) : 0;
     PathRows<double, G, R> P;
-    const bool fin = load_rows<double, float, G, R>(n, ext, path, valid, false, nullptr, P);
+    const bool fin = load_rows<double, float, G, R>(n, pm.nmax, ext, q, vbase, valid, false, nullptr, P);
+    // rows n..nw-1 become identity rows (their unknowns solve to 0)
+    const int lane = threadIdx.x & (G - 1);
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const int r = lane + G * s;
+      if (r >= n && r < nw) {
+#pragma unroll
+        for (int c = 0; c < G * R; ++c)
+          if (c == r) P.a[s][c] = mk<double>(1.0, 0.0);
+      }
+    }
     cx<double> xE[R], xN[R];
     double cond;
-    const bool ok = group_solve<double, G, R>(n, P, xE, xN, cond, sm) && fin;
+    const bool ok = group_solve<double, G, R>(nw, P, xE, xN, cond, sm) && fin;
     if (valid) {
       cx<float> fE[R], fN[R];
 #pragma unroll
@@ -532,7 +577,7 @@ redo_fp64_kernel(int n, const void* __restrict__ ext, hpt_paths S, hpt_params pr
         fE[s] = mk<float>((float)xE[s].x, (float)xE[s].y);
         fN[s] = mk<float>((float)xN[s].x, (float)xN[s].y);
       }
-      update_path<float, G, R>(n, path, S.status[path], ok, fE, fN, S, prm);
+      update_path<float, G, R>(n, path, vbase, S.status[path], ok, fE, fN, S, prm);
     }
     __syncwarp();
   }
@@ -549,7 +594,7 @@ newton_kernel(int n, int64_t p, const void* __restrict__ ext, double2* __restric
   const bool valid = path < p && done[path] == 0;
   if (!__any_sync(0xffffffffu, valid)) return;
   PathRows<double, G, R> P;
-  const bool fin = load_rows<double, double, G, R>(n, ext, path, valid, false, nullptr, P);
+  const bool fin = load_rows<double, double, G, R>(n, n, ext, path, (size_t)path * n, valid, false, nullptr, P);
   cx<double> xE[R], xN[R];
   double cond;
   const bool ok =
@@ -605,7 +650,7 @@ adjoint_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t*
   const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const bool valid = path < p;
   PathRows<double, G, R> P;
-  const bool fin = load_rows<double, double, G, R>(n, ext, path, valid, true, gx, P);
+  const bool fin = load_rows<double, double, G, R>(n, n, ext, path, (size_t)path * n, valid, true, gx, P);
   cx<double> lam[R], dummy[R];
   double cond;
   const bool ok =
@@ -725,13 +770,29 @@ cudaError_t set_smem(K kernel, int bytes) {
                            : cudaSuccess;
 }
 
+// Persistent grids: enough blocks to cover the positions once, capped at a
+// few waves of resident blocks (the kernels loop over positions).
+inline unsigned solve_grid(int64_t p, int G) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int64_t need = std::max<int64_t>(1, (p * G + kSolveThreads - 1) / kSolveThreads);
+  return (unsigned)std::min<int64_t>(need, (int64_t)sms * 32);
+}
+
 template <typename T, int G, int R>
 cudaError_t launch_solve_shape(const StepArgs& a, int32_t* rc, int64_t* rl, cudaStream_t st) {
   const int smem = (kSolveThreads / G) * GroupSmem<T, G * R>::bytes;
   cudaError_t e = set_smem(solve_update_kernel<T, G, R>, smem);
   if (e != cudaSuccess) return e;
-  solve_update_kernel<T, G, R><<<blocks_for(a.p * G, kSolveThreads), kSolveThreads, smem, st>>>(
-      a.n, a.p, a.ext, a.st, a.prm, rc, rl);
+  PathMap pm = a.map;
+  if (!pm.nmax) pm.nmax = a.n;
+  solve_update_kernel<T, G, R><<<solve_grid(a.p, G), kSolveThreads, smem, st>>>(a.n, a.p, a.ext, a.st, a.prm, rc,
+                                                                                 rl, pm);
   return cudaGetLastError();
 }
 
@@ -740,8 +801,10 @@ cudaError_t launch_redo_shape(const StepArgs& a, cudaStream_t st) {
   const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
   cudaError_t e = set_smem(redo_fp64_kernel<G, R>, smem);
   if (e != cudaSuccess) return e;
+  PathMap pm = a.map;
+  if (!pm.nmax) pm.nmax = a.n;
   const unsigned nb = blocks_for(std::min<int64_t>(a.p, 8192) * G, kSolveThreads);
-  redo_fp64_kernel<G, R><<<nb, kSolveThreads, smem, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+  redo_fp64_kernel<G, R><<<nb, kSolveThreads, smem, st>>>(a.n, a.ext, a.st, a.prm, a.redo_count, a.redo_list, pm);
   return cudaGetLastError();
 }
 
@@ -797,6 +860,22 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
                  : launch_redo_shape<32, 1>(a, st);
   prof_end(s, pi, st);
   return e;
+}
+
+int solve_shape_of(int n) { return shape_of(n); }
+
+cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st) {
+  if (a.p <= 0) return cudaSuccess;
+  return shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
+       : shape == 1 ? launch_solve_shape<float, 8, 2>(a, a.redo_count, a.redo_list, st)
+                    : launch_solve_shape<float, 32, 1>(a, a.redo_count, a.redo_list, st);
+}
+
+cudaError_t launch_redo_fp64_shape(int shape, const StepArgs& a, cudaStream_t st) {
+  if (a.p <= 0) return cudaSuccess;
+  return shape == 0 ? launch_redo_shape<8, 1>(a, st)
+       : shape == 1 ? launch_redo_shape<8, 2>(a, st)
+                    : launch_redo_shape<32, 1>(a, st);
 }
 
 cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void* x, int32_t* done,

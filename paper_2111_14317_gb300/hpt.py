@@ -27,9 +27,12 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA err
                 7: "not supported"}
 
 EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lift_exponents",
+           "hpt_binomial_start",
            "hpt_create_system", "hpt_destroy", "hpt_get_info", "hpt_get_texp", "hpt_eval",
            "hpt_paths_init", "hpt_step", "hpt_step_static", "hpt_track", "hpt_polish", "hpt_adjoint",
-           "hpt_device_error", "hpt_profile_enable", "hpt_profile_read"]
+           "hpt_device_error", "hpt_profile_enable", "hpt_profile_read", "hpt_binomial_points",
+           "hpt_batch_create", "hpt_batch_destroy", "hpt_batch_get_tuning", "hpt_batch_set_tuning",
+           "hpt_batch_track", "hpt_batch_autotune", "hpt_batch_stats"]
 
 
 class HptError(RuntimeError):
@@ -68,11 +71,20 @@ class _Paths(ctypes.Structure):
                  "rejects", "streak")]
 
 
+class Tuning(ctypes.Structure):
+    """hpt_batch_tuning."""
+    _fields_ = [("steps_per_round", ctypes.c_int32), ("eval_ctas_per_sm", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (int(self.steps_per_round), int(self.eval_ctas_per_sm))
+
+
 _VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
 _lib.hpt_status_string.restype = ctypes.c_char_p
 _lib.hpt_last_error.restype = ctypes.c_char_p
 for _name, _args in {
     "hpt_lift_exponents": [_I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_binomial_start": [_I32, _VP, _VP, _VP, _VP, _I64, _I64, _VP, _VP],
     "hpt_create_system": [_I32, _VP, _VP, _VP, _VP, _VP, _I32, _VP],
     "hpt_destroy": [_VP],
     "hpt_get_info": [_VP, _VP, _VP, _VP, ctypes.c_double, _VP],
@@ -87,6 +99,14 @@ for _name, _args in {
     "hpt_device_error": [_VP],
     "hpt_profile_enable": [_VP, _I32],
     "hpt_profile_read": [_VP, _I32, _VP, _VP, _VP, _VP],
+    "hpt_binomial_points": [_I32, _VP, _VP, _VP, _VP, _I64, _VP, _VP],
+    "hpt_batch_create": [_I32, _VP, _VP],
+    "hpt_batch_destroy": [_VP],
+    "hpt_batch_get_tuning": [_VP, _VP],
+    "hpt_batch_set_tuning": [_VP, _VP],
+    "hpt_batch_track": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_batch_autotune": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_batch_stats": [_VP, _VP, _VP, _VP],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int
@@ -156,6 +176,34 @@ def lift_exponents(n, m, exponents, lifting, cell):
                                    _np_ptr(e), ctypes.byref(D), _np_ptr(al), _np_ptr(be)),
            "hpt_lift_exponents")
     return dict(e=e.tolist(), D=int(D.value), alpha_num=al.tolist(), beta_num=be.tolist())
+
+
+def binomial_start(n, m, exponents, coeffs, pairs, first=0, count=None):
+    """Host-only start points of a cell given by pairs: (y0 (count, n)
+    complex128 numpy, |det V|)."""
+    msz, ex, co, _, M = _arrays(n, m, exponents, coeffs, np.zeros(sum(np.atleast_1d(m))))
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    tot = ctypes.c_int64(0)
+    _check(_lib.hpt_binomial_start(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), 0, 0, None,
+                                   ctypes.byref(tot)), "hpt_binomial_start")
+    if count is None:
+        count = int(tot.value) - first
+    y0 = np.zeros((count, n), np.complex128)
+    _check(_lib.hpt_binomial_start(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), int(first),
+                                   int(count), _np_ptr(y0), ctypes.byref(tot)), "hpt_binomial_start")
+    return y0, int(tot.value)
+
+
+def binomial_points(n, m, exponents, coeffs, pairs, k):
+    """Host-only start points y = exp(V^-1 (log b + 2 pi i k)) for the integer
+    rows of k (count, n): (count, n) complex128 numpy."""
+    msz, ex, co, _, M = _arrays(n, m, exponents, coeffs, np.zeros(sum(np.atleast_1d(m))))
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    kv = np.ascontiguousarray(np.asarray(k, dtype=np.int64).reshape(-1, n))
+    y0 = np.zeros((kv.shape[0], n), np.complex128)
+    _check(_lib.hpt_binomial_points(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), kv.shape[0],
+                                    _np_ptr(kv), _np_ptr(y0)), "hpt_binomial_points")
+    return y0
 
 
 class PathState:
@@ -316,3 +364,79 @@ class System:
                                      ctypes.byref(cnt)), "hpt_profile_read")
         return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(cnt.value, cap))}
 
+
+class Batch:
+    """Many HPT_MIXED systems tracked together (hpt_batch).  Keeps the System
+    objects alive for its own lifetime."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)
+        self.n = [s.n for s in self.systems]
+        arr = (ctypes.c_void_p * len(self.systems))(*[s._h.value for s in self.systems])
+        h = ctypes.c_void_p()
+        _check(_lib.hpt_batch_create(len(self.systems), arr, ctypes.byref(h)), "hpt_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.hpt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def tuning(self):
+        t = Tuning()
+        _check(_lib.hpt_batch_get_tuning(self._h, ctypes.byref(t)), "hpt_batch_get_tuning")
+        return t.as_tuple()
+
+    @tuning.setter
+    def tuning(self, kv):
+        t = Tuning(int(kv[0]), int(kv[1]))
+        _check(_lib.hpt_batch_set_tuning(self._h, ctypes.byref(t)), "hpt_batch_set_tuning")
+
+    def _paths(self, y0s):
+        p = np.ascontiguousarray(np.array([int(y.shape[0]) for y in y0s], dtype=np.int64))
+        assert len(p) == len(self.systems)
+        return p
+
+    def track(self, y0, paths, params=None, stream=None):
+        """y0: (sum p_s n_s,) complex128 device tensor (systems concatenated,
+        path-major); paths: per-system path counts.  Returns (x like y0,
+        status (P,) int32, steps (P,) int32)."""
+        params = params or Params()
+        p = np.ascontiguousarray(np.asarray(paths, dtype=np.int64))
+        assert y0.dtype == torch.complex128 and y0.is_contiguous()
+        x = torch.empty_like(y0)
+        P = int(p.sum())
+        st = torch.empty(P, dtype=torch.int32, device=y0.device)
+        sp = torch.empty(P, dtype=torch.int32, device=y0.device)
+        _check(_lib.hpt_batch_track(self._h, _np_ptr(p), _t_ptr(y0), ctypes.byref(params), _t_ptr(x),
+                                    _t_ptr(st), _t_ptr(sp), _stream(stream)), "hpt_batch_track")
+        return x, st, sp
+
+    def autotune(self, y0, paths, params=None, stream=None):
+        """Runs every candidate tuning once, keeps the fastest.  Returns
+        (best (K, ctas), {(K, ctas): ms})."""
+        params = params or Params()
+        p = np.ascontiguousarray(np.asarray(paths, dtype=np.int64))
+        x = torch.empty_like(y0)
+        cap = 16
+        cand = (Tuning * cap)()
+        ms = np.zeros(cap)
+        nc = ctypes.c_int32(cap)
+        best = Tuning()
+        _check(_lib.hpt_batch_autotune(self._h, _np_ptr(p), _t_ptr(y0), ctypes.byref(params), _t_ptr(x),
+                                       _stream(stream), ctypes.byref(best), cand, _np_ptr(ms),
+                                       ctypes.byref(nc)), "hpt_batch_autotune")
+        return best.as_tuple(), {cand[i].as_tuple(): float(ms[i]) for i in range(nc.value)}
+
+    def stats(self):
+        r, ps, k = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(_lib.hpt_batch_stats(self._h, ctypes.byref(r), ctypes.byref(ps), ctypes.byref(k)),
+               "hpt_batch_stats")
+        return dict(rounds=int(r.value), position_steps=int(ps.value), kernels_per_round=int(k.value))

@@ -85,3 +85,86 @@ def test_lift_errors(hpt):
     with pytest.raises(hpt.HptError) as e:
         hpt.lift_exponents(2, [3, 3], bad, lift, {"kind": "pairs", "pairs": [[0, 1], [0, 1]]})
     assert e.value.code == 5
+
+
+@pytest.mark.parametrize("cfg", [W.config1, W.config2])
+def test_binomial_start_matches_oracle(hpt, cfg):
+    """The library's start points (its own integer diagonal form) are the
+    oracle's start set: same count |det V|, same points up to order."""
+    s, cl, _ = _util.first_generic(cfg)
+    for c in cl[:8]:
+        y_lib, tot = hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, c["pairs"])
+        assert tot == c["det"]
+        assert _util.match_solutions(y_lib, cells.start_points(s, c["pairs"])) < 1e-9
+
+
+def test_binomial_start_large_determinant(hpt):
+    """n=8 planted cell with |det V| ~ 1e5 (unimodular factors with entries
+    ~1e8): the library's start points solve y^V = b to rounding level and are
+    distinct."""
+    s, pairs, _, d = _util.planted_case(W.config5, 4096)
+    y, tot = hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, pairs, 1000, 3000)
+    assert tot == d
+    V = np.array(cells.pair_matrix(s, pairs))
+    off = s.offsets
+    b = np.array([-s.coeffs[off[k] + pairs[k][0]] / s.coeffs[off[k] + pairs[k][1]] for k in range(s.n)])
+    res = np.abs(np.prod(y[:, None, :] ** V[None, :, :], axis=2) / b[None, :] - 1).max()
+    assert res < 1e-12
+    dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
+    np.fill_diagonal(dd, np.inf)
+    assert dd.min() > 1e-8
+
+
+def test_binomial_points_match_oracle(hpt):
+    """hpt_binomial_points equals the oracle's linear-solve start points
+    (FP64 rounding only) on many-systems workload systems."""
+    for idx in (0, 1, 5):
+        s, pairs = W.config4_system(idx)
+        V = np.array(cells.pair_matrix(s, pairs))
+        off = s.offsets
+        b = np.array([-s.coeffs[off[k] + pairs[k][0]] / s.coeffs[off[k] + pairs[k][1]] for k in range(s.n)])
+        rng = np.random.default_rng(idx)
+        ks = rng.integers(-50, 50, size=(16, s.n))
+        got = hpt.binomial_points(s.n, s.m, s.exponents, s.coeffs, pairs, ks)
+        want = cells.binomial_points(V, b, ks)
+        err = np.abs(got - want).max() / np.abs(want).max()
+        assert err < 1e-9, (idx, err)
+
+
+def test_binomial_points_singular(hpt):
+    s, pairs = W.config4_system(0)
+    pr = np.array(pairs).copy()
+    pr[1] = pr[0] if s.m[1] > max(pr[0]) else pr[1]
+    # a pair matrix with two equal rows: copy equation 0's support into 1's pairs
+    ex = np.array(s.exponents).copy()
+    off = s.offsets
+    ex[off[1] + pr[1][0]] = ex[off[0] + pr[0][0]]
+    ex[off[1] + pr[1][1]] = ex[off[0] + pr[0][1]]
+    with pytest.raises(hpt.HptError) as ei:
+        hpt.binomial_points(s.n, s.m, ex, s.coeffs, pr, np.zeros((1, s.n), np.int64))
+    assert ei.value.code == 5
+
+
+def test_lift_large_planted_cells_bit_exact(hpt):
+    """Planted pair cells of the many-systems workload (n up to 24, |det V|
+    beyond 64-bit range): the library's exact lift equals the oracle's."""
+    for idx in (1, 3, 4, 5):
+        s, pairs = W.config4_system(idx)
+        cell = {"kind": "pairs", "pairs": pairs}
+        want = cells.t_exponents(s, cell)
+        got = hpt.lift_exponents(s.n, s.m, s.exponents, s.lifting, cell)
+        assert got["e"] == [int(v) for v in want["e"]]
+        assert got["D"] == want["D"]
+
+
+def test_lift_singular_planted_cell(hpt):
+    """A planted cell whose pair matrix has two equal rows is refused
+    (HPT_ENOTCELL) by the exact modular determinant check."""
+    s, pairs = W.config4_system(4)
+    ex = np.array(s.exponents).copy()
+    off = s.offsets
+    ex[off[1] + pairs[1][0]] = ex[off[0] + pairs[0][0]]
+    ex[off[1] + pairs[1][1]] = ex[off[0] + pairs[0][1]]
+    with pytest.raises(hpt.HptError) as ei:
+        hpt.lift_exponents(s.n, s.m, ex, s.lifting, {"kind": "pairs", "pairs": pairs})
+    assert ei.value.code == 5

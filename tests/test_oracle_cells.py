@@ -183,3 +183,66 @@ def test_start_points_large_determinant():
     dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
     np.fill_diagonal(dd, np.inf)
     assert dd.min() > 1e-8
+
+
+def _pair_data(s, pairs):
+    V = np.array(cells.pair_matrix(s, pairs))
+    off = s.offsets
+    b = np.array([-s.coeffs[off[k] + pairs[k][0]] / s.coeffs[off[k] + pairs[k][1]] for k in range(s.n)])
+    return V, b
+
+
+def _powprod(y, V):
+    """prod_j y_j^{V[k][j]} by repeated multiplication (complex128)."""
+    out = np.ones((y.shape[0], V.shape[0]), dtype=np.complex128)
+    for k in range(V.shape[0]):
+        for j in range(V.shape[1]):
+            e = int(V[k, j])
+            f = y[:, j] if e >= 0 else 1.0 / y[:, j]
+            for _ in range(abs(e)):
+                out[:, k] *= f
+    return out
+
+
+def test_binomial_points_cover_the_exact_enumeration():
+    """Small |det V|: points for k over a box that meets every coset of
+    V Z^n are exactly the |det V| solutions of the exact enumeration."""
+    import _util
+
+    def small(att):
+        s = W.laurent_system(7, 2, 4, -2, 2, 0, attempt=att)
+        lift, pairs = W.planted_lifting(7, s.m, 16, attempt=att)
+        return s.with_lifting(lift), pairs
+
+    s, pairs, _, d = _util.planted_case(small, 3, 12)
+    V, b = _pair_data(s, pairs)
+    exact = cells.start_points(s, pairs)
+    assert exact.shape[0] == d
+    # d e_j lies in V Z^n (d V^{-1} is integral), so [0, d)^n meets every coset
+    ks = np.array(list(itertools.product(*([range(d)] * s.n))), dtype=np.int64)
+    ys = cells.binomial_points(V, b, ks)
+    # distinct points of ys
+    reps = []
+    for y in ys:
+        if not any(np.abs(y - r).max() < 1e-9 for r in reps):
+            reps.append(y)
+    assert len(reps) == d
+    for r in reps:
+        assert np.abs(exact - r).max(axis=1).min() < 1e-10
+
+
+def test_binomial_points_large_determinant():
+    """Many-systems workload systems (n up to 24, |det V| far beyond 2^62):
+    points for k = j e_1 solve y^V = b (checked by repeated multiplication)
+    and are distinct."""
+    for idx in (0, 3, 7):
+        s, pairs = W.config4_system(idx)
+        V, b = _pair_data(s, pairs)
+        ks = np.zeros((24, s.n), np.int64)
+        ks[:, 0] = np.arange(24)
+        y = cells.binomial_points(V, b, ks)
+        res = np.abs(_powprod(y, V) / b[None, :] - 1).max()
+        assert res < 1e-9, (idx, s.n, res)
+        dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
+        np.fill_diagonal(dd, np.inf)
+        assert dd.min() > 1e-8
