@@ -231,9 +231,94 @@ def run_gpu(args):
         h.close()
         del st, pristine_dev
         torch.cuda.empty_cache()
+    if args.batch_systems > 0:
+        out["batch"] = run_batch(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     return out, ws, rank
+
+
+BATCH_WORKLOAD = ("many-systems batch: 256 random Laurent systems, n ~ U{4..24}, m_k ~ U{n+1..4n}, "
+                  "exponents in [-3,3], coefficients e^{i theta}, planted pair cell (lifting 0 on one pair "
+                  "per support, U{1..16} elsewhere); 512 paths per system from the start points "
+                  "exp(V^-1 (log b + 2 pi i j e_1)), j < 512; tracked t: 0 -> 1 and polished")
+
+
+def run_batch(args, dev):
+    """The batching form on the many-systems workload: autotune, then time
+    whole hpt_batch_track calls (device-resident start points) and one
+    end-to-end call with the start points copied from pinned host memory and
+    the solutions copied back inside the timed region."""
+    import torch
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+    nsys, npaths = args.batch_systems, args.batch_paths
+    t0 = time.perf_counter()
+    systems, y0s = [], []
+    for idx in range(nsys):
+        s, pairs = W.config4_system(idx)
+        systems.append(hpt.System.from_laurent(s, {"kind": "pairs", "pairs": pairs}, hpt.HPT_MIXED))
+        ks = np.zeros((npaths, s.n), np.int64)
+        ks[:, 0] = np.arange(npaths)
+        y0s.append(hpt.binomial_points(s.n, s.m, s.exponents, s.coeffs, pairs, ks).reshape(-1))
+    setup_s = time.perf_counter() - t0
+    paths = [npaths] * nsys
+    y0_host = torch.from_numpy(np.concatenate(y0s))
+    y0 = y0_host.to(dev)
+    b = hpt.Batch(systems)
+    prm = hpt.Params(tol_accept=3e-3)
+    best, cand = b.autotune(y0, paths, prm)
+    for _ in range(max(1, min(args.warmup, 2))):
+        b.track(y0, paths, prm)
+    reps = max(1, args.batch_reps)
+    with ClockSampler(dev.index or 0) as clk:
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, st, sp = b.track(y0, paths, prm)
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) * 1e3)
+    stats = b.stats()
+    # end to end: pinned host start points in, solutions and statuses out
+    pinned = y0_host.pin_memory()
+    x_host = torch.empty_like(y0_host).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    yd = pinned.to(dev, non_blocking=True)
+    x, st, sp = b.track(yd, paths, prm)
+    x_host.copy_(x, non_blocking=True)
+    st_h = st.cpu()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    sp_h = sp.cpu().numpy()
+    st_n = st_h.numpy()
+    total_steps = int(sp_h.sum())
+    t_ms = statistics.median(ms)
+    conv = sp_h[st_n == hpt.CONVERGED]
+    out = {
+        "workload": BATCH_WORKLOAD, "systems": nsys, "paths": nsys * npaths,
+        "ms_per_track": t_ms, "ms_list": ms,
+        "value": total_steps / (t_ms * 1e-3), "unit": "path-steps/s",
+        "paths_per_s": nsys * npaths / (t_ms * 1e-3),
+        "e2e": {"ms_per_track": e2e_ms, "value": total_steps / (e2e_ms * 1e-3), "unit": "path-steps/s",
+                "h2d_bytes": int(y0_host.numel() * 16), "d2h_bytes": int(y0_host.numel() * 16 + st_n.size * 4)},
+        "path_steps": total_steps, "position_steps": stats["position_steps"],
+        "lane_efficiency": total_steps / max(stats["position_steps"], 1),
+        "rounds": stats["rounds"], "kernels_per_round": stats["kernels_per_round"],
+        "gpu_launches_rounds": stats["rounds"] * stats["kernels_per_round"],
+        "tuning": {"steps_per_round": best[0], "eval_ctas_per_sm": best[1],
+                   "candidates_ms": {f"K={k},ctas={c}": v for (k, c), v in cand.items()}},
+        "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st_n, return_counts=True))},
+        "steps_per_path": {"min": int(conv.min()) if conv.size else None,
+                           "median": float(np.median(conv)) if conv.size else None,
+                           "max": int(conv.max()) if conv.size else None},
+        "setup_s": setup_s, "clocks": clk.summary(),
+    }
+    b.close()
+    for h in systems:
+        h.close()
+    return out
 
 
 def cpu_baseline(seconds=12.0, max_paths=PATHS):
@@ -271,6 +356,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch-systems", type=int, default=256, help="0 skips the many-systems batch")
+    ap.add_argument("--batch-paths", type=int, default=512)
+    ap.add_argument("--batch-reps", type=int, default=3)
     args = ap.parse_args()
     ws, rank, _ = _dist()
 
@@ -314,6 +402,10 @@ def main():
             kinfo[name] = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
                            "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "ms_avg": avg * 1e3,
                            "launches": launches, "share": msum}
+        elif name.startswith("redo"):
+            # re-solves a device-side list of a few paths: no per-path figure
+            kinfo[name] = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                           "ms_avg": avg * 1e3, "launches": launches, "share": msum}
         else:
             byts = paths_per_launch * (N_VARS * (N_VARS + 2) * 8 + 3 * N_VARS * 8 * 2 + 3 * 8 * 2 + 5 * 4 * 2)
             ach = byts / avg / 1e9
@@ -349,6 +441,8 @@ def main():
         "clocks": mx["clocks"],
         "gpu_launches": mx["launches"],
     }
+    if "batch" in out:
+        line["batch"] = out["batch"]
     print(json.dumps(line))
 
 

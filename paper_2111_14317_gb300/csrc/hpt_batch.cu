@@ -50,6 +50,7 @@ struct hpt_batch_s {
   // constants on the device
   uint8_t* d_chunks = nullptr;
   hpt::MixedSys* d_tab = nullptr;
+  hpt::Fp64Sys* d_f64 = nullptr;
   int32_t* d_sys_n = nullptr;
   int32_t* d_order = nullptr;
   int32_t* d_err = nullptr;
@@ -79,10 +80,10 @@ namespace {
 
 constexpr int kCtlWords = 8;   // [0] positions, [1..3] bucket begins, [4..6] bucket ends
 
-// One block per system: the system's live paths in order, into tmp at the
-// system's own path range; cnt[s] = their number.
+// One block per system: the system's live paths (flag == want) in order,
+// into tmp at the system's own path range; cnt[s] = their number.
 __global__ void compact_count_kernel(const int64_t* __restrict__ pb, const int32_t* __restrict__ np,
-                                     const int32_t* __restrict__ status, int64_t* __restrict__ tmp,
+                                     const int32_t* __restrict__ flag, int32_t want, int64_t* __restrict__ tmp,
                                      int32_t* __restrict__ cnt) {
   __shared__ int wsum[8];
   const int s = blockIdx.x;
@@ -92,7 +93,7 @@ __global__ void compact_count_kernel(const int64_t* __restrict__ pb, const int32
   int total = 0;
   for (int i0 = 0; i0 < p; i0 += 256) {
     const int i = i0 + threadIdx.x;
-    const bool live = i < p && status[base + i] == HPT_PATH_ACTIVE;
+    const bool live = i < p && flag[base + i] == want;
     const unsigned bal = __ballot_sync(0xffffffffu, live);
     if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
@@ -173,7 +174,7 @@ struct Problem {
   int64_t pmax = 0;              // largest paths[s]
   // byte offsets in d_state
   size_t o_y, o_ya, o_de, o_tau, o_dt, o_ta, o_st, o_sp, o_ac, o_rj, o_sk, o_done, o_vofs, o_pb, o_np, o_tmp,
-      o_cnt, o_tb, o_list, o_tsys, o_ctl, o_rc, o_rl, o_ext, o_pext, total;
+      o_cnt, o_tb, o_list, o_tsys, o_ctl, o_rc, o_rl, o_ext, total;
 };
 
 Problem plan(const hpt_batch_s* b, const int64_t* paths) {
@@ -220,12 +221,9 @@ Problem plan(const hpt_batch_s* b, const int64_t* paths) {
   q.o_ctl = take(kCtlWords * 4);
   q.o_rc = take(4);
   q.o_rl = take((size_t)std::max<int64_t>(q.cap, 1) * 8);
-  q.o_ext = take(ext_entries(std::max<int64_t>(q.cap, 1), b->nmax) * 8);
-  // FP64 polish scratch: the extended Jacobian of the largest system's paths
-  size_t pext = 0;
-  for (int s = 0; s < b->nsys; ++s)
-    pext = std::max(pext, ext_entries(std::max<int64_t>(paths[s], 1), b->sys_n[s]) * 16);
-  q.o_pext = take(pext);
+  // extended Jacobian of every position: complex64 while tracking,
+  // complex128 while polishing
+  q.o_ext = take(ext_entries(std::max<int64_t>(q.cap, 1), b->nmax) * 16);
   q.total = off;
   return q;
 }
@@ -264,12 +262,13 @@ hpt_paths sub_state(const hpt_paths& S, int64_t pb, int64_t vb) {
   return o;
 }
 
-// The compaction kernels (3 launches) on stream st.
-cudaError_t enqueue_compaction(const hpt_batch_s* b, const Problem& q, cudaStream_t st) {
+// The compaction kernels (3 launches) on stream st: the paths whose flag
+// (status while tracking, done while polishing) equals want.
+cudaError_t enqueue_compaction(const hpt_batch_s* b, const Problem& q, const int32_t* flag, int32_t want,
+                               cudaStream_t st) {
   char* d = (char*)b->d_state;
-  compact_count_kernel<<<b->nsys, 256, 0, st>>>((const int64_t*)(d + q.o_pb), (const int32_t*)(d + q.o_np),
-                                                (const int32_t*)(d + q.o_st), (int64_t*)(d + q.o_tmp),
-                                                (int32_t*)(d + q.o_cnt));
+  compact_count_kernel<<<b->nsys, 256, 0, st>>>((const int64_t*)(d + q.o_pb), (const int32_t*)(d + q.o_np), flag,
+                                                want, (int64_t*)(d + q.o_tmp), (int32_t*)(d + q.o_cnt));
   compact_scan_kernel<<<1, 1024, 0, st>>>(b->nsys, b->d_order, b->span, (const int32_t*)(d + q.o_cnt),
                                           (int32_t*)(d + q.o_tb), (int32_t*)(d + q.o_ctl));
   compact_scatter_kernel<<<b->nsys, 256, 0, st>>>((const int64_t*)(d + q.o_pb), (const int64_t*)(d + q.o_tmp),
@@ -323,7 +322,7 @@ cudaError_t enqueue_round(hpt_batch_s* b, const Problem& q, const hpt_params& pr
     e = launch_redo_fp64_shape(b->redo_shape, a, st);
     ++nk;
   }
-  if (e == cudaSuccess) e = enqueue_compaction(b, q, st);
+  if (e == cudaSuccess) e = enqueue_compaction(b, q, S.status, HPT_PATH_ACTIVE, st);
   nk += 3;
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_ctl, ctl, kCtlWords * 4, cudaMemcpyDeviceToHost, st);
   *kernels = nk;
@@ -377,7 +376,7 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
                           sub_state(S, q.pb[s], q.vb[s]), st);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4, st);
-  if (e == cudaSuccess) e = enqueue_compaction(b, q, st);   // the initial list: every path
+  if (e == cudaSuccess) e = enqueue_compaction(b, q, S.status, HPT_PATH_ACTIVE, st);   // every path
   if (e != cudaSuccess) return cuda_fail(e, "batch init");
   // the round graph, captured again when the problem, the tuning or the
   // parameters changed (it holds them as launch arguments)
@@ -426,11 +425,31 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
                             done + q.pb[s], st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "batch output");
-  for (int s = 0; s < b->nsys; ++s) {
-    if (!paths[s]) continue;
-    rc = polish_paths(b->sys[s], paths[s], (char*)x_out + q.vb[s] * 16, done + q.pb[s], prm, d + q.o_pext,
-                      paths[s], st);
-    if (rc) return rc;
+  // FP64 Newton polish of the converged paths of every system at once:
+  // each iteration compacts the paths still to polish (done == 0), then per
+  // shape bucket evaluates (FP64) and updates them
+  int32_t* ctl = (int32_t*)(d + q.o_ctl);
+  PathMap pm;
+  pm.list = (const int64_t*)(d + q.o_list);
+  pm.tile_sys = (const int32_t*)(d + q.o_tsys);
+  pm.sys_n = b->d_sys_n;
+  pm.vofs = (const int64_t*)(d + q.o_vofs);
+  pm.nmax = b->nmax;
+  for (int it = 0; it < prm.polish_iters; ++it) {
+    e = enqueue_compaction(b, q, done, 0, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_ctl, ctl, kCtlWords * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch polish compaction");
+    if (b->h_ctl[0] == 0) break;
+    for (int sh = 0; sh < 3 && e == cudaSuccess; ++sh) {
+      if (!q.cap_bucket[sh]) continue;
+      pm.pos_begin = ctl + 1 + sh;
+      pm.npos = ctl + 4 + sh;
+      e = launch_eval_fp64_map(sh, b->d_f64, q.cap_bucket[sh], x_out, nullptr, pm, d + q.o_ext, st);
+      if (e == cudaSuccess)
+        e = launch_newton_map(sh, q.cap_bucket[sh], d + q.o_ext, x_out, done, prm.polish_tol, pm, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch polish");
   }
   e = cudaEventRecord(b->ev_out, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, b->ev_out, 0);
@@ -530,6 +549,10 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
                    cudaMemcpyDeviceToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tab, sizeof(MixedSys) * nsys);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_tab, tab.data(), sizeof(MixedSys) * nsys, cudaMemcpyHostToDevice);
+  std::vector<Fp64Sys> f64(nsys);
+  for (int s = 0; s < nsys; ++s) f64[s] = fp64_sys_of(systems[s]);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_f64, sizeof(Fp64Sys) * nsys);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_f64, f64.data(), sizeof(Fp64Sys) * nsys, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_sys_n, 4 * nsys);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_sys_n, b->sys_n.data(), 4 * nsys, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->d_order, 4 * nsys);
@@ -558,6 +581,7 @@ hpt_status hpt_batch_destroy(hpt_batch b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   cudaFree(b->d_chunks);
   cudaFree(b->d_tab);
+  cudaFree(b->d_f64);
   cudaFree(b->d_sys_n);
   cudaFree(b->d_order);
   cudaFree(b->d_err);

@@ -17,33 +17,52 @@
 namespace hpt {
 namespace {
 
-template <int NMAX>
+// MAP: 32 consecutive positions of a position map per block (inside one
+// 128-position tile, so one system: S from the per-system table); otherwise
+// positions are the paths of the single system S.
+template <int NMAX, bool MAP>
 __global__ void __launch_bounds__(128)
-eval_fp64_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t* __restrict__ off,
-                 const double* __restrict__ ahat, const double2* __restrict__ bcol,
-                 const double2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
-                 double2* __restrict__ ext, double2* __restrict__ oH, double2* __restrict__ oHy,
-                 double2* __restrict__ oHt) {
+eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const double* __restrict__ tin,
+                 int tau_is_t, double2* __restrict__ ext, double2* __restrict__ oH, double2* __restrict__ oHy,
+                 double2* __restrict__ oHt, PathMap pm, const Fp64Sys* __restrict__ tab) {
   __shared__ double2 zs[NMAX][32];
   __shared__ double2 iys[NMAX][32];
   __shared__ double taus[32];
   __shared__ double tinv[32];
-  const int64_t base = (int64_t)blockIdx.x * 32;
+  __shared__ int64_t spath[32];
+  int64_t base = (int64_t)blockIdx.x * 32;
+  int nmax = S.n;
+  if (MAP) {
+    base += *pm.pos_begin;
+    if (base >= *pm.npos) return;
+    S = tab[pm.tile_sys[base >> 7]];
+    nmax = pm.nmax;
+  }
+  const int n = S.n;
+  const int32_t* __restrict__ msz = S.msz;
+  const int32_t* __restrict__ off = S.off;
+  const double* __restrict__ ahat = S.ahat;
+  const double2* __restrict__ bcol = S.b;
+  if (threadIdx.x < 32) {
+    const int64_t q = base + threadIdx.x;
+    spath[threadIdx.x] = MAP ? pm.list[q] : (q < p ? q : -1);
+  }
+  __syncthreads();
 
   // op. 1 of Algorithm 2: Z <- log Y (principal branch), and 1/y for the
   // final diag(e^{-z}) scaling.
   for (int idx = threadIdx.x; idx < 32 * n; idx += blockDim.x) {
     const int q = idx / n, j = idx - q * n;
-    const int64_t path = base + q;
+    const int64_t path = spath[q];
     double2 v = make_double2(1.0, 0.0);
-    if (path < p) v = y[path * n + j];
+    if (path >= 0) v = y[(MAP ? (size_t)pm.vofs[path] : (size_t)path * n) + j];
     const double r2 = v.x * v.x + v.y * v.y;
     zs[j][q] = make_double2(log(hypot(v.x, v.y)), atan2(v.y, v.x));
     iys[j][q] = make_double2(v.x / r2, -v.y / r2);
   }
   if (threadIdx.x < 32) {
-    const int64_t path = base + threadIdx.x;
-    double tv = (path < p && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);   // no tin: t = 1
+    const int64_t path = spath[threadIdx.x];
+    double tv = (path >= 0 && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);   // no tin: t = 1
     double tau = tau_is_t ? log(tv) : tv;
     taus[threadIdx.x] = tau;
     tinv[threadIdx.x] = tau_is_t ? 1.0 / tv : exp(-tau);
@@ -51,7 +70,8 @@ eval_fp64_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_
   __syncthreads();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t path = base + lane;
+  const int64_t path = spath[lane];
+  const int64_t pos = base + lane;
   const double tau = taus[lane];
   const int np2 = n + 2;
   for (int k = warp; k < n; k += 4) {
@@ -93,19 +113,19 @@ eval_fp64_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_
       accH.x = fma(er, ch.x, fma(-ei, ch.y, accH.x));
       accH.y = fma(er, ch.y, fma(ei, ch.x, accH.y));
     }
-    if (path >= p) continue;
+    if (path < 0) continue;
     // op. 3 of Algorithm 2: D_y h_k = D_z h_k diag(e^{-z})
     if (ext) {
 #pragma unroll
       for (int u = 0; u < NMAX; ++u) {
         if (u < n) {
           const double2 iy = iys[u][lane];
-          ext[ext_index(path, k, u, n)] =
+          ext[ext_index(pos, k, u, nmax)] =
               make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
         }
       }
-      ext[ext_index(path, k, n, n)] = accT;
-      ext[ext_index(path, k, n + 1, n)] = accH;
+      ext[ext_index(pos, k, n, nmax)] = accT;
+      ext[ext_index(pos, k, n + 1, nmax)] = accH;
     }
     if (oHy) {
       double2* row = oHy + ((size_t)path * n + k) * n;
@@ -127,6 +147,17 @@ eval_fp64_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_
 
 }  // namespace
 
+Fp64Sys fp64_sys_of(const hpt_system s) {
+  Fp64Sys f;
+  f.n = s->n;
+  f.pad_ = 0;
+  f.msz = s->d_msz;
+  f.off = s->d_off;
+  f.ahat = s->d_ahat;
+  f.b = (const double2*)s->d_b;
+  return f;
+}
+
 cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const double* tau,
                              int tau_is_t, const EvalOut& out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
@@ -138,14 +169,33 @@ cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const doubl
   double2* H = (double2*)out.H;
   double2* Hy = (double2*)out.Hy;
   double2* Ht = (double2*)out.Ht;
-  const double2* b = (const double2*)s->d_b;
+  const Fp64Sys f = fp64_sys_of(s);
+  const PathMap none;
   if (s->n <= 8)
-    eval_fp64_kernel<8><<<(unsigned)blocks, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, b, yy, tau, tau_is_t, ext, H, Hy, Ht);
+    eval_fp64_kernel<8, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   else if (s->n <= 16)
-    eval_fp64_kernel<16><<<(unsigned)blocks, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, b, yy, tau, tau_is_t, ext, H, Hy, Ht);
+    eval_fp64_kernel<16, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   else
-    eval_fp64_kernel<32><<<(unsigned)blocks, 128, 0, st>>>(s->n, p, s->d_msz, s->d_off, s->d_ahat, b, yy, tau, tau_is_t, ext, H, Hy, Ht);
+    eval_fp64_kernel<32, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   prof_end(s, pi, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_fp64_map(int shape, const Fp64Sys* tab, int64_t cap, const void* y, const double* tau,
+                                 const PathMap& pm, void* ext, cudaStream_t st) {
+  if (cap <= 0) return cudaSuccess;
+  if (!pm.list || !pm.tile_sys || !pm.vofs || !pm.npos || !pm.pos_begin || !tab) return cudaErrorInvalidValue;
+  const int64_t blocks = (cap + 31) / 32;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+  const Fp64Sys f{};
+  const double2* yy = (const double2*)y;
+  double2* e = (double2*)ext;
+  if (shape == 0)
+    eval_fp64_kernel<8, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
+  else if (shape == 1)
+    eval_fp64_kernel<16, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
+  else
+    eval_fp64_kernel<32, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
   return cudaGetLastError();
 }
 

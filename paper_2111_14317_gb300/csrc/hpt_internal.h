@@ -44,6 +44,15 @@ struct MixedSys {
   int64_t chunk_off;   // byte offset of the system's constant images
 };
 
+// One system's FP64 constants as the FP64 evaluation kernel reads them.
+struct Fp64Sys {
+  int n, pad_;
+  const int32_t* msz;
+  const int32_t* off;
+  const double* ahat;
+  const double2* b;
+};
+
 // Byte offset of element (r, k) of an R x K bf16 operand in the canonical
 // K-major no-swizzle layout used by the tensor-core descriptors: 8-row x
 // 16-byte core matrices, K-adjacent cores 128 bytes apart (leading byte
@@ -153,6 +162,13 @@ struct EvalOut {
 cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const double* tau,
                              int tau_is_t, const EvalOut& out, cudaStream_t st);
 
+Fp64Sys fp64_sys_of(const hpt_system s);
+// The same over the position range [*pm.pos_begin, *pm.npos) of a map whose
+// systems all have shape_of(n) == shape (tab: per-system constants); cap
+// bounds the range's length.  Writes the extended Jacobian (FP64) only.
+cudaError_t launch_eval_fp64_map(int shape, const Fp64Sys* tab, int64_t cap, const void* y, const double* tau,
+                                 const PathMap& pm, void* ext, cudaStream_t st);
+
 // Mixed tensor-core evaluation, complex64 in and out.
 cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const double* tau,
                               int tau_is_t, const EvalOut& out, cudaStream_t st);
@@ -188,6 +204,11 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
 // re-solves to a.redo_list (the caller zeroes a.redo_count once per step),
 // and the FP64 re-solve of the whole list with a shape that covers a.map.nmax.
 int solve_shape_of(int n);
+// FP64 Newton polish update over the position range [*pm.pos_begin,
+// *pm.npos) of a map (shape as above; cap bounds the range's length); x is
+// complex128 at pm.vofs, done per path.
+cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, int32_t* done, double tol,
+                              const PathMap& pm, cudaStream_t st);
 cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st);
 cudaError_t launch_redo_fp64_shape(int shape, const StepArgs& a, cudaStream_t st);
 

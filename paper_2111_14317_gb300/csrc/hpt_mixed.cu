@@ -142,10 +142,14 @@ constexpr int kEvalThreads = 256;   // two warpgroups over the 128 TMEM lanes
 
 // Barriers in shared memory: [0], [1] constant buffers; [2], [3] exponent
 // accumulators W[0], W[1]; [4] coefficient accumulator J.
+// MAP: positions come from a position map (many systems); otherwise position
+// = path of the single system described by P.sys.
+template <bool MAP>
 __global__ void __launch_bounds__(kEvalThreads, 2)
 eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
                   const uint8_t* __restrict__ chunks, float2* __restrict__ ext, float2* __restrict__ oH,
-                  float2* __restrict__ oHy, float2* __restrict__ oHt, int32_t* __restrict__ err, PathMap pm) {
+                  float2* __restrict__ oHy, float2* __restrict__ oHt, int32_t* __restrict__ err, PathMap pm_in) {
+  const PathMap pm = MAP ? pm_in : PathMap();   // null pointers fold away in the single-system form
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sAre = sm + P.s_are;
@@ -451,7 +455,9 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.nbuf = 1;
   }
   if (smem > max_smem) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(eval_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const bool map = pm.list != nullptr;
+  cudaError_t e = cudaFuncSetAttribute(map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // resident CTAs per SM are bounded by tensor memory (512 columns)
   const int max_per_sm = eval_mixed_max_ctas(tmem_cols);
@@ -460,9 +466,9 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) return cudaSuccess;
   int pi = prof_begin(prof, "eval_mixed_tc", st);
-  eval_mixed_kernel<<<(unsigned)grid, kEvalThreads, smem, st>>>(a, (const float2*)y, tin, tau_is_t, chunks,
-                                                               (float2*)out.ext, (float2*)out.H, (float2*)out.Hy,
-                                                               (float2*)out.Ht, err, pm);
+  auto kern = map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>;
+  kern<<<(unsigned)grid, kEvalThreads, smem, st>>>(a, (const float2*)y, tin, tau_is_t, chunks, (float2*)out.ext,
+                                                 (float2*)out.H, (float2*)out.Hy, (float2*)out.Ht, err, pm);
   prof_end(prof, pi, st);
   return cudaGetLastError();
 }

@@ -489,12 +489,39 @@ __device__ __forceinline__ int64_t pm_begin(const PathMap& m) { return m.pos_beg
 // control.  T is the state and solve precision.  FP32 solves whose pivot
 // ratio (after equilibration) exceeds prm.cond_max are not applied here: the
 // position goes to redo_list and is solved again in FP64 by redo_fp64_kernel.
-// Persistent: the warps loop over the positions (32/G consecutive positions
-// per warp, always inside one 128-position tile, so n is warp-uniform).
+// One system: G threads per path, a grid that covers every path once.
 template <typename T, int G, int R>
 __global__ void __launch_bounds__(kSolveThreads)
-solve_update_kernel(int n0, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
-                    int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list, PathMap pm) {
+solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
+                    int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & (G - 1);
+  const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int32_t status = path < p ? S.status[path] : -1;
+  const bool valid = status == HPT_PATH_ACTIVE;
+  if (!__any_sync(0xffffffffu, valid)) return;   // warp-uniform exit
+  const size_t vbase = (size_t)path * n;
+  PathRows<T, G, R> P;
+  const bool fin = load_rows<T, T, G, R>(n, n, ext, path, vbase, valid, false, nullptr, P);
+  cx<T> xE[R], xN[R];
+  T cond;
+  const bool ok =
+      group_solve<T, G, R>(n, P, xE, xN, cond, smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes) && fin;
+  if (!valid) return;   // group-uniform; only group-masked shuffles below
+  if (sizeof(T) == 4 && redo_list && ok && !(cond <= (T)prm.cond_max)) {
+    if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = path;
+    return;
+  }
+  update_path<T, G, R>(n, path, vbase, status, ok, xE, xN, S, prm);
+}
+
+// The same over a position map (many systems).  Persistent: the warps loop
+// over the positions of [*pos_begin, *npos) (32/G consecutive positions per
+// warp, always inside one 128-position tile, so n is warp-uniform).
+template <typename T, int G, int R>
+__global__ void __launch_bounds__(kSolveThreads)
+solve_update_map_kernel(int n0, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
+                        int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list, PathMap pm) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int per_warp = 32 / G;
   const int lane = threadIdx.x & (G - 1);
@@ -584,17 +611,26 @@ redo_fp64_kernel(int n0, const void* __restrict__ ext, hpt_paths S, hpt_params p
 }
 
 // Newton polish update at t = 1 (FP64): x += dN until |dN|/max(1,|x|) <= tol.
-template <int G, int R>
+// MAP: positions [*pm.pos_begin, *pm.npos) of a position map (a warp's
+// positions lie in one tile, so n is warp-uniform); otherwise the p paths of
+// one system.
+template <int G, int R, bool MAP>
 __global__ void __launch_bounds__(kSolveThreads)
-newton_kernel(int n, int64_t p, const void* __restrict__ ext, double2* __restrict__ x,
-              int32_t* __restrict__ done, double tol) {
+newton_kernel(int n0, int64_t p, const void* __restrict__ ext, double2* __restrict__ x,
+              int32_t* __restrict__ done, double tol, PathMap pm) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (G - 1);
-  const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const bool valid = path < p && done[path] == 0;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G + (MAP ? (int64_t)*pm.pos_begin : 0);
+  const int64_t end = MAP ? (int64_t)*pm.npos : p;
+  const bool in = q < end;
+  const int64_t path = in ? (MAP ? pm.list[q] : q) : -1;
+  const bool valid = path >= 0 && done[path] == 0;
   if (!__any_sync(0xffffffffu, valid)) return;
+  const int n = MAP ? pm.sys_n[pm.tile_sys[q >> 7]] : n0;
+  const size_t vbase = MAP ? (valid ? (size_t)pm.vofs[path] : 0) : (size_t)path * n;
   PathRows<double, G, R> P;
-  const bool fin = load_rows<double, double, G, R>(n, n, ext, path, (size_t)path * n, valid, false, nullptr, P);
+  const bool fin =
+      load_rows<double, double, G, R>(n, MAP ? pm.nmax : n, ext, q, vbase, valid, false, nullptr, P);
   cx<double> xE[R], xN[R];
   double cond;
   const bool ok =
@@ -608,7 +644,7 @@ newton_kernel(int n, int64_t p, const void* __restrict__ ext, double2* __restric
 #pragma unroll
   for (int s = 0; s < R; ++s) {
     const int j = lane + G * s;
-    y[s] = j < n ? ld<double>(x, (size_t)path * n + j) : mk<double>(0, 0);
+    y[s] = j < n ? ld<double>(x, vbase + j) : mk<double>(0, 0);
     if (j < n) {
       sfin = sfin && finite(xN[s]);
       y[s] = mk<double>(y[s].x + xN[s].x, y[s].y + xN[s].y);
@@ -629,7 +665,7 @@ newton_kernel(int n, int64_t p, const void* __restrict__ ext, double2* __restric
 #pragma unroll
   for (int s = 0; s < R; ++s) {
     const int j = lane + G * s;
-    if (j < n) st<double>(x, (size_t)path * n + j, y[s]);
+    if (j < n) st<double>(x, vbase + j, y[s]);
   }
   if (lane == 0 && nd / fmax(1.0, ny) <= tol) done[path] = 1;
 }
@@ -787,12 +823,19 @@ inline unsigned solve_grid(int64_t p, int G) {
 template <typename T, int G, int R>
 cudaError_t launch_solve_shape(const StepArgs& a, int32_t* rc, int64_t* rl, cudaStream_t st) {
   const int smem = (kSolveThreads / G) * GroupSmem<T, G * R>::bytes;
-  cudaError_t e = set_smem(solve_update_kernel<T, G, R>, smem);
+  if (!a.map.list) {
+    cudaError_t e = set_smem(solve_update_kernel<T, G, R>, smem);
+    if (e != cudaSuccess) return e;
+    solve_update_kernel<T, G, R><<<blocks_for(a.p * G, kSolveThreads), kSolveThreads, smem, st>>>(
+        a.n, a.p, a.ext, a.st, a.prm, rc, rl);
+    return cudaGetLastError();
+  }
+  cudaError_t e = set_smem(solve_update_map_kernel<T, G, R>, smem);
   if (e != cudaSuccess) return e;
   PathMap pm = a.map;
   if (!pm.nmax) pm.nmax = a.n;
-  solve_update_kernel<T, G, R><<<solve_grid(a.p, G), kSolveThreads, smem, st>>>(a.n, a.p, a.ext, a.st, a.prm, rc,
-                                                                                 rl, pm);
+  solve_update_map_kernel<T, G, R><<<solve_grid(a.p, G), kSolveThreads, smem, st>>>(a.n, a.p, a.ext, a.st, a.prm,
+                                                                                     rc, rl, pm);
   return cudaGetLastError();
 }
 
@@ -810,12 +853,19 @@ cudaError_t launch_redo_shape(const StepArgs& a, cudaStream_t st) {
 
 template <int G, int R>
 cudaError_t launch_newton_shape(int n, int64_t p, const void* ext, void* x, int32_t* done, double tol,
-                                cudaStream_t st) {
+                                const PathMap* pm, cudaStream_t st) {
   const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
-  cudaError_t e = set_smem(newton_kernel<G, R>, smem);
+  if (pm) {
+    cudaError_t e = set_smem(newton_kernel<G, R, true>, smem);
+    if (e != cudaSuccess) return e;
+    newton_kernel<G, R, true><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(
+        n, p, ext, (double2*)x, done, tol, *pm);
+    return cudaGetLastError();
+  }
+  cudaError_t e = set_smem(newton_kernel<G, R, false>, smem);
   if (e != cudaSuccess) return e;
-  newton_kernel<G, R><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(n, p, ext, (double2*)x,
-                                                                                      done, tol);
+  newton_kernel<G, R, false><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(
+      n, p, ext, (double2*)x, done, tol, PathMap());
   return cudaGetLastError();
 }
 
@@ -864,6 +914,15 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
 
 int solve_shape_of(int n) { return shape_of(n); }
 
+cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, int32_t* done, double tol,
+                              const PathMap& pm, cudaStream_t st) {
+  if (cap <= 0) return cudaSuccess;
+  if (!pm.list || !pm.tile_sys || !pm.sys_n || !pm.vofs || !pm.npos || !pm.pos_begin) return cudaErrorInvalidValue;
+  return shape == 0 ? launch_newton_shape<8, 1>(0, cap, ext, x, done, tol, &pm, st)
+       : shape == 1 ? launch_newton_shape<8, 2>(0, cap, ext, x, done, tol, &pm, st)
+                    : launch_newton_shape<32, 1>(0, cap, ext, x, done, tol, &pm, st);
+}
+
 cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st) {
   if (a.p <= 0) return cudaSuccess;
   return shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
@@ -883,9 +942,9 @@ cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void*
   if (p <= 0) return cudaSuccess;
   const int shape = shape_of(s->n);
   int pi = prof_begin(s, "newton_fp64", st);
-  cudaError_t e = shape == 0 ? launch_newton_shape<8, 1>(s->n, p, ext, x, done, tol, st)
-                : shape == 1 ? launch_newton_shape<8, 2>(s->n, p, ext, x, done, tol, st)
-                             : launch_newton_shape<32, 1>(s->n, p, ext, x, done, tol, st);
+  cudaError_t e = shape == 0 ? launch_newton_shape<8, 1>(s->n, p, ext, x, done, tol, nullptr, st)
+                : shape == 1 ? launch_newton_shape<8, 2>(s->n, p, ext, x, done, tol, nullptr, st)
+                             : launch_newton_shape<32, 1>(s->n, p, ext, x, done, tol, nullptr, st);
   prof_end(s, pi, st);
   return e;
 }
