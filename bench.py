@@ -307,8 +307,8 @@ def run_batch(args, dev):
         "lane_efficiency": total_steps / max(stats["position_steps"], 1),
         "rounds": stats["rounds"], "kernels_per_round": stats["kernels_per_round"],
         "gpu_launches_rounds": stats["rounds"] * stats["kernels_per_round"],
-        "tuning": {"steps_per_round": best[0], "eval_ctas_per_sm": best[1],
-                   "candidates_ms": {f"K={k},ctas={c}": v for (k, c), v in cand.items()}},
+        "tuning": {"steps_per_round": best[0], "eval_ctas_per_sm": best[1], "solve_lanes_n17_24": best[2],
+                   "candidates_ms": {f"K={k},ctas={c},lanes={ln}": v for (k, c, ln), v in cand.items()}},
         "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st_n, return_counts=True))},
         "steps_per_path": {"min": int(conv.min()) if conv.size else None,
                            "median": float(np.median(conv)) if conv.size else None,

@@ -298,6 +298,8 @@ typedef struct hpt_batch_s* hpt_batch;
 typedef struct {
   int32_t steps_per_round;    /* K: steps between compactions (1..256) */
   int32_t eval_ctas_per_sm;   /* resident evaluation CTAs per SM: 1 or 2 (capped by tensor memory) */
+  int32_t solve_lanes_n17_24; /* FP32 solve of systems with 17 <= n <= 24: 8 lanes x 3 rows or
+                                 32 lanes x 1 row per path (8 or 32) */
 } hpt_batch_tuning;
 
 /* Groups nsys (>= 1) HPT_MIXED system handles of the current device (their
@@ -320,11 +322,13 @@ hpt_status hpt_batch_set_tuning(hpt_batch b, const hpt_batch_tuning* t);
 hpt_status hpt_batch_track(hpt_batch b, const int64_t* paths, const void* y0, const hpt_params* prm,
                            void* x_out, int32_t* status_out, int32_t* steps_out, void* stream);
 
-/* The project's autotuner: runs hpt_batch_track once per candidate tuning
- * (K in {4, 8, 16, 32} x eval CTAs/SM in {1, 2} where 2 fits) on the given
- * problem and keeps the fastest as the batch's tuning.  Writes the chosen
- * tuning to *best, and, where not NULL, each candidate's tuning and
- * milliseconds to cand[] / ms[] (capacity *ncand in, count out). */
+/* The project's autotuner: times whole hpt_batch_track calls on the given
+ * problem, one knob at a time from the current tuning (coordinate descent):
+ * the mid-size solve shape (8 or 32 lanes), then eval CTAs/SM (1, 2 where
+ * tensor memory allows), then K in {4, 8, 16, 32}; keeps the fastest as the
+ * batch's tuning.  Writes the chosen tuning to *best, and, where not NULL,
+ * each timed candidate's tuning and milliseconds to cand[] / ms[] (capacity
+ * *ncand in, count out). */
 hpt_status hpt_batch_autotune(hpt_batch b, const int64_t* paths, const void* y0, const hpt_params* prm,
                               void* x_out, void* stream, hpt_batch_tuning* best, hpt_batch_tuning* cand,
                               double* ms, int32_t* ncand);

@@ -7,7 +7,7 @@
 // offset of the first one).  A position list names the live paths, padded per
 // system to whole 128-position tiles (entry -1 = padding), so every tile
 // belongs to one system (tile_sys).  Systems are ordered by lane-group shape
-// bucket (n <= 8, <= 16, <= 32), inside a bucket by decreasing evaluation
+// bucket (n <= 8, <= 16, <= 24, <= 32), inside a bucket by decreasing evaluation
 // cost, so each solve launch covers one contiguous position range and the
 // evaluation kernel's round-robin tile walk meets the large tiles first.
 //
@@ -26,11 +26,13 @@
 #include "hpt_internal.h"
 
 namespace hpt {
+constexpr int kBuckets = 4;   // n <= 8, <= 16, <= 24, <= 32
+inline int bucket_of(int n) { return n <= 8 ? 0 : (n <= 16 ? 1 : (n <= 24 ? 2 : 3)); }
 // Order indices of the first and last system of each shape bucket (-1: the
 // bucket is empty); order is sorted by bucket, so a bucket's tiles are one
 // contiguous range.
 struct BucketSpan {
-  int first[3], last[3];
+  int first[kBuckets], last[kBuckets];
 };
 }  // namespace hpt
 
@@ -42,7 +44,7 @@ struct hpt_batch_s {
   std::vector<int> bucket;        // lane-group shape of each system
   std::vector<int32_t> order;     // systems in position order
   hpt::BucketSpan span{};
-  hpt::MixedSys maxs{};
+  hpt::MixedSys maxs{};   // the largest of each operand dimension
   int tmem_cols = 0;
   int nmax = 0;
   int redo_shape = 0;
@@ -67,10 +69,10 @@ struct hpt_batch_s {
   cudaGraphExec_t exec = nullptr;
   void* key_state = nullptr;
   std::vector<int64_t> key_paths;
-  hpt_batch_tuning key_tune{0, 0};
+  hpt_batch_tuning key_tune{0, 0, 0};
   hpt_params key_prm{};
 
-  hpt_batch_tuning tune{16, 2};
+  hpt_batch_tuning tune{16, 2, 8};
   int64_t rounds = 0, position_steps = 0;
   int32_t kernels_per_round = 0;
 };
@@ -78,7 +80,8 @@ struct hpt_batch_s {
 namespace hpt {
 namespace {
 
-constexpr int kCtlWords = 8;   // [0] positions, [1..3] bucket begins, [4..6] bucket ends
+// control words: [0] positions, [1 + b] bucket b's first position, [1 + kBuckets + b] its end
+constexpr int kCtlWords = 2 + 2 * kBuckets;
 
 // One block per system: the system's live paths (flag == want) in order,
 // into tmp at the system's own path range; cnt[s] = their number.
@@ -134,7 +137,7 @@ __global__ void compact_scan_kernel(int nsys, const int32_t* __restrict__ order,
     run += (cnt[s] + 127) / 128;
   }
   __syncthreads();
-  if (t < 3) {
+  if (t < kBuckets) {
     int begin = 0, end = 0;
     if (bs.first[t] >= 0) {
       const int sf = order[bs.first[t]], sl = order[bs.last[t]];
@@ -142,7 +145,7 @@ __global__ void compact_scan_kernel(int nsys, const int32_t* __restrict__ order,
       end = tile_base[sl] + (cnt[sl] + 127) / 128;
     }
     ctl[1 + t] = begin * 128;
-    ctl[4 + t] = end * 128;
+    ctl[1 + kBuckets + t] = end * 128;
   }
   if (t == 0) ctl[0] = part[1023] * 128;
 }
@@ -170,7 +173,7 @@ struct Problem {
   std::vector<int64_t> pb, vb;   // path and variable offsets per system
   int64_t P = 0, V = 0;          // paths, variables
   int64_t cap = 0;               // list capacity (positions)
-  int64_t cap_bucket[3] = {0, 0, 0};
+  int64_t cap_bucket[kBuckets] = {0, 0, 0, 0};
   int64_t pmax = 0;              // largest paths[s]
   // byte offsets in d_state
   size_t o_y, o_ya, o_de, o_tau, o_dt, o_ta, o_st, o_sp, o_ac, o_rj, o_sk, o_done, o_vofs, o_pb, o_np, o_tmp,
@@ -277,6 +280,15 @@ cudaError_t enqueue_compaction(const hpt_batch_s* b, const Problem& q, const int
   return cudaGetLastError();
 }
 
+// FP32 solve shape of bucket bk: 8-lane groups with 1, 2 or 3 rows per lane
+// (n <= 8, 16, 24) or 32-lane groups; the n <= 24 bucket takes 32-lane
+// groups instead when the tuning says so.
+int fp32_shape(const hpt_batch_s* b, int bk) {
+  if (bk < 2) return bk;
+  if (bk == 2) return b->tune.solve_lanes_n17_24 == 8 ? kShape8x3 : 2;
+  return 2;
+}
+
 // K steps and the compaction on st (captured by the caller).
 cudaError_t enqueue_round(hpt_batch_s* b, const Problem& q, const hpt_params& prm, cudaStream_t st,
                           int32_t* kernels) {
@@ -307,13 +319,13 @@ cudaError_t enqueue_round(hpt_batch_s* b, const Problem& q, const hpt_params& pr
     a.err = b->d_err;
     a.redo_count = (int32_t*)(d + q.o_rc);
     a.redo_list = (int64_t*)(d + q.o_rl);
-    for (int sh = 0; sh < 3 && e == cudaSuccess; ++sh) {
-      if (!q.cap_bucket[sh]) continue;
-      a.p = q.cap_bucket[sh];
+    for (int bk = 0; bk < kBuckets && e == cudaSuccess; ++bk) {
+      if (!q.cap_bucket[bk]) continue;
+      a.p = q.cap_bucket[bk];
       a.map = pm;
-      a.map.pos_begin = ctl + 1 + sh;
-      a.map.npos = ctl + 4 + sh;
-      e = launch_solve_fp32_shape(sh, a, st);
+      a.map.pos_begin = ctl + 1 + bk;
+      a.map.npos = ctl + 1 + kBuckets + bk;
+      e = launch_solve_fp32_shape(fp32_shape(b, bk), a, st);
       ++nk;
     }
     if (e != cudaSuccess) break;
@@ -382,8 +394,7 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
   // parameters changed (it holds them as launch arguments)
   const std::vector<int64_t> key(paths, paths + b->nsys);
   if (!b->exec || b->key_state != b->d_state || b->key_paths != key ||
-      b->key_tune.steps_per_round != b->tune.steps_per_round ||
-      b->key_tune.eval_ctas_per_sm != b->tune.eval_ctas_per_sm || !same_prm(b->key_prm, prm)) {
+      memcmp(&b->key_tune, &b->tune, sizeof(hpt_batch_tuning)) != 0 || !same_prm(b->key_prm, prm)) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -441,13 +452,14 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "batch polish compaction");
     if (b->h_ctl[0] == 0) break;
-    for (int sh = 0; sh < 3 && e == cudaSuccess; ++sh) {
-      if (!q.cap_bucket[sh]) continue;
-      pm.pos_begin = ctl + 1 + sh;
-      pm.npos = ctl + 4 + sh;
-      e = launch_eval_fp64_map(sh, b->d_f64, q.cap_bucket[sh], x_out, nullptr, pm, d + q.o_ext, st);
+    for (int bk = 0; bk < kBuckets && e == cudaSuccess; ++bk) {
+      if (!q.cap_bucket[bk]) continue;
+      pm.pos_begin = ctl + 1 + bk;
+      pm.npos = ctl + 1 + kBuckets + bk;
+      const int sh = bk < 2 ? bk : 2;   // FP64: n <= 8, <= 16, <= 32 lane groups
+      e = launch_eval_fp64_map(sh, b->d_f64, q.cap_bucket[bk], x_out, nullptr, pm, d + q.o_ext, st);
       if (e == cudaSuccess)
-        e = launch_newton_map(sh, q.cap_bucket[sh], d + q.o_ext, x_out, done, prm.polish_tol, pm, st);
+        e = launch_newton_map(sh, q.cap_bucket[bk], d + q.o_ext, x_out, done, prm.polish_tol, pm, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batch polish");
   }
@@ -517,7 +529,7 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
     tab[s].chunk_off = chunk_total;
     chunk_total += (int64_t)h->n * h->ml.chunk_bytes;
     b->sys_n.push_back(h->n);
-    b->bucket.push_back(solve_shape_of(h->n));
+    b->bucket.push_back(bucket_of(h->n));
     mx.n = std::max(mx.n, h->n);
     mx.MP = std::max(mx.MP, h->ml.MP);
     mx.KX = std::max(mx.KX, h->ml.KX);
@@ -525,10 +537,10 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
     mx.KC = std::max(mx.KC, h->ml.KC);
     mx.chunk_bytes = std::max(mx.chunk_bytes, h->ml.chunk_bytes);
     b->tmem_cols = std::max(b->tmem_cols, h->ml.tmem_cols);
+    b->nmax = std::max(b->nmax, h->n);
     // evaluation work of one tile: n equations x (exponent + coefficient GEMM + exp)
     cost[s] = (double)h->n * (h->ml.MP * (double)h->ml.KX + 3.0 * h->ml.NJ * h->ml.KC + 8.0 * h->ml.MP);
   }
-  b->nmax = mx.n;
   b->redo_shape = solve_shape_of(b->nmax);
   b->order.resize(nsys);
   std::iota(b->order.begin(), b->order.end(), 0);
@@ -536,7 +548,7 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
     if (b->bucket[x] != b->bucket[y]) return b->bucket[x] < b->bucket[y];
     return cost[x] > cost[y];
   });
-  for (int k = 0; k < 3; ++k) b->span.first[k] = b->span.last[k] = -1;
+  for (int k = 0; k < kBuckets; ++k) b->span.first[k] = b->span.last[k] = -1;
   for (int i = 0; i < nsys; ++i) {
     const int k = b->bucket[b->order[i]];
     if (b->span.first[k] < 0) b->span.first[k] = i;
@@ -603,7 +615,8 @@ hpt_status hpt_batch_get_tuning(hpt_batch b, hpt_batch_tuning* t) {
 
 hpt_status hpt_batch_set_tuning(hpt_batch b, const hpt_batch_tuning* t) {
   if (!b || !t) { set_error("NULL argument"); return HPT_EINVAL; }
-  if (t->steps_per_round < 1 || t->steps_per_round > 256 || t->eval_ctas_per_sm < 1 || t->eval_ctas_per_sm > 2) {
+  if (t->steps_per_round < 1 || t->steps_per_round > 256 || t->eval_ctas_per_sm < 1 || t->eval_ctas_per_sm > 2 ||
+      (t->solve_lanes_n17_24 != 8 && t->solve_lanes_n17_24 != 32)) {
     set_error("tuning out of range");
     return HPT_EINVAL;
   }
@@ -629,28 +642,44 @@ hpt_status hpt_batch_autotune(hpt_batch b, const int64_t* paths, const void* y0,
   if ((rc = check_params(prm))) return rc;
   if ((rc = check_paths(b, paths, y0, x_out))) return rc;
   const int cap = ncand ? *ncand : 0;
-  const int max_ctas = eval_mixed_max_ctas(b->tmem_cols);
-  const int Ks[4] = {4, 8, 16, 32};
-  const hpt_batch_tuning saved = b->tune;
-  hpt_batch_tuning win = saved;
-  double win_ms = -1;
   int count = 0;
-  for (int c = 1; c <= max_ctas; ++c)
-    for (int K : Ks) {
-      b->tune.steps_per_round = K;
-      b->tune.eval_ctas_per_sm = c;
-      const auto t0 = std::chrono::steady_clock::now();
-      rc = track_impl(b, paths, y0, *prm, x_out, nullptr, nullptr, (cudaStream_t)stream);
-      const auto t1 = std::chrono::steady_clock::now();
-      if (rc) { b->tune = saved; return rc; }
-      const double t = std::chrono::duration<double, std::milli>(t1 - t0).count();
-      if (count < cap) {
-        if (cand) cand[count] = b->tune;
-        if (ms) ms[count] = t;
-      }
-      ++count;
-      if (win_ms < 0 || t < win_ms) { win_ms = t; win = b->tune; }
+  hpt_batch_tuning win = b->tune;
+  double win_ms = -1;
+  // times one candidate; keeps it if it is the fastest so far
+  auto trial = [&](const hpt_batch_tuning& t) -> hpt_status {
+    b->tune = t;
+    const auto t0 = std::chrono::steady_clock::now();
+    hpt_status r = track_impl(b, paths, y0, *prm, x_out, nullptr, nullptr, (cudaStream_t)stream);
+    const auto t1 = std::chrono::steady_clock::now();
+    if (r) return r;
+    const double el = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (count < cap) {
+      if (cand) cand[count] = t;
+      if (ms) ms[count] = el;
     }
+    ++count;
+    if (win_ms < 0 || el < win_ms) { win_ms = el; win = t; }
+    return HPT_OK;
+  };
+  const hpt_batch_tuning start = b->tune;
+  const int max_ctas = eval_mixed_max_ctas(b->tmem_cols);
+  hpt_batch_tuning t = start;
+  for (int lanes : {8, 32}) {
+    t.solve_lanes_n17_24 = lanes;
+    if ((rc = trial(t))) { b->tune = start; return rc; }
+  }
+  t = win;
+  for (int c = 1; c <= max_ctas; ++c) {
+    if (c == win.eval_ctas_per_sm) continue;
+    t.eval_ctas_per_sm = c;
+    if ((rc = trial(t))) { b->tune = start; return rc; }
+  }
+  t = win;
+  for (int K : {4, 8, 16, 32}) {
+    if (K == win.steps_per_round) continue;
+    t.steps_per_round = K;
+    if ((rc = trial(t))) { b->tune = start; return rc; }
+  }
   b->tune = win;
   if (best) *best = win;
   if (ncand) *ncand = std::min(count, cap);

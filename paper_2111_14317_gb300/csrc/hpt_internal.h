@@ -176,7 +176,7 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
 // system, chunks holds every system's constant images, maxs the largest of
 // each operand dimension (it sizes shared memory; maxs.n = pm.nmax) and
 // tmem_cols the largest tensor-memory need.  p bounds the positions;
-// ctas_per_sm 0 picks the default.  Writes the extended Jacobian only.
+// ctas_per_sm 0 picks the most that fit.  Writes the extended Jacobian only.
 cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tmem_cols, const uint8_t* chunks,
                                   int64_t p, const void* y, const double* tau, const PathMap& pm, void* ext,
                                   int32_t* err, int ctas_per_sm, cudaStream_t st);
@@ -202,8 +202,10 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
 // Many-systems pieces of the mixed step: the FP32 solve of one lane-group
 // shape (shape_of(n)) over the map's position range, appending FP64
 // re-solves to a.redo_list (the caller zeroes a.redo_count once per step),
-// and the FP64 re-solve of the whole list with a shape that covers a.map.nmax.
+// and the FP64 re-solve of the whole list with a shape that covers a.map.nmax
+// (shapes: 0, 1, 2 as solve_shape_of, kShape8x3 for the FP32 solve).
 int solve_shape_of(int n);
+constexpr int kShape8x3 = 3;   // FP32 solve only: 8 lanes x 3 rows per path, n <= 24
 // FP64 Newton polish update over the position range [*pm.pos_begin,
 // *pm.npos) of a map (shape as above; cap bounds the range's length); x is
 // complex128 at pm.vofs, done per path.

@@ -459,8 +459,17 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
   cudaError_t e = cudaFuncSetAttribute(map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  // resident CTAs per SM are bounded by tensor memory (512 columns)
-  const int max_per_sm = eval_mixed_max_ctas(tmem_cols);
+  // resident CTAs per SM are bounded by tensor memory (512 columns) and by
+  // shared memory: a persistent grid larger than what is resident would run
+  // in two waves
+  int max_per_sm = eval_mixed_max_ctas(tmem_cols);
+  {
+    int dev = 0, sm_total = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int fit = sm_total / (smem + 1024);   // 1 KB per CTA is reserved by the system
+    if (fit < max_per_sm) max_per_sm = fit < 1 ? 1 : fit;
+  }
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, max_per_sm) : max_per_sm;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > ntiles) grid = ntiles;
@@ -508,7 +517,7 @@ cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tme
                                   int64_t p, const void* y, const double* tau, const PathMap& pm, void* ext,
                                   int32_t* err, int ctas_per_sm, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
-  if (!pm.list || !pm.tile_sys || !pm.vofs || !pm.npos || !pm.sys_tab || pm.nmax != maxs.n)
+  if (!pm.list || !pm.tile_sys || !pm.vofs || !pm.npos || !pm.sys_tab || maxs.n != pm.nmax)
     return cudaErrorInvalidValue;
   EvalOut out;
   out.ext = ext;

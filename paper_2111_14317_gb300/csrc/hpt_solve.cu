@@ -200,6 +200,59 @@ __device__ __forceinline__ bool load_rows(int n, int nmax, const void* ext, int6
   return (ball & seg) == seg;
 }
 
+// 32-lane groups (one path per warp) would load every entry of the
+// position-interleaved scratch from its own 32-byte sector.  Instead the
+// block's four paths (consecutive positions q0..q0+3 of one tile, so one n)
+// are staged cooperatively: four threads read the same entry of the four
+// paths, one sector, and write it to the path's group region in shared memory
+// as rows of kStageLD entries (odd, so the row reads below hit distinct
+// banks).  Only paths with act set are read.  Call with every thread of the
+// block between two block barriers.
+constexpr int kStageLD = 35;
+template <typename S>
+__device__ __forceinline__ void stage_block_rows(int n, int nmax, const void* __restrict__ ext, int64_t q0, bool act,
+                                                 unsigned char* smem, int region_bytes) {
+  if (!act) return;   // act: path (threadIdx.x & 3) of the block is to be solved
+  typedef typename cplx_t<S>::type V;
+  const int i = threadIdx.x & 3;
+  V* region = (V*)(smem + i * region_bytes);
+  const int np2 = n + 2, total = n * np2;
+  for (int e = threadIdx.x >> 2; e < total; e += 32) {
+    const int k = e / np2, u = e - k * np2;
+    region[k * kStageLD + u] = ((const V*)ext)[ext_index(q0 + i, k, u, nmax)];
+  }
+}
+
+// load_rows for a 32-lane group from its staged region (lane r = row r).
+template <typename T, typename S>
+__device__ __forceinline__ bool load_rows_staged(int n, const unsigned char* region, bool valid,
+                                                 PathRows<T, 32, 1>& P) {
+  typedef typename cplx_t<S>::type V;
+  const V* rg = (const V*)region;
+  const int r = threadIdx.x & 31;
+  const bool have = valid && r < n;
+  T chk = T(0);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    P.a[0][c] = mk<T>(0, 0);
+    if (have && c < n) {
+      const V v = rg[r * kStageLD + c];
+      P.a[0][c] = mk<T>((T)v.x, (T)v.y);
+      chk += t_abs(P.a[0][c].x) + t_abs(P.a[0][c].y);
+    }
+  }
+  P.bE[0] = mk<T>(0, 0);
+  P.bN[0] = mk<T>(0, 0);
+  if (have) {
+    const V ht = rg[r * kStageLD + n], h = rg[r * kStageLD + n + 1];
+    P.bE[0] = mk<T>(-(T)ht.x, -(T)ht.y);
+    P.bN[0] = mk<T>(-(T)h.x, -(T)h.y);
+    chk += t_abs(P.bE[0].x) + t_abs(P.bE[0].y) + t_abs(P.bN[0].x) + t_abs(P.bN[0].y);
+  }
+  __syncwarp();   // every row is in registers before the solve writes U over the region
+  return __all_sync(0xffffffffu, isfinite(chk));
+}
+
 // Solves the path held in P (n <= G R) with equilibration and partial
 // pivoting.  Returns false (group-uniform) when a pivot is zero or not
 // finite; cond receives max |u_jj| / min |u_jj|.  On return lane l holds
@@ -499,14 +552,22 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
   const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int32_t status = path < p ? S.status[path] : -1;
   const bool valid = status == HPT_PATH_ACTIVE;
+  unsigned char* sm = smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes;
+  if (G == 32) {   // block-uniform: stage the block's four paths
+    const int64_t q0 = (int64_t)blockIdx.x * (kSolveThreads / 32);
+    const int64_t qi = q0 + (threadIdx.x & 3);
+    stage_block_rows<T>(n, n, ext, q0, qi < p && S.status[qi] == HPT_PATH_ACTIVE, smem, GroupSmem<T, G * R>::bytes);
+    __syncthreads();
+  }
   if (!__any_sync(0xffffffffu, valid)) return;   // warp-uniform exit
   const size_t vbase = (size_t)path * n;
   PathRows<T, G, R> P;
-  const bool fin = load_rows<T, T, G, R>(n, n, ext, path, vbase, valid, false, nullptr, P);
+  bool fin;
+  if constexpr (G == 32) fin = load_rows_staged<T, T>(n, sm, valid, P);
+  else fin = load_rows<T, T, G, R>(n, n, ext, path, vbase, valid, false, nullptr, P);
   cx<T> xE[R], xN[R];
   T cond;
-  const bool ok =
-      group_solve<T, G, R>(n, P, xE, xN, cond, smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes) && fin;
+  const bool ok = group_solve<T, G, R>(n, P, xE, xN, cond, sm) && fin;
   if (!valid) return;   // group-uniform; only group-masked shuffles below
   if (sizeof(T) == 4 && redo_list && ok && !(cond <= (T)prm.cond_max)) {
     if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = path;
@@ -531,16 +592,29 @@ solve_update_map_kernel(int n0, int64_t p, const void* __restrict__ ext, hpt_pat
   unsigned char* sm = smem + (threadIdx.x / G) * GroupSmem<T, G * R>::bytes;
   const int64_t npos = pm_count(pm, p);
   const int nmax = pm.nmax;
+  // with 32-lane groups the block's four warps take consecutive positions of
+  // one tile and run the same number of iterations (npos is a multiple of
+  // 128), so the staging barriers below are reached by the whole block
   for (int64_t base = pm_begin(pm) + warp_id * per_warp; base < npos; base += nwarps * per_warp) {
     const int64_t q = base + g;
     const int n = pm_n(pm, base, n0);
     const int64_t path = q < npos ? pm_path(pm, q) : -1;
     const int32_t status = path >= 0 ? S.status[path] : -1;
     const bool valid = status == HPT_PATH_ACTIVE;
+    if (G == 32) {
+      const int64_t q0 = base - (threadIdx.x >> 5);
+      const int64_t pi = pm_path(pm, q0 + (threadIdx.x & 3));
+      __syncthreads();   // the previous iteration's solves are done with the regions
+      stage_block_rows<T>(n, nmax, ext, q0, pi >= 0 && S.status[pi] == HPT_PATH_ACTIVE, smem,
+                          GroupSmem<T, G * R>::bytes);
+      __syncthreads();
+    }
     if (!__any_sync(0xffffffffu, valid)) continue;   // warp-uniform skip
     const size_t vbase = valid ? pm_vbase(pm, path, n) : 0;
     PathRows<T, G, R> P;
-    const bool fin = load_rows<T, T, G, R>(n, nmax, ext, q, vbase, valid, false, nullptr, P);
+    bool fin;
+    if constexpr (G == 32) fin = load_rows_staged<T, T>(n, sm, valid, P);
+    else fin = load_rows<T, T, G, R>(n, nmax, ext, q, vbase, valid, false, nullptr, P);
     cx<T> xE[R], xN[R];
     T cond;
     const bool ok = group_solve<T, G, R>(n, P, xE, xN, cond, sm) && fin;
@@ -625,17 +699,27 @@ newton_kernel(int n0, int64_t p, const void* __restrict__ ext, double2* __restri
   const bool in = q < end;
   const int64_t path = in ? (MAP ? pm.list[q] : q) : -1;
   const bool valid = path >= 0 && done[path] == 0;
+  unsigned char* sm = smem + (threadIdx.x / G) * GroupSmem<double, G * R>::bytes;
+  if (G == 32) {   // block-uniform: stage the block's four positions
+    const int64_t q0 = q - (threadIdx.x >> 5);
+    if (q0 >= end) return;   // the whole block (end is a multiple of 4)
+    const int n = MAP ? pm.sys_n[pm.tile_sys[q0 >> 7]] : n0;
+    const int64_t qi = q0 + (threadIdx.x & 3);
+    const int64_t pi = qi < end ? (MAP ? pm.list[qi] : qi) : -1;
+    stage_block_rows<double>(n, MAP ? pm.nmax : n, ext, q0, pi >= 0 && done[pi] == 0, smem,
+                             GroupSmem<double, G * R>::bytes);
+    __syncthreads();
+  }
   if (!__any_sync(0xffffffffu, valid)) return;
   const int n = MAP ? pm.sys_n[pm.tile_sys[q >> 7]] : n0;
   const size_t vbase = MAP ? (valid ? (size_t)pm.vofs[path] : 0) : (size_t)path * n;
   PathRows<double, G, R> P;
-  const bool fin =
-      load_rows<double, double, G, R>(n, MAP ? pm.nmax : n, ext, q, vbase, valid, false, nullptr, P);
+  bool fin;
+  if constexpr (G == 32) fin = load_rows_staged<double, double>(n, sm, valid, P);
+  else fin = load_rows<double, double, G, R>(n, MAP ? pm.nmax : n, ext, q, vbase, valid, false, nullptr, P);
   cx<double> xE[R], xN[R];
   double cond;
-  const bool ok =
-      group_solve<double, G, R>(n, P, xE, xN, cond, smem + (threadIdx.x / G) * GroupSmem<double, G * R>::bytes) &&
-      fin;
+  const bool ok = group_solve<double, G, R>(n, P, xE, xN, cond, sm) && fin;
   if (!valid) return;
   const unsigned gmask = group_mask<G>();
   bool sfin = true;
@@ -927,6 +1011,7 @@ cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t s
   if (a.p <= 0) return cudaSuccess;
   return shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
        : shape == 1 ? launch_solve_shape<float, 8, 2>(a, a.redo_count, a.redo_list, st)
+       : shape == kShape8x3 ? launch_solve_shape<float, 8, 3>(a, a.redo_count, a.redo_list, st)
                     : launch_solve_shape<float, 32, 1>(a, a.redo_count, a.redo_list, st);
 }
 

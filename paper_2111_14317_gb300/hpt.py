@@ -73,10 +73,11 @@ class _Paths(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     """hpt_batch_tuning."""
-    _fields_ = [("steps_per_round", ctypes.c_int32), ("eval_ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("steps_per_round", ctypes.c_int32), ("eval_ctas_per_sm", ctypes.c_int32),
+                ("solve_lanes_n17_24", ctypes.c_int32)]
 
     def as_tuple(self):
-        return (int(self.steps_per_round), int(self.eval_ctas_per_sm))
+        return (int(self.steps_per_round), int(self.eval_ctas_per_sm), int(self.solve_lanes_n17_24))
 
 
 _VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
@@ -396,7 +397,10 @@ class Batch:
 
     @tuning.setter
     def tuning(self, kv):
-        t = Tuning(int(kv[0]), int(kv[1]))
+        """(K, eval CTAs/SM[, solve lanes for 17 <= n <= 24]); omitted entries keep their value."""
+        cur = self.tuning
+        kv = tuple(kv) + cur[len(kv):]
+        t = Tuning(int(kv[0]), int(kv[1]), int(kv[2]))
         _check(_lib.hpt_batch_set_tuning(self._h, ctypes.byref(t)), "hpt_batch_set_tuning")
 
     def _paths(self, y0s):
@@ -420,8 +424,8 @@ class Batch:
         return x, st, sp
 
     def autotune(self, y0, paths, params=None, stream=None):
-        """Runs every candidate tuning once, keeps the fastest.  Returns
-        (best (K, ctas), {(K, ctas): ms})."""
+        """Coordinate-descent autotuner (hpt_batch_autotune).  Returns
+        (best (K, ctas, lanes), {(K, ctas, lanes): ms})."""
         params = params or Params()
         p = np.ascontiguousarray(np.asarray(paths, dtype=np.int64))
         x = torch.empty_like(y0)

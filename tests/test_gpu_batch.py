@@ -135,14 +135,37 @@ def test_batch_autotune_and_tuning(hpt):
     y0 = np.concatenate([_starts(s, pr, p).reshape(-1) for (s, pr, _), p in zip(systems, paths)])
     b = hpt.Batch([h for _, _, h in systems])
     best, ms = b.autotune(torch.from_numpy(y0).cuda(), paths, hpt.Params(tol_accept=3e-3))
-    assert best in ms and len(ms) >= 4
+    assert best in ms and len(ms) >= 5
     assert b.tuning == best
-    b.tuning = (8, 1)
-    assert b.tuning == (8, 1)
+    b.tuning = (8, 1, 32)
+    assert b.tuning == (8, 1, 32)
     with pytest.raises(hpt.HptError):
-        b.tuning = (0, 1)
+        b.tuning = (0, 1, 8)
     with pytest.raises(hpt.HptError):
-        b.tuning = (8, 3)
+        b.tuning = (8, 3, 8)
+    with pytest.raises(hpt.HptError):
+        b.tuning = (8, 1, 16)
+
+
+def test_batch_solve_shapes_agree(hpt):
+    """Systems with 17 <= n <= 24 solved by 8-lane x 3-row and by 32-lane
+    groups: same statuses, solutions within 1e-9 after polish."""
+    systems = _systems(hpt, _indices(17, 24, 3))
+    paths = [96, 130, 64]
+    y0 = np.concatenate([_starts(s, pr, p).reshape(-1) for (s, pr, _), p in zip(systems, paths)])
+    b = hpt.Batch([h for _, _, h in systems])
+    prm = hpt.Params(tol_accept=3e-3)
+    out = {}
+    for lanes in (8, 32):
+        b.tuning = (8, 1, lanes)
+        x, st, _ = b.track(torch.from_numpy(y0).cuda(), paths, prm)
+        out[lanes] = (x.cpu().numpy(), st.cpu().numpy())
+    (x8, s8), (x32, s32) = out[8], out[32]
+    assert (s8 == s32).mean() > 0.98
+    both = np.repeat((s8 == hpt.CONVERGED) & (s32 == hpt.CONVERGED),
+                     [s.n for (s, _, _), p in zip(systems, paths) for _ in range(p)])
+    rel = np.abs(x8[both] - x32[both]) / np.maximum(1.0, np.abs(x32[both]))
+    assert rel.max() < 1e-9
 
 
 def test_batch_refuses_fp64_handles(hpt):
