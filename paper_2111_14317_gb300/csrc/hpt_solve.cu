@@ -341,14 +341,22 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
     cx<T> l[R];
 #pragma unroll
     for (int s = 0; s < R; ++s) l[s] = used[s] ? mk<T>(0, 0) : cmul_conj_scale(P.a[s][0], pj, rp);
-    // shifted update: a[c-1] = a[c] - l u_{j, j+c} over the live width
+    // shifted update: a[c-1] = a[c] - l u_{j, j+c} over the live width, in
+    // chunks of four columns behind one warp-uniform branch each (the
+    // columns of the last chunk beyond the live width are updated too; they
+    // are never read again)
     const int lim = n - 1 - j;
 #pragma unroll
-    for (int c = 1; c < NC; ++c) {
-      if (c <= lim) {   // uniform over the group
-        const cx<T> u = U[j * LD + c];
+    for (int c0 = 1; c0 < NC; c0 += 4) {
+      if (c0 <= lim) {
 #pragma unroll
-        for (int s = 0; s < R; ++s) P.a[s][c - 1] = csub_mul(P.a[s][c], l[s], u);
+        for (int c = c0; c < c0 + 4; ++c) {
+          if (c < NC) {
+            const cx<T> u = U[j * LD + c];
+#pragma unroll
+            for (int s = 0; s < R; ++s) P.a[s][c - 1] = csub_mul(P.a[s][c], l[s], u);
+          }
+        }
       }
     }
     const cx<T> uE = U[j * LD + NC], uN = U[j * LD + NC + 1];
