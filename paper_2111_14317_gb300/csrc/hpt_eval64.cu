@@ -114,19 +114,17 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
       accH.y = fma(er, ch.y, fma(ei, ch.x, accH.y));
     }
     if (path < 0) continue;
-    // op. 3 of Algorithm 2: D_y h_k = D_z h_k diag(e^{-z})
+    // the step scratch keeps D_z h_k: op. 3 of Algorithm 2 (the diag(e^{-z})
+    // scaling) is applied by the solve to its n-vector solutions instead of
+    // to the n x n block here
     if (ext) {
 #pragma unroll
-      for (int u = 0; u < NMAX; ++u) {
-        if (u < n) {
-          const double2 iy = iys[u][lane];
-          ext[ext_index(pos, k, u, nmax)] =
-              make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
-        }
-      }
+      for (int u = 0; u < NMAX; ++u)
+        if (u < n) ext[ext_index(pos, k, u, nmax)] = accJ[u];
       ext[ext_index(pos, k, n, nmax)] = accT;
       ext[ext_index(pos, k, n + 1, nmax)] = accH;
     }
+    // op. 3 of Algorithm 2 for the caller's H_y: D_y h_k = D_z h_k diag(e^{-z})
     if (oHy) {
       double2* row = oHy + ((size_t)path * n + k) * n;
 #pragma unroll

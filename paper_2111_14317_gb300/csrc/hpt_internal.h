@@ -147,9 +147,10 @@ int prof_begin(hpt_system s, const char* name, cudaStream_t st);
 void prof_end(hpt_system s, int idx, cudaStream_t st);
 
 // Kernel launchers (return cudaSuccess or the launch error).
-// Output layout: either the extended Jacobian (row k = [dH_k/dy_0..
-// dH_k/dy_{n-1}, dH_k/dtau, H_k], stored at ext_index) or the user layout of
-// hpt_eval.
+// Output layout: either the extended Jacobian in z = log y coordinates (row
+// k = [dH_k/dz_0 .. dH_k/dz_{n-1}, dH_k/dtau, H_k] with dH/dz_j =
+// y_j dH/dy_j, stored at ext_index; the solves turn their solutions back into
+// y coordinates) or the user layout of hpt_eval (H_y, H_t, H).
 struct EvalOut {
   void* ext = nullptr;       // extended Jacobian (step scratch)
   void* H = nullptr;         // user layout

@@ -16,7 +16,9 @@
 //   op. 2b  [D_z h_k | D_tau h_k | h_k] = E_k B_k^T as a real GEMM on
 //           [Re E, Im E] x [[Re B, Im B], [-Im B, Re B]]^T, three passes
 //           hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory;
-//   op. 3   D_y h_k = D_z h_k diag(1/y), written out.
+//   op. 3   D_y h_k = D_z h_k diag(1/y) for the caller's H_y.  The step's
+//           scratch keeps D_z h_k instead: the solve applies diag(1/y) to
+//           its two n-vector solutions (n products per path, not n^2).
 // The per-equation constants (exponent operand, B_k hi/lo, e) are one
 // contiguous image per equation, double-buffered into shared memory with
 // cp.async.bulk (the bulk-copy engine) while the previous equation computes.
@@ -245,8 +247,10 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     for (int j = half; j < n; j += 2) {
       float2 v = live ? y[vbase + j] : make_float2(1.f, 0.f);
       const float zr = logf(hypotf(v.x, v.y)), zi = atan2f(v.y, v.x);
-      const float r2 = v.x * v.x + v.y * v.y;
-      sInvY[j * 128 + row] = make_float2(v.x / r2, -v.y / r2);
+      if (oHy) {
+        const float r2 = v.x * v.x + v.y * v.y;
+        sInvY[j * 128 + row] = make_float2(v.x / r2, -v.y / r2);
+      }
       float rem_r = zr, rem_i = zi;
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
@@ -363,10 +367,11 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
             const int u = c0 / 2 + q;
             const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
             if (u < n) {
-              const float2 iy = sInvY[u * 128 + row];
-              const float2 hy = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
-              if (ext) ext[ext_index(pos, k, u, nmax)] = hy;
-              if (oHy) oHy[((size_t)path * n + k) * n + u] = hy;
+              if (ext) ext[ext_index(pos, k, u, nmax)] = v;   // D_z h: the solve applies diag(1/y)
+              if (oHy) {
+                const float2 iy = sInvY[u * 128 + row];
+                oHy[((size_t)path * n + k) * n + u] = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
+              }
             } else if (u == n) {
               if (ext) ext[ext_index(pos, k, n, nmax)] = v;
               if (oHt) oHt[(size_t)path * n + k] = make_float2(v.x * t_inv, v.y * t_inv);

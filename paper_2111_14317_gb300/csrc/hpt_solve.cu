@@ -2,8 +2,12 @@
 // per-path step control, plus the small kernels around them (state init,
 // active count, Newton polish at t = 1, implicit-function adjoint).
 //
+// The scratch holds D_z H = H_y diag(y) (z = log y).  H_y d = r is solved as
+// D_z H w = r, d = diag(y) w: the diag(1/y) scaling of op. 3 of Algorithm 2
+// costs n products per path here instead of n^2 in the evaluation.
+//
 // Solve mapping: a group of G lanes owns one path and every lane holds R rows
-// of [H_y | -H_tau | -H] in registers (rows lane, lane + G, ...), n <= G R.
+// of [D_z H | -H_tau | -H] in registers (rows lane, lane + G, ...), n <= G R.
 // The rows are equilibrated by exact powers of two, then Gaussian elimination
 // with partial pivoting runs over a run-time column loop.  Rows are "shifted":
 // after column j is eliminated every live row moves one register to the left,
@@ -38,6 +42,10 @@ __device__ __forceinline__ cx<T> mk(T a, T b) {
 template <typename T>
 __device__ __forceinline__ cx<T> csub_mul(cx<T> acc, cx<T> a, cx<T> b) {  // acc - a b
   return mk<T>(acc.x - (a.x * b.x - a.y * b.y), acc.y - (a.x * b.y + a.y * b.x));
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename T>
 __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) {
@@ -157,8 +165,8 @@ __device__ __forceinline__ unsigned group_mask() {
   return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
 }
 
-// Loads the rows of [H_y | -H_tau | -H] (adjoint = false) or of
-// [J^H | g | 0] (adjoint = true, J = H_y, g from gx) for one path; returns
+// Loads the rows of [D_z H | -H_tau | -H] (adjoint = false) or of
+// [(D_z H)^H | g | 0] (adjoint = true, g from gx) for one path; returns
 // whether every entry is finite (group-uniform).
 template <typename T, typename S, int G, int R>
 __device__ __forceinline__ bool load_rows(int n, int nmax, const void* ext, int64_t q, size_t vbase, bool valid,
@@ -420,11 +428,11 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
 // handles the variables l + G s.
 template <typename TS, int G, int R>
 __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, int32_t status, bool ok,
-                                            const cx<TS> (&xE)[R], const cx<TS> (&xN)[R], const hpt_paths& S,
+                                            const cx<TS> (&wE)[R], const cx<TS> (&wN)[R], const hpt_paths& S,
                                             const hpt_params& prm) {
   const int lane = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
-  cx<TS> y[R], yacc[R], dEacc[R];
+  cx<TS> y[R], yacc[R], dEacc[R], xE[R], xN[R];
   bool solfin = true;
   TS ny = TS(0), nd = TS(0);
 #pragma unroll
@@ -435,6 +443,10 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
     y[s] = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
     yacc[s] = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
     dEacc[s] = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
+    // the scratch holds D_z H = H_y diag(y): the solve gave diag(1/y) times
+    // the directions
+    xE[s] = cmul(y[s], wE[s]);
+    xN[s] = cmul(y[s], wN[s]);
     if (mine) {
       solfin = solfin && finite(xE[s]) && finite(xN[s]);
       ny = t_max(ny, cabs_t(y[s]));
@@ -737,6 +749,7 @@ newton_kernel(int n0, int64_t p, const void* __restrict__ ext, double2* __restri
   for (int s = 0; s < R; ++s) {
     const int j = lane + G * s;
     y[s] = j < n ? ld<double>(x, vbase + j) : mk<double>(0, 0);
+    xN[s] = cmul(y[s], xN[s]);   // D_z H in the scratch: the correction is x * w
     if (j < n) {
       sfin = sfin && finite(xN[s]);
       y[s] = mk<double>(y[s].x + xN[s].x, y[s].y + xN[s].y);
@@ -779,6 +792,16 @@ adjoint_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t*
   const bool valid = path < p;
   PathRows<double, G, R> P;
   const bool fin = load_rows<double, double, G, R>(n, n, ext, path, (size_t)path * n, valid, true, gx, P);
+  // D_z H = H_y diag(x) in the scratch: H_y^H lambda = g becomes
+  // (D_z H)^H lambda = conj(x) g
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int r = lane + G * s;
+    if (valid && r < n) {
+      const double2 v = x[(size_t)path * n + r];
+      P.bE[s] = cmul(mk<double>(v.x, -v.y), P.bE[s]);
+    }
+  }
   cx<double> lam[R], dummy[R];
   double cond;
   const bool ok =
