@@ -267,7 +267,10 @@ def run_batch(args, dev):
     y0 = y0_host.to(dev)
     b = hpt.Batch(systems)
     prm = hpt.Params(tol_accept=3e-3)
-    best, cand = b.autotune(y0, paths, prm)
+    if args.no_autotune:
+        best, cand = b.tuning, {}
+    else:
+        best, cand = b.autotune(y0, paths, prm)
     for _ in range(max(1, min(args.warmup, 2))):
         b.track(y0, paths, prm)
     reps = max(1, args.batch_reps)
@@ -359,6 +362,10 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=256, help="0 skips the many-systems batch")
     ap.add_argument("--batch-paths", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default tuning")
+    ap.add_argument("--workload", default="all", choices=["all", "step", "batch"],
+                    help="step: the n=16 hpt_step line only; batch: the many-systems batch only "
+                         "(prints its own JSON object, for profiling)")
     args = ap.parse_args()
     ws, rank, _ = _dist()
 
@@ -384,6 +391,15 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.workload == "batch":
+        import torch
+        from paper_2111_14317_gb300 import build as hbuild
+        hbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"batch": run_batch(args, torch.device("cuda", 0))}))
+        return
+    if args.workload == "step":
+        args.batch_systems = 0
     out, ws, rank = run_gpu(args)
     if rank != 0:
         return
