@@ -60,6 +60,23 @@ def shard_seed(rank: int) -> int:
     return 1 + rank
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest of every rank's value (the slowest rank's time); the value
+    itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -201,11 +218,7 @@ def run_gpu(args):
         # headline pass (no per-kernel events), clocks sampled meanwhile
         with ClockSampler(local) as clk:
             ms = timed(False)
-        tot = sum(ms)
-        if ws > 1:
-            t = torch.tensor([tot], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(ms), dev)
         # second pass: CUDA events around every kernel on the launching stream
         timed(True)
         kern = h.profile_read()
@@ -405,8 +418,8 @@ def main():
         return
     peaks, peak_kind = _peaks()
     mx, fp = out["mixed"], out["fp64"]
-    value = ws * PATHS / (mx["ms_per_step"] * 1e-3)
-    fp_value = ws * PATHS / (fp["ms_per_step"] * 1e-3)
+    value = whole_job_rate(ws, PATHS, mx["ms_per_step"] * 1e-3)
+    fp_value = whole_job_rate(ws, PATHS, fp["ms_per_step"] * 1e-3)
     # per-kernel roofline of the mixed step
     kinfo = {}
     for name, (launches, msum) in mx["kernels"].items():
