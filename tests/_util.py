@@ -19,6 +19,15 @@ def first_generic(cfg, min_mv=2):
     raise RuntimeError("no generic sample")
 
 
+def min_separation(y):
+    """Smallest Euclidean distance between two rows of a complex point set
+    (k-d tree over the real coordinates, O(N log N) memory-light)."""
+    from scipy.spatial import cKDTree
+    pts = np.concatenate([np.real(y), np.imag(y)], axis=1)
+    d, _ = cKDTree(pts).query(pts, k=2)
+    return float(d[:, 1].min())
+
+
 def scaled_err(got, ref, scale):
     return float(np.max(np.abs(np.asarray(got) - ref) / np.maximum(scale, 1e-300)))
 

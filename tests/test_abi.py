@@ -110,9 +110,7 @@ def test_binomial_start_large_determinant(hpt):
     b = np.array([-s.coeffs[off[k] + pairs[k][0]] / s.coeffs[off[k] + pairs[k][1]] for k in range(s.n)])
     res = np.abs(np.prod(y[:, None, :] ** V[None, :, :], axis=2) / b[None, :] - 1).max()
     assert res < 1e-12
-    dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
-    np.fill_diagonal(dd, np.inf)
-    assert dd.min() > 1e-8
+    assert _util.min_separation(y) > 1e-8
 
 
 def test_binomial_points_match_oracle(hpt):

@@ -180,9 +180,7 @@ def test_start_points_large_determinant():
     res = np.abs(np.prod(y[:, None, :] ** V[None, :, :], axis=2) / b[None, :] - 1).max()
     assert res < 1e-12
     # distinct points
-    dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
-    np.fill_diagonal(dd, np.inf)
-    assert dd.min() > 1e-8
+    assert _util.min_separation(y) > 1e-8
 
 
 def _pair_data(s, pairs):
@@ -235,6 +233,7 @@ def test_binomial_points_large_determinant():
     """Many-systems workload systems (n up to 24, |det V| far beyond 2^62):
     points for k = j e_1 solve y^V = b (checked by repeated multiplication)
     and are distinct."""
+    import _util
     for idx in (0, 3, 7):
         s, pairs = W.config4_system(idx)
         V, b = _pair_data(s, pairs)
@@ -243,6 +242,4 @@ def test_binomial_points_large_determinant():
         y = cells.binomial_points(V, b, ks)
         res = np.abs(_powprod(y, V) / b[None, :] - 1).max()
         assert res < 1e-9, (idx, s.n, res)
-        dd = np.abs(y[:, None, :] - y[None, :, :]).max(-1)
-        np.fill_diagonal(dd, np.inf)
-        assert dd.min() > 1e-8
+        assert _util.min_separation(y) > 1e-8
