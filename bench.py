@@ -246,6 +246,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
     if args.batch_systems > 0:
         out["batch"] = run_batch(args, dev)
+    if args.workload == "all":
+        out["track_adjoint"] = run_track_adjoint(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     return out, ws, rank
@@ -267,9 +269,11 @@ def run_batch(args, dev):
     import workloads as W
     nsys, npaths = args.batch_systems, args.batch_paths
     t0 = time.perf_counter()
-    systems, y0s = [], []
+    systems, y0s, gemm_flop = [], [], []
     for idx in range(nsys):
         s, pairs = W.config4_system(idx)
+        M = int(sum(s.m))
+        gemm_flop.append(2 * (2 * s.n + 1) * M + 8 * (s.n + 2) * M)   # per path-step, as for n=16
         systems.append(hpt.System.from_laurent(s, {"kind": "pairs", "pairs": pairs}, hpt.HPT_MIXED))
         ks = np.zeros((npaths, s.n), np.int64)
         ks[:, 0] = np.arange(npaths)
@@ -312,6 +316,11 @@ def run_batch(args, dev):
     total_steps = int(sp_h.sum())
     t_ms = statistics.median(ms)
     conv = sp_h[st_n == hpt.CONVERGED]
+    # algorithmic GEMM work of every path-step taken, over the whole track time
+    steps_per_sys = sp_h.reshape(nsys, npaths).sum(axis=1)
+    flop = float(np.dot(steps_per_sys, np.array(gemm_flop, dtype=np.float64)))
+    peaks, peak_kind = _peaks()
+    ach = flop / (t_ms * 1e-3) / 1e12
     out = {
         "workload": BATCH_WORKLOAD, "systems": nsys, "paths": nsys * npaths,
         "ms_per_track": t_ms, "ms_list": ms,
@@ -330,10 +339,82 @@ def run_batch(args, dev):
                            "median": float(np.median(conv)) if conv.size else None,
                            "max": int(conv.max()) if conv.size else None},
         "setup_s": setup_s, "clocks": clk.summary(),
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"],
+                     "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops_sustained"],
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json, sustained)",
+                     "note": "algorithmic exponent + coefficient GEMM flops of all path-steps over the whole "
+                             "track time (evaluation, solves, compaction and polish included)"},
     }
     b.close()
     for h in systems:
         h.close()
+    return out
+
+
+ADJ_WORKLOAD = ("adjoint workload: n=8, 12 monomials/equation, exponents in [-2,2], planted pair cell "
+                "with |det V| >= 4096; 4,096 start points tracked to t = 1 (mixed form + FP64 polish), "
+                "then the implicit-function coefficient gradient at the converged solutions")
+FP64_PEAK_TFLOPS = 1.25   # nominal FP64 (non-tensor) rate of the part
+
+
+def run_track_adjoint(args, dev):
+    """hpt_track on the adjoint workload's 4,096 paths (whole tracks with the
+    FP64 polish), then hpt_adjoint at the converged solutions."""
+    import torch
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+    n_sol = 4096
+    for att in range(200):
+        s, pairs = W.config5(att)
+        try:
+            y0, tot = hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, pairs, 0, 1)
+            if tot < n_sol:
+                continue
+            y0, _ = hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, pairs, 0, n_sol)
+            h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": pairs}, hpt.HPT_MIXED)
+            break
+        except hpt.HptError:
+            continue
+    prm = hpt.Params(tol_accept=3e-3)
+    yd = torch.from_numpy(y0).to(dev)
+    h.track(yd, prm)
+    reps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        x, st, sp = h.track(yd, prm)
+    torch.cuda.synchronize()
+    track_ms = (time.perf_counter() - t0) * 1e3 / reps
+    conv = st == hpt.CONVERGED
+    xc = x[conv].contiguous()
+    gx = (2.0 * xc).contiguous()             # gradient of sum |x|^2
+    for _ in range(3):
+        h.adjoint(xc, gx)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(10):
+        gc = h.adjoint(xc, gx)
+    ev[1].record()
+    torch.cuda.synchronize()
+    adj_ms = ev[0].elapsed_time(ev[1]) / 10
+    nconv = int(conv.sum().item())
+    n, M = s.n, h.M
+    # FP64 work per solution: evaluation (dot products, coefficient sums),
+    # LU with one right-hand side and the contributions; exp/sincos not counted
+    flop = M * (2 * n + 8 * (n + 2)) + 8 * (n - 1) * n * (2 * n - 1) // 6 + 8 * n * n + M * (2 * n + 8)
+    achieved = nconv * flop / (adj_ms * 1e-3) / 1e12
+    out = {
+        "workload": ADJ_WORKLOAD, "attempt": att, "det_V": int(tot),
+        "track": {"paths": n_sol, "ms": track_ms, "paths_per_s": n_sol / (track_ms * 1e-3),
+                  "path_steps_per_s": float(sp.sum().item()) / (track_ms * 1e-3),
+                  "converged": nconv, "median_steps": float(sp.float().median().item())},
+        "adjoint": {"solutions": nconv, "ms": adj_ms, "value": nconv / (adj_ms * 1e-3), "unit": "solutions/s",
+                    "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                 "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate",
+                                 "flop_per_solution": flop}},
+    }
+    h.close()
     return out
 
 
@@ -472,6 +553,8 @@ def main():
     }
     if "batch" in out:
         line["batch"] = out["batch"]
+    if "track_adjoint" in out:
+        line["track_adjoint"] = out["track_adjoint"]
     print(json.dumps(line))
 
 
