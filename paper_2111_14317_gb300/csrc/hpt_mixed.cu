@@ -77,12 +77,10 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -285,14 +283,16 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       {
         const float* texp = (const float*)(cbuf(g) + S.off_texp);
         const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * S.MP) + lane_base;
-        for (int c0 = 16 * half; c0 < S.MP; c0 += 32) {
-          uint32_t wre[16], wim[16];
-          tmem_ld16(tw + c0, wre);
-          tmem_ld16(tw + S.MP + c0, wim);
+        // chunks of 8 monomials alternate between the warpgroups (MP is a
+        // multiple of 16, so both get the same number)
+        for (int c0 = 8 * half; c0 < S.MP; c0 += 16) {
+          uint32_t wre[8], wim[8];
+          tmem_ld8(tw + c0, wre);
+          tmem_ld8(tw + S.MP + c0, wim);
           tmem_wait_ld();
-          uint32_t hr[8], hi_[8], lr[8], li[8];
+          uint32_t hr[4], hi_[4], lr[4], li[4];
 #pragma unroll
-          for (int q = 0; q < 16; q += 2) {
+          for (int q = 0; q < 8; q += 2) {
             float er[2], ei[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -316,15 +316,11 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
             lr[q / 2] = *(const uint32_t*)&lre;
             li[q / 2] = *(const uint32_t*)&lim;
           }
-          // Re E at K = c0.., Im E at K = MP + c0..; 16 values = two core columns
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int kre = c0 + 8 * h, kim = S.MP + c0 + 8 * h;
-            *(uint4*)(sAcHi + canon(row, kre, S.KC)) = make_uint4(hr[4 * h], hr[4 * h + 1], hr[4 * h + 2], hr[4 * h + 3]);
-            *(uint4*)(sAcLo + canon(row, kre, S.KC)) = make_uint4(lr[4 * h], lr[4 * h + 1], lr[4 * h + 2], lr[4 * h + 3]);
-            *(uint4*)(sAcHi + canon(row, kim, S.KC)) = make_uint4(hi_[4 * h], hi_[4 * h + 1], hi_[4 * h + 2], hi_[4 * h + 3]);
-            *(uint4*)(sAcLo + canon(row, kim, S.KC)) = make_uint4(li[4 * h], li[4 * h + 1], li[4 * h + 2], li[4 * h + 3]);
-          }
+          // Re E at K = c0.., Im E at K = MP + c0..; 8 values = one core column
+          *(uint4*)(sAcHi + canon(row, c0, S.KC)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+          *(uint4*)(sAcLo + canon(row, c0, S.KC)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+          *(uint4*)(sAcHi + canon(row, S.MP + c0, S.KC)) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+          *(uint4*)(sAcLo + canon(row, S.MP + c0, S.KC)) = make_uint4(li[0], li[1], li[2], li[3]);
         }
       }
       proxy_fence();
@@ -355,28 +351,33 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
         proxy_fence();
         load_next();   // item g + nbuf into this buffer
       }
-      // ---- op. 3: scale to y-coordinates and write row k (column chunks split by half)
+      // ---- row k of the outputs: 8-column chunks (4 complex entries) alternate
+      // between the warpgroups (NJ is a multiple of 16)
       if (ok) {
-        for (int c0 = 16 * half; c0 < S.NJ; c0 += 32) {
-          uint32_t jr[16];
-          tmem_ld16(t_j + lane_base + c0, jr);
+        // the step scratch row [D_z h_k | D_tau h_k | h_k] is contiguous in u
+        // with stride 128 (ext_index); the solve applies diag(1/y)
+        float2* erow = ext ? ext + ext_index(pos, k, 0, nmax) : nullptr;
+        for (int c0 = 8 * half; c0 < S.NJ; c0 += 16) {
+          uint32_t jr[8];
+          tmem_ld8(t_j + lane_base + c0, jr);
           tmem_wait_ld();
           if (!live) continue;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 4; ++q) {
             const int u = c0 / 2 + q;
             const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
+            if (erow) {
+              if (u < n + 2) erow[(size_t)u * 128] = v;
+              continue;
+            }
             if (u < n) {
-              if (ext) ext[ext_index(pos, k, u, nmax)] = v;   // D_z h: the solve applies diag(1/y)
               if (oHy) {
                 const float2 iy = sInvY[u * 128 + row];
                 oHy[((size_t)path * n + k) * n + u] = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
               }
             } else if (u == n) {
-              if (ext) ext[ext_index(pos, k, n, nmax)] = v;
               if (oHt) oHt[(size_t)path * n + k] = make_float2(v.x * t_inv, v.y * t_inv);
             } else if (u == n + 1) {
-              if (ext) ext[ext_index(pos, k, n + 1, nmax)] = v;
               if (oH) oH[(size_t)path * n + k] = v;
             }
           }
