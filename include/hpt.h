@@ -192,8 +192,10 @@ hpt_status hpt_binomial_points(int32_t n, const int32_t* support_sizes, const in
  * upload of the constants (A with the t-exponent row, B_k for every k, and for
  * HPT_MIXED their split-BF16 operand images) to the current device.
  * coeffs[2M] are c_{k,i} as (re, im) doubles.  HPT_MIXED needs |a_j| <= 256 and
- * sum_j |a_j| <= 64 for every monomial (HPT_ERANGE), n <= 32, m_k <= 128
- * (HPT_ENOTSUP).  *out receives the handle. */
+ * sum_j |a_j| <= 64 for every monomial (HPT_ERANGE), n <= 32, m_k <= 128 and
+ * operand shapes that fit the evaluation kernel's shared and tensor memory
+ * (for example n = 24 with m_k <= 96, n = 8 with m_k <= 128; HPT_ENOTSUP
+ * otherwise).  *out receives the handle. */
 hpt_status hpt_create_system(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
                              const double* coeffs, const int64_t* lifting, const hpt_cell* cell,
                              hpt_precision prec, hpt_system* out);

@@ -721,6 +721,13 @@ hpt_status hpt_create_system(int32_t n, const int32_t* msz, const int32_t* exps,
   if (prec == HPT_MIXED) {
     MixedLayout& ml = s->ml;
     ml = mixed_layout(n, max_m);
+    int max_smem = 0;
+    CU(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+    if (!eval_mixed_fits(n, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, max_smem)) {
+      set_error("n=%d with m_k up to %d exceeds the mixed form's on-chip memory", n, max_m);
+      hpt_destroy(s);
+      return HPT_ENOTSUP;
+    }
     std::vector<uint8_t> img((size_t)n * ml.chunk_bytes, 0);
     for (int k = 0; k < n; ++k) {
       uint8_t* ch = img.data() + (size_t)k * ml.chunk_bytes;

@@ -181,6 +181,10 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
 cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tmem_cols, const uint8_t* chunks,
                                   int64_t p, const void* y, const double* tau, const PathMap& pm, void* ext,
                                   int32_t* err, int ctas_per_sm, cudaStream_t st);
+// Whether the mixed evaluation kernel can run these operand shapes at all
+// (its leanest configuration within max_smem bytes of shared memory and the
+// 512 tensor-memory columns of an SM).
+bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, int max_smem);
 // Resident eval CTAs per SM the tensor memory allows for tmem_cols (1 or 2).
 int eval_mixed_max_ctas(int tmem_cols);
 MixedSys mixed_sys_of(const hpt_system s);

@@ -40,6 +40,7 @@ struct MixedArgs {
   MixedSys sys;   // the system of a single-system launch
   int tmem_cols;
   int nbuf;   // constant-image buffers: 2 (prefetch next equation) or 1
+  int wbuf;   // exponent accumulators W in tensor memory: 2 (next GEMM under the epilogue) or 1
   // shared-memory carve-up (bytes from the 1024-aligned base)
   int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_bar;
   int64_t p;
@@ -167,7 +168,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   const int ntiles = pm.npos ? (*pm.npos + 127) / 128 : P.ntiles;
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   if (my_tiles <= 0) return;
-  const bool lookahead = P.nbuf == 2;
+  const bool lookahead = P.nbuf == 2 && P.wbuf == 2;
   const int nmax = pm.nmax ? pm.nmax : P.sys.n;
   // work items are (tile, equation) pairs; a tile's system fixes the shapes
   auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
@@ -198,7 +199,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     if (!mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g))) return false;
     tc_fence_after();
     const uint32_t cb = su32(cbuf(g));
-    const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * S.MP);
+    const uint32_t tw = tbase + (uint32_t)((P.wbuf == 2 ? (g & 1) : 0) * 2 * S.MP);
     const uint32_t idx_x = idesc_bf16(128, S.MP), sbo_x = S.KX * 16;
     for (int s = 0; s < S.KX / 16; ++s) {
       const uint64_t bd = smem_desc(cb + S.off_bexp + s * 256, 128, sbo_x);
@@ -231,7 +232,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     const int tile = tile_of(it);
     const MixedSys S = pm.sys_tab ? pm.sys_tab[sys_of(tile)] : P.sys;
     const int n = S.n;
-    const uint32_t t_j = tbase + 4 * S.MP;
+    const uint32_t t_j = tbase + (uint32_t)(P.wbuf * 2 * S.MP);
     const int64_t pos = (int64_t)tile * 128 + row;   // position of this row
     const int64_t path = pm.list ? pm.list[pos] : pos;
     const bool live = pm.list ? path >= 0 : pos < P.p;
@@ -268,6 +269,40 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     __syncthreads();
     if (tid == 0 && lookahead && !issue_exp(g, S)) atomicExch(sAbort, 1);
 
+    // row kk of the outputs from J: 8-column chunks (4 complex entries)
+    // alternate between the warpgroups (NJ is a multiple of 16)
+    auto write_row = [&](int kk) {
+      const uint32_t tj = t_j + lane_base;
+      // the step scratch row [D_z h_kk | D_tau h_kk | h_kk] is contiguous in u
+      // with stride 128 (ext_index); the solve applies diag(1/y)
+      float2* erow = ext ? ext + ext_index(pos, kk, 0, nmax) : nullptr;
+      for (int c0 = 8 * half; c0 < S.NJ; c0 += 16) {
+        uint32_t jr[8];
+        tmem_ld8(tj + c0, jr);
+        tmem_wait_ld();
+        if (!live) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int u = c0 / 2 + q;
+          const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
+          if (erow) {
+            if (u < n + 2) erow[(size_t)u * 128] = v;
+            continue;
+          }
+          if (u < n) {
+            if (oHy) {
+              const float2 iy = sInvY[u * 128 + row];
+              oHy[((size_t)path * n + kk) * n + u] = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
+            }
+          } else if (u == n) {
+            if (oHt) oHt[(size_t)path * n + kk] = make_float2(v.x * t_inv, v.y * t_inv);
+          } else if (u == n + 1) {
+            if (oH) oH[(size_t)path * n + kk] = v;
+          }
+        }
+      }
+    };
+
     for (int k = 0; k < n; ++k, ++g) {
       // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
       // GEMM of equation k+1 is issued now and runs under this epilogue
@@ -282,7 +317,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       // ---- complex exponential, BF16 hi/lo split into the op. 2b A operand
       {
         const float* texp = (const float*)(cbuf(g) + S.off_texp);
-        const uint32_t tw = tbase + (uint32_t)((g & 1) * 2 * S.MP) + lane_base;
+        const uint32_t tw = tbase + (uint32_t)((P.wbuf == 2 ? (g & 1) : 0) * 2 * S.MP) + lane_base;
         // chunks of 8 monomials alternate between the warpgroups (MP is a
         // multiple of 16, so both get the same number)
         for (int c0 = 8 * half; c0 < S.MP; c0 += 16) {
@@ -332,57 +367,28 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
         tc_fence_after();
         const uint32_t cb = su32(cbuf(g));
         const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
+        const uint32_t tj = t_j;
         for (int s = 0; s < S.KC / 16; ++s) {
           const uint64_t ah = smem_desc(su32(sAcHi) + s * 256, 128, sbo_c);
           const uint64_t al = smem_desc(su32(sAcLo) + s * 256, 128, sbo_c);
           const uint64_t bh = smem_desc(cb + S.off_bhi + s * 256, 128, sbo_c);
           const uint64_t bl = smem_desc(cb + S.off_blo + s * 256, 128, sbo_c);
-          mma_bf16(t_j, ah, bh, idx_c, s > 0);
-          mma_bf16(t_j, ah, bl, idx_c, 1);
-          mma_bf16(t_j, al, bh, idx_c, 1);
+          mma_bf16(tj, ah, bh, idx_c, s > 0);
+          mma_bf16(tj, ah, bl, idx_c, 1);
+          mma_bf16(tj, al, bh, idx_c, 1);
         }
         mma_commit(su32(&bars[4]));
       }
       ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[4]), (uint32_t)g & 1u));
       if (!ok) atomicExch(sAbort, 1);
       tc_fence_after();
-      // both GEMMs of equation k are done: its constant buffer is free
+      // both GEMMs of equation k are done: its constant buffer and the E
+      // operand are free
       if (tid == 0 && ok) {
         proxy_fence();
         load_next();   // item g + nbuf into this buffer
       }
-      // ---- row k of the outputs: 8-column chunks (4 complex entries) alternate
-      // between the warpgroups (NJ is a multiple of 16)
-      if (ok) {
-        // the step scratch row [D_z h_k | D_tau h_k | h_k] is contiguous in u
-        // with stride 128 (ext_index); the solve applies diag(1/y)
-        float2* erow = ext ? ext + ext_index(pos, k, 0, nmax) : nullptr;
-        for (int c0 = 8 * half; c0 < S.NJ; c0 += 16) {
-          uint32_t jr[8];
-          tmem_ld8(t_j + lane_base + c0, jr);
-          tmem_wait_ld();
-          if (!live) continue;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int u = c0 / 2 + q;
-            const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
-            if (erow) {
-              if (u < n + 2) erow[(size_t)u * 128] = v;
-              continue;
-            }
-            if (u < n) {
-              if (oHy) {
-                const float2 iy = sInvY[u * 128 + row];
-                oHy[((size_t)path * n + k) * n + u] = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
-              }
-            } else if (u == n) {
-              if (oHt) oHt[(size_t)path * n + k] = make_float2(v.x * t_inv, v.y * t_inv);
-            } else if (u == n + 1) {
-              if (oH) oH[(size_t)path * n + k] = v;
-            }
-          }
-        }
-      }
+      if (ok) write_row(k);
       tc_fence_before();
       __syncthreads();
       if (*sAbort) goto teardown;
@@ -421,74 +427,92 @@ int num_sms() {
 
 // Shared-memory carve-up for the largest shapes of a launch (maxs), the
 // single-system arguments (sys) and the grid; then the launch.
-cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& maxs, int tmem_cols, int64_t p,
-                        int64_t ntiles, const uint8_t* chunks, const void* y, const double* tin, int tau_is_t,
-                        const EvalOut& out, int32_t* err, const PathMap& pm, int ctas_per_sm, cudaStream_t st) {
-  MixedArgs a;
-  a.sys = sys;
-  a.tmem_cols = tmem_cols;
-  int off = 0;
-  auto take = [&](int bytes) {
-    int o = off;
-    off += (bytes + 1023) / 1024 * 1024;
-    return o;
-  };
-  a.s_are = take(128 * maxs.KX * 2);
-  a.s_aim = take(128 * maxs.KX * 2);
-  a.s_invy = take(128 * maxs.n * 8);
-  a.s_achi = take(128 * maxs.KC * 2);
-  a.s_aclo = take(128 * maxs.KC * 2);
-  a.s_const0 = take(maxs.chunk_bytes);
-  const int off_single = off;
-  a.s_const1 = take(maxs.chunk_bytes);
-  a.s_bar = take(128);
-  int smem = off + 1024;   // slack for aligning the dynamic base
-  a.p = p;
+cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& maxs, int64_t p, int64_t ntiles,
+                        const uint8_t* chunks, const void* y, const double* tin, int tau_is_t, const EvalOut& out,
+                        int32_t* err, const PathMap& pm, int ctas_per_sm, cudaStream_t st) {
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
-  a.ntiles = (int)ntiles;
-  int max_smem = 0;
-  {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  }
-  a.nbuf = 2;
-  if (smem > max_smem) {   // large shapes: one constant buffer, no prefetch
-    off = off_single;
-    a.s_const1 = a.s_const0;
-    a.s_bar = take(128);
-    smem = off + 1024;
-    a.nbuf = 1;
-  }
-  if (smem > max_smem) return cudaErrorInvalidConfiguration;
   const bool map = pm.list != nullptr;
-  cudaError_t e = cudaFuncSetAttribute(map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto kern = map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>;
+  int dev = 0, max_smem = 0, sm_smem = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  // Configurations in order of preference, the first that fits wins:
+  // (nbuf, wbuf) = (2, 2) prefetches the next equation's constants and
+  // issues its exponent GEMM into the second W accumulator under the current
+  // epilogue; (1, 2) is that without the prefetch; (1, 1) drops both and
+  // needs the least shared and tensor memory (it is the one that serves
+  // m_k up to 128).  At n = 16 the overlap is worth more than residency:
+  // (1, 1) with three CTAs per SM measured 177 us against 117 us for (2, 2)
+  // with two.  Residency is bounded by shared memory, registers and the 512
+  // tensor-memory columns of an SM; a persistent grid above it would run in
+  // two waves.
+  MixedArgs best{};
+  int best_smem = 0, best_per_sm = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
-  // resident CTAs per SM are bounded by tensor memory (512 columns) and by
-  // shared memory: a persistent grid larger than what is resident would run
-  // in two waves
-  int max_per_sm = eval_mixed_max_ctas(tmem_cols);
-  {
-    int dev = 0, sm_total = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sm_total, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    const int fit = sm_total / (smem + 1024);   // 1 KB per CTA is reserved by the system
-    if (fit < max_per_sm) max_per_sm = fit < 1 ? 1 : fit;
+  const int regs_per_cta = (fa.numRegs + 7) / 8 * 8 * kEvalThreads;
+  const int cfg[3][2] = {{2, 2}, {1, 2}, {1, 1}};
+  for (const auto& c : cfg) {
+    MixedArgs a;
+    a.sys = sys;
+    a.nbuf = c[0];
+    a.wbuf = c[1];
+    int cols = a.wbuf * 2 * maxs.MP + maxs.NJ, t = 32;
+    while (t < cols) t *= 2;
+    if (t > 512) continue;
+    a.tmem_cols = t;
+    int off = 0;
+    auto take = [&](int bytes) {
+      int o = off;
+      off += (bytes + 1023) / 1024 * 1024;
+      return o;
+    };
+    a.s_are = take(128 * maxs.KX * 2);
+    a.s_aim = take(128 * maxs.KX * 2);
+    a.s_invy = take(out.Hy ? 128 * maxs.n * 8 : 0);   // 1/y only for the caller's H_y
+    a.s_achi = take(128 * maxs.KC * 2);
+    a.s_aclo = take(128 * maxs.KC * 2);
+    a.s_const0 = take(maxs.chunk_bytes);
+    a.s_const1 = a.nbuf == 2 ? take(maxs.chunk_bytes) : a.s_const0;
+    a.s_bar = take(128);
+    a.p = p;
+    a.ntiles = (int)ntiles;
+    const int smem = off + 1024;   // slack for aligning the dynamic base
+    if (smem > max_smem) continue;
+    // 1 KB of shared memory per CTA is reserved by the system
+    const int per_sm = std::min({sm_smem / (smem + 1024), 65536 / regs_per_cta, 512 / a.tmem_cols});
+    if (per_sm >= 1) {
+      best = a;
+      best_smem = smem;
+      best_per_sm = per_sm;
+      break;
+    }
   }
-  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, max_per_sm) : max_per_sm;
+  if (best_per_sm < 1) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, best_smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, best_per_sm) : best_per_sm;
   int64_t grid = (int64_t)num_sms() * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) return cudaSuccess;
   int pi = prof_begin(prof, "eval_mixed_tc", st);
-  auto kern = map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>;
-  kern<<<(unsigned)grid, kEvalThreads, smem, st>>>(a, (const float2*)y, tin, tau_is_t, chunks, (float2*)out.ext,
-                                                 (float2*)out.H, (float2*)out.Hy, (float2*)out.Ht, err, pm);
+  kern<<<(unsigned)grid, kEvalThreads, best_smem, st>>>(best, (const float2*)y, tin, tau_is_t, chunks,
+                                                       (float2*)out.ext, (float2*)out.H, (float2*)out.Hy,
+                                                       (float2*)out.Ht, err, pm);
   prof_end(prof, pi, st);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, int max_smem) {
+  auto r = [](int v) { return (v + 1023) / 1024 * 1024; };
+  // the leanest configuration (one constant buffer, one W accumulator), 1/y included
+  const int smem = r(128 * KX * 2) * 2 + r(128 * n * 8) + r(128 * KC * 2) * 2 + r(chunk_bytes) + r(128) + 1024;
+  return smem <= max_smem && 2 * MP + NJ <= 512;
+}
 
 int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }
 
@@ -515,8 +539,8 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
                               const EvalOut& out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
   const MixedSys m = mixed_sys_of(s);
-  return launch_core(s, m, m, s->ml.tmem_cols, p, (p + 127) / 128, s->d_chunks, y, tin, tau_is_t, out, s->d_err,
-                     PathMap(), 0, st);
+  return launch_core(s, m, m, p, (p + 127) / 128, s->d_chunks, y, tin, tau_is_t, out, s->d_err, PathMap(), 0,
+                     st);
 }
 
 cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tmem_cols, const uint8_t* chunks,
@@ -527,8 +551,8 @@ cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tme
     return cudaErrorInvalidValue;
   EvalOut out;
   out.ext = ext;
-  return launch_core(prof, maxs, maxs, tmem_cols, p, (p + 127) / 128, chunks, y, tau, 0, out, err, pm,
-                     ctas_per_sm, st);
+  (void)tmem_cols;
+  return launch_core(prof, maxs, maxs, p, (p + 127) / 128, chunks, y, tau, 0, out, err, pm, ctas_per_sm, st);
 }
 
 }  // namespace hpt

@@ -91,3 +91,13 @@ def test_mixed_rejects_inexact_exponents(hpt):
         hpt.System.from_laurent(s2, cell, 1)
     assert err.value.code == 4
     hpt.System.from_laurent(s2, cell, 0).close()   # FP64 form takes it
+
+
+def test_mixed_refuses_shapes_beyond_on_chip_memory(hpt):
+    """n = 24 with 128 monomials per equation does not fit the evaluation
+    kernel's shared memory: HPT_ENOTSUP at creation, not a failing launch."""
+    s = W.laurent_system(31, 24, 128, -1, 1, 8, nnz=4)
+    alpha = W.random_alpha(31, 24, -1, 1)
+    with pytest.raises(hpt.HptError) as ei:
+        hpt.System.from_laurent(s, {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}, hpt.HPT_MIXED)
+    assert ei.value.code == 7
