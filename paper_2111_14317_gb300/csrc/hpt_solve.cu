@@ -81,6 +81,15 @@ __device__ __forceinline__ float t_min(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double t_min(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float t_sqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double t_sqrt(double a) { return sqrt(a); }
+// Reciprocal on the elimination's critical path: the approximate MUFU
+// reciprocal (at most 1 ulp off) for FP32, whose solves the Newton corrector
+// refines anyway; a correctly rounded one for FP64.
+__device__ __forceinline__ float t_rcp(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ double t_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ float t_abs(float a) { return fabsf(a); }
 __device__ __forceinline__ double t_abs(double a) { return fabs(a); }
 // 2^-e for m in [2^(e-1), 2^e): an exact power-of-two scale bringing m to
@@ -305,7 +314,7 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
 #pragma unroll
   for (int s = 0; s < R; ++s) used[s] = lane + G * s >= n;
   bool ok = true;
-  T pmax = 0, pmin = 0;
+  T pmax = 0, pmin = 0;   // extreme |u_jj|^2
 #pragma unroll 1
   for (int j = 0; j < n; ++j) {
     unsigned key = 0u;
@@ -340,10 +349,9 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
     const cx<T> pj = U[j * LD];
     const T p2 = abs2(pj);
     if (!(p2 > T(0)) || !isfinite(p2)) ok = false;
-    const T pa = t_sqrt(p2);
-    pmax = j == 0 ? pa : t_max(pmax, pa);
-    pmin = j == 0 ? pa : t_min(pmin, pa);
-    const T rp = T(1) / p2;   // one reciprocal per pivot, shared by all rows
+    pmax = j == 0 ? p2 : t_max(pmax, p2);
+    pmin = j == 0 ? p2 : t_min(pmin, p2);
+    const T rp = t_rcp(p2);   // one reciprocal per pivot, shared by all rows
     // multipliers; rows already used get 0, so the unpredicated update below
     // only shifts them (their values are no longer read)
     cx<T> l[R];
@@ -396,7 +404,7 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
       if (s == js) { vE = rE[s]; vN = rN[s]; }
     vE = shfl<T, G>(vE, j & (G - 1));
     vN = shfl<T, G>(vN, j & (G - 1));
-    const T ru = T(1) / abs2(ujj);
+    const T ru = t_rcp(abs2(ujj));
     const cx<T> xe = cmul_conj_scale(vE, ujj, ru), xn = cmul_conj_scale(vN, ujj, ru);
 #pragma unroll
     for (int s = 0; s < R; ++s) {
@@ -419,7 +427,7 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
     }
   }
   __syncwarp();   // the group's shared memory is reused by its next solve
-  cond = pmin > T(0) ? pmax / pmin : T(INFINITY);
+  cond = pmin > T(0) ? t_sqrt(pmax / pmin) : T(INFINITY);
   return ok;
 }
 
