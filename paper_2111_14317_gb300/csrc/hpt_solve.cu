@@ -570,9 +570,12 @@ __device__ __forceinline__ int64_t pm_begin(const PathMap& m) { return m.pos_beg
 // control.  T is the state and solve precision.  FP32 solves whose pivot
 // ratio (after equilibration) exceeds prm.cond_max are not applied here: the
 // position goes to redo_list and is solved again in FP64 by redo_fp64_kernel.
-// One system: G threads per path, a grid that covers every path once.
+// One system: G threads per path, a grid that covers every path once.  The
+// FP32 8-lane two-row form is register-capped for five resident blocks per
+// SM (shared memory allows five): more warps to cover each warp's dependent
+// chain of loads, shuffles and shared-memory round trips.
 template <typename T, int G, int R>
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(kSolveThreads, (sizeof(T) == 4 && G == 8 && R == 2) ? 5 : 1)
 solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S, hpt_params prm,
                     int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list) {
   extern __shared__ __align__(16) unsigned char smem[];
