@@ -141,6 +141,32 @@ constexpr float kInvTwoPi = 0.159154943091895336f;
 
 constexpr int kEvalThreads = 256;   // two warpgroups over the 128 TMEM lanes
 
+// Packed FP32 pairs (sm_100 family): one instruction rounds each half exactly
+// as the scalar operation would, so the results are those of the scalar code.
+__device__ __forceinline__ uint64_t f2pk(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2up(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {   // a * b + c
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // Barriers in shared memory: [0], [1] constant buffers; [2], [3] exponent
 // accumulators W[0], W[1]; [4] coefficient accumulator J.
 // MAP: positions come from a position map (many systems); otherwise position
@@ -326,26 +352,37 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
           tmem_ld8(tw + S.MP + c0, wim);
           tmem_wait_ld();
           uint32_t hr[4], hi_[4], lr[4], li[4];
+          // two monomials per pass, in packed FP32 pairs where the steps are
+          // plain arithmetic
+          const uint64_t TAU = f2pk(tau_d, tau_d), INV = f2pk(kInvTwoPi, kInvTwoPi);
+          const uint64_t NHI = f2pk(-kTwoPiHi, -kTwoPiHi), NLO = f2pk(-kTwoPiLo, -kTwoPiLo);
 #pragma unroll
           for (int q = 0; q < 8; q += 2) {
-            float er[2], ei[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const float wr = fmaf(tau_d, texp[c0 + q + u], __uint_as_float(wre[q + u]));
-              const float wi = __uint_as_float(wim[q + u]);
-              const float kq = rintf(wi * kInvTwoPi);
-              const float rr = fmaf(-kq, kTwoPiLo, fmaf(-kq, kTwoPiHi, wi));
-              float sn, cs;
-              __sincosf(rr, &sn, &cs);
-              const float m = __expf(wr);
-              er[u] = m * cs;
-              ei[u] = m * sn;
-            }
-            const __nv_bfloat162 hre = __floats2bfloat162_rn(er[0], er[1]);
-            const __nv_bfloat162 him = __floats2bfloat162_rn(ei[0], ei[1]);
+            const float2 te = *(const float2*)&texp[c0 + q];
+            const uint64_t wr = fma2(TAU, f2pk(te.x, te.y), f2pk(__uint_as_float(wre[q]), __uint_as_float(wre[q + 1])));
+            const uint64_t wi = f2pk(__uint_as_float(wim[q]), __uint_as_float(wim[q + 1]));
+            float t0, t1;
+            f2up(mul2(wi, INV), t0, t1);
+            const uint64_t kq = f2pk(rintf(t0), rintf(t1));
+            float r0, r1, w0, w1;
+            f2up(fma2(kq, NLO, fma2(kq, NHI, wi)), r0, r1);   // Cody-Waite: wi - kq hi - kq lo
+            f2up(wr, w0, w1);
+            float s0, c0_, s1, c1_;
+            __sincosf(r0, &s0, &c0_);
+            __sincosf(r1, &s1, &c1_);
+            const uint64_t m = f2pk(__expf(w0), __expf(w1));
+            float er0, er1, ei0, ei1;
+            const uint64_t er = mul2(m, f2pk(c0_, c1_)), ei = mul2(m, f2pk(s0, s1));
+            f2up(er, er0, er1);
+            f2up(ei, ei0, ei1);
+            const __nv_bfloat162 hre = __floats2bfloat162_rn(er0, er1);
+            const __nv_bfloat162 him = __floats2bfloat162_rn(ei0, ei1);
             const float2 fre = __bfloat1622float2(hre), fim = __bfloat1622float2(him);
-            const __nv_bfloat162 lre = __floats2bfloat162_rn(er[0] - fre.x, er[1] - fre.y);
-            const __nv_bfloat162 lim = __floats2bfloat162_rn(ei[0] - fim.x, ei[1] - fim.y);
+            float lr0, lr1, li0, li1;
+            f2up(sub2(er, f2pk(fre.x, fre.y)), lr0, lr1);
+            f2up(sub2(ei, f2pk(fim.x, fim.y)), li0, li1);
+            const __nv_bfloat162 lre = __floats2bfloat162_rn(lr0, lr1);
+            const __nv_bfloat162 lim = __floats2bfloat162_rn(li0, li1);
             hr[q / 2] = *(const uint32_t*)&hre;
             hi_[q / 2] = *(const uint32_t*)&him;
             lr[q / 2] = *(const uint32_t*)&lre;
