@@ -252,7 +252,10 @@ hpt_status hpt_step_static(hpt_system sys, int64_t p, const hpt_paths* state, in
 
 /* Whole tracks: start points y0_dev[p*n] complex128 at tau0 -> tau = 0, then an
  * FP64 Newton polish at t = 1 of the converged paths.  Writes x_out_dev[p*n]
- * complex128, status_dev[p], steps_dev[p].  Synchronises the stream. */
+ * complex128, status_dev[p], steps_dev[p].  Synchronises the stream.  The
+ * HPT_MIXED form runs as a one-system hpt_batch_track (created on first use
+ * and kept with the handle), which compacts finished paths out of the
+ * launches; results are those of stepping all paths together. */
 hpt_status hpt_track(hpt_system sys, int64_t p, const void* y0_dev, const hpt_params* params,
                      void* x_out_dev, int32_t* status_dev, int32_t* steps_dev, void* stream);
 

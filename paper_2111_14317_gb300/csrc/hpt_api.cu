@@ -195,6 +195,17 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
   if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
   if (p == 0) return HPT_OK;
   if (!y0 || !x_out) { set_error("y0 or x_out is NULL"); return HPT_EINVAL; }
+  if (s->prec == HPT_MIXED) {
+    // the mixed form tracks through a one-system batch (cached in the handle):
+    // finished paths leave the launches after every round instead of being
+    // evaluated until the last path ends; per path the arithmetic is the same
+    if (!s->self_batch) {
+      hpt_batch b = nullptr;
+      if ((rc = hpt_batch_create(1, &s, &b))) return rc;
+      s->self_batch = b;
+    }
+    return hpt_batch_track(s->self_batch, &p, y0, prm, x_out, status_out, steps_out, stream);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int n = s->n;
   const size_t cs = csize(s);

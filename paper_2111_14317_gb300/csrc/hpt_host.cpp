@@ -774,6 +774,7 @@ hpt_status hpt_destroy(hpt_system s) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
+  if (s->self_batch) hpt_batch_destroy(s->self_batch);
   cudaFree(s->d_msz);
   cudaFree(s->d_off);
   cudaFree(s->d_ahat);

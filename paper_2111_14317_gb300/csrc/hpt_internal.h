@@ -129,6 +129,7 @@ struct hpt_system_s {
   void* d_track = nullptr;           // hpt_track state
   size_t track_bytes = 0;
   int32_t* h_count = nullptr;        // pinned host counter
+  hpt_batch self_batch = nullptr;    // hpt_track of the mixed form: a one-system batch
 
   // profiling
   bool profiling = false;

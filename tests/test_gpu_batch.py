@@ -55,6 +55,24 @@ def _run_batch(hpt, systems, paths, prm):
     return b, y0, x.cpu().numpy(), st.cpu().numpy(), sp.cpu().numpy()
 
 
+def _track_by_steps(hpt, h, y0, prm):
+    """The paths of one system stepped together with hpt_step until none is
+    active, then the FP64 polish of the converged ones (hpt_polish): a track
+    without the batch machinery (no compaction, no graph)."""
+    p, n = y0.shape
+    st = hpt.PathState(p, n, hpt.HPT_MIXED)
+    h.paths_init(st, torch.from_numpy(np.ascontiguousarray(y0)).cuda(), prm)
+    done = 0
+    while done <= prm.max_steps + 32:
+        h.step(st, 32, prm)
+        done += 32
+        if int((st.status == hpt.ACTIVE).sum().item()) == 0:
+            break
+    x = st.y_acc.to(torch.complex128)
+    h.polish(x, st.status, prm)
+    return x.cpu().numpy(), st.status.cpu().numpy(), st.steps.cpu().numpy()
+
+
 def _split(systems, paths, x, st, sp):
     out, vo, po = [], 0, 0
     for (s, _, _), p in zip(systems, paths):
@@ -65,7 +83,9 @@ def _split(systems, paths, x, st, sp):
 
 
 def test_batch_equals_per_system_track_one_shape(hpt):
-    """n in [9, 16] (one solve shape): bit-identical to hpt_track per system."""
+    """n in [9, 16] (one solve shape): bit-identical to stepping each system's
+    paths with hpt_step and polishing them (no batch machinery), and to
+    hpt_track (which runs as a one-system batch)."""
     systems = _systems(hpt, _indices(9, 16, 5))
     paths = [130, 0, 127, 1, 256]
     prm = hpt.Params(tol_accept=3e-3)
@@ -73,10 +93,12 @@ def test_batch_equals_per_system_track_one_shape(hpt):
     for (s, pr, h), p, y, (xb, stb, spb) in zip(systems, paths, y0, _split(systems, paths, x, st, sp)):
         if p == 0:
             continue
-        xs, sts, sps = h.track(torch.from_numpy(y).cuda(), prm)
-        assert np.array_equal(stb, sts.cpu().numpy())
-        assert np.array_equal(spb, sps.cpu().numpy())
-        assert np.array_equal(xb, xs.cpu().numpy())
+        xs, sts, sps = _track_by_steps(hpt, h, y, prm)
+        assert np.array_equal(stb, sts)
+        assert np.array_equal(spb, sps)
+        assert np.array_equal(xb, xs)
+        xt, stt, spt = h.track(torch.from_numpy(y).cuda(), prm)
+        assert np.array_equal(xb, xt.cpu().numpy()) and np.array_equal(stb, stt.cpu().numpy())
     st_all = st
     assert (st_all == hpt.CONVERGED).mean() > 0.9, np.bincount(st_all)
     r = b.stats()
