@@ -196,3 +196,20 @@ def test_batch_refuses_fp64_handles(hpt):
     with pytest.raises(hpt.HptError) as ei:
         hpt.Batch([h])
     assert ei.value.code == 7
+
+
+def test_batch_fp64_resolve_everything(hpt):
+    """Every FP32 solve of a mixed-shape batch redone in FP64 (cond_max = 1,
+    the warp solves with its largest n, identity rows pad smaller systems):
+    the polished solutions equal those of the FP32 solves."""
+    idx = _indices(4, 8, 1) + _indices(9, 16, 1) + _indices(17, 24, 1)
+    systems = _systems(hpt, idx)
+    paths = [64, 64, 64]
+    _, _, x1, st1, _ = _run_batch(hpt, systems, paths, hpt.Params(tol_accept=3e-3, cond_max=1.0))
+    _, _, x2, st2, _ = _run_batch(hpt, systems, paths, hpt.Params(tol_accept=3e-3))
+    assert (st1 == st2).mean() > 0.97
+    for (s, _, _), (xa, sa, _), (xb, sb, _) in zip(systems, _split(systems, paths, x1, st1, st1),
+                                                    _split(systems, paths, x2, st2, st2)):
+        both = (sa == hpt.CONVERGED) & (sb == hpt.CONVERGED)
+        rel = np.abs(xa[both] - xb[both]).max(-1) / np.maximum(1.0, np.abs(xb[both]).max(-1))
+        assert (rel < 1e-9).mean() > 0.97, (s.n, np.sort(rel)[-5:])

@@ -76,3 +76,35 @@ def test_step_resume_is_exact(hpt, oracle_mod, prec):
     for k in ha:
         assert torch.equal(ha[k], hb[k]), k
     h.close()
+
+
+@pytest.mark.parametrize("n,m", [(6, 10), (16, 32), (24, 40)])
+def test_fp64_resolve_path(hpt, n, m):
+    """The mixed form's FP64 re-solve (redo_fp64_kernel): with cond_max = 1
+    every FP32 solve is redone in FP64 from the same FP32 Jacobian; the step
+    agrees with the all-FP32 step (cond_max = 1e30) to FP32 solve accuracy."""
+    sysm = W.laurent_system(40 + n, n, m, -3, 3, 64, nnz=min(4, n))
+    alpha = W.random_alpha(40 + n, n)
+    cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
+    h = hpt.System.from_laurent(sysm, cell, hpt.HPT_MIXED)
+    y, t = W.random_points(9, 2000, n)
+    out = []
+    for cmax in (1.0, 1e30):
+        st = hpt.PathState(2000, n, hpt.HPT_MIXED)
+        yd = torch.from_numpy(y).cuda().to(torch.complex64)
+        st.y.copy_(yd)
+        st.y_acc.copy_(yd)
+        st.tau.copy_(torch.from_numpy(np.log(t)))
+        st.tau_acc.copy_(st.tau)
+        st.dtau.fill_(1e-3)
+        st.accepts.fill_(1)
+        h.step(st, 1, hpt.Params(tol_accept=3e-3, cond_max=cmax))
+        torch.cuda.synchronize()
+        out.append(st.to_host())
+    a, b = out
+    same = (a["accepts"] == b["accepts"]) & (a["status"] == b["status"])
+    assert same.float().mean() > 0.97
+    ya, yb = a["y_acc"].numpy()[same.numpy()], b["y_acc"].numpy()[same.numpy()]
+    rel = np.abs(ya - yb).max(-1) / np.maximum(1.0, np.abs(yb).max(-1))
+    assert np.median(rel) < 1e-5 and (rel < 1e-3).mean() > 0.97
+    h.close()
