@@ -222,20 +222,40 @@ def run_gpu(args):
         # second pass: CUDA events around every kernel on the launching stream
         timed(True)
         kern = h.profile_read()
-        # end-to-end through the C ABI: pinned host state -> device, step, -> host
-        host = {k: v.pin_memory() for k, v in pristine.items()}
-        back = {k: torch.empty_like(v).pin_memory() for k, v in pristine.items()}
-        h2d = sum(v.numel() * v.element_size() for v in host.values())
-        e2e_steps = max(3, steps // 2)
+        # end-to-end through the C ABI: every step copies the whole state (one
+        # contiguous arena) from pinned host memory to the device, steps it and
+        # copies it back.  Two device states alternate, with the copies in on
+        # one stream, the steps on another and the copies out on a third, so
+        # step i runs while step i+1's input arrives and step i-1's result
+        # leaves (each direction is ordered against the others by events).
+        e2e_steps = max(4, steps // 2)
+        hin = [hpt.PathState(PATHS, N_VARS, prec, device="cpu", pin=True) for _ in range(2)]
+        hout = [hpt.PathState(PATHS, N_VARS, prec, device="cpu", pin=True) for _ in range(2)]
+        for hh in hin:
+            hh.load(pristine)
+        dev2 = [st, hpt.PathState(PATHS, N_VARS, prec, device=dev)]
+        h2d = hin[0].arena.numel()
+        s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_run = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            for k, v in host.items():
-                getattr(st, k).copy_(v, non_blocking=True)
-            h.step(st, 1, prm)
-            for k, v in back.items():
-                v.copy_(getattr(st, k), non_blocking=True)
-            torch.cuda.synchronize()
+        for i in range(e2e_steps):
+            b = i % 2
+            with torch.cuda.stream(s_in):
+                if i >= 2:
+                    s_in.wait_event(ev_out[b])          # step i-2's result has left dev2[b]
+                dev2[b].arena.copy_(hin[b].arena, non_blocking=True)
+                ev_in[b].record(s_in)
+            s_run.wait_event(ev_in[b])
+            h.step(dev2[b], 1, prm, stream=s_run)
+            ev_run[b].record(s_run)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_run[b])
+                hout[b].arena.copy_(dev2[b].arena, non_blocking=True)
+                ev_out[b].record(s_out)
+        torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         out[form] = dict(steps=steps, ms_per_step=tot / steps, ms_list=ms, kernels=kern,
                          clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=h2d,

@@ -208,26 +208,40 @@ def binomial_points(n, m, exponents, coeffs, pairs, k):
 
 
 class PathState:
-    """Caller-owned structure-of-arrays path state on the device."""
+    """Caller-owned structure-of-arrays path state on a device (or in pinned
+    host memory with device="cpu", pin=True): every field is a view into one
+    contiguous byte arena, so the whole state moves between host and device
+    in one copy (`arena`)."""
 
-    def __init__(self, p, n, precision, device="cuda"):
+    FIELDS = ("y", "tau", "dtau", "y_acc", "tau_acc", "dE_acc", "status", "steps", "accepts",
+              "rejects", "streak")
+
+    def __init__(self, p, n, precision, device="cuda", pin=False):
         cdt = torch.complex128 if precision == HPT_FP64 else torch.complex64
-        z = lambda *s, dt: torch.zeros(*s, dtype=dt, device=device)  # noqa: E731
-        self.p, self.n = p, n
-        self.y, self.y_acc, self.dE_acc = (z(p, n, dt=cdt) for _ in range(3))
-        self.tau, self.dtau, self.tau_acc = (z(p, dt=torch.float64) for _ in range(3))
-        self.status, self.steps, self.accepts, self.rejects, self.streak = (
-            z(p, dt=torch.int32) for _ in range(5))
+        self.p, self.n, self.precision = p, n, precision
+        shapes = {"y": ((p, n), cdt), "y_acc": ((p, n), cdt), "dE_acc": ((p, n), cdt),
+                  "tau": ((p,), torch.float64), "dtau": ((p,), torch.float64), "tau_acc": ((p,), torch.float64),
+                  "status": ((p,), torch.int32), "steps": ((p,), torch.int32), "accepts": ((p,), torch.int32),
+                  "rejects": ((p,), torch.int32), "streak": ((p,), torch.int32)}
+        offs, off = {}, 0
+        for k in self.FIELDS:
+            shp, dt = shapes[k]
+            nb = int(np.prod(shp)) * torch.empty((), dtype=dt).element_size()
+            offs[k] = (off, nb)
+            off += (nb + 255) // 256 * 256
+        self.arena = torch.zeros(max(off, 256), dtype=torch.uint8, device=device)
+        if pin:
+            self.arena = self.arena.pin_memory()
+        for k in self.FIELDS:
+            shp, dt = shapes[k]
+            o, nb = offs[k]
+            setattr(self, k, self.arena[o:o + nb].view(dt).view(*shp))
 
     def _c(self):
-        return _Paths(*[t.data_ptr() for t in (self.y, self.tau, self.dtau, self.y_acc, self.tau_acc,
-                                               self.dE_acc, self.status, self.steps, self.accepts,
-                                               self.rejects, self.streak)])
+        return _Paths(*[getattr(self, k).data_ptr() for k in self.FIELDS])
 
     def to_host(self):
-        return {k: getattr(self, k).cpu() for k in ("y", "tau", "dtau", "y_acc", "tau_acc",
-                                                     "dE_acc", "status", "steps", "accepts",
-                                                     "rejects", "streak")}
+        return {k: getattr(self, k).cpu() for k in self.FIELDS}
 
     def load(self, host):
         for k, v in host.items():
