@@ -122,7 +122,11 @@ typedef struct {
   int32_t grow_after;   /* default 3 */
   int32_t max_steps;    /* default 10000 */
   double div_bound;     /* default 1e8 */
-  double polish_tol;    /* default 1e-13: FP64 Newton polish at t = 1 stops below */
+  double polish_tol;    /* default 1e-13: the FP64 Newton polish at t = 1 stops when the
+                           relative correction |dN|/max(1,|x|) is below it, or when the
+                           error it leaves is: r_k^3 / r_{k-1}^2 <= polish_tol for the last
+                           two corrections once they shrink at least tenfold (quadratic
+                           convergence) */
   int32_t polish_iters; /* default 8 */
   int32_t check_every;  /* hpt_track: steps between host checks, default 32 */
   double cond_max;      /* HPT_MIXED: pivot-ratio bound above which the solve is

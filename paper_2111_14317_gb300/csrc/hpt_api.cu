@@ -72,19 +72,21 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
   return HPT_OK;
 }
 
-hpt_status polish_impl(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm,
+hpt_status polish_impl(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
                        cudaStream_t st) {
   const int64_t chunk = std::min<int64_t>(p, kChunk);
   hpt_status rc = ensure_scratch(s, ext_entries(chunk, s->n) * 16);
   if (rc) return rc;
-  return polish_paths(s, p, x, done, prm, s->d_scratch, chunk, st);
+  return polish_paths(s, p, x, done, last, prm, s->d_scratch, chunk, st);
 }
 
 }  // namespace
 
-hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm, void* ext,
-                        int64_t chunk, cudaStream_t st) {
+hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
+                        void* ext, int64_t chunk, cudaStream_t st) {
   const int n = s->n;
+  cudaError_t e0 = cudaMemsetAsync(last, 0, (size_t)p * sizeof(float), st);
+  if (e0 != cudaSuccess) return cuda_fail(e0, "polish init");
   for (int it = 0; it < prm.polish_iters; ++it) {
     for (int64_t q0 = 0; q0 < p; q0 += chunk) {
       const int64_t cnt = std::min(chunk, p - q0);
@@ -93,7 +95,7 @@ hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, const h
       void* xq = (char*)x + q0 * n * 16;
       cudaError_t e = launch_eval_fp64(s, cnt, xq, nullptr, 0, out, st);
       if (e != cudaSuccess) return cuda_fail(e, "polish evaluation launch");
-      e = launch_newton_update(s, cnt, ext, xq, done + q0, prm.polish_tol, st);
+      e = launch_newton_update(s, cnt, ext, xq, done + q0, last + q0, prm.polish_tol, st);
       if (e != cudaSuccess) return cuda_fail(e, "polish update launch");
     }
   }
@@ -219,7 +221,7 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
   const size_t o_y = take(p * n * cs), o_ya = take(p * n * cs), o_de = take(p * n * cs);
   const size_t o_tau = take(p * 8), o_dt = take(p * 8), o_ta = take(p * 8);
   const size_t o_st = take(p * 4), o_sp = take(p * 4), o_ac = take(p * 4), o_rj = take(p * 4),
-               o_sk = take(p * 4), o_done = take(p * 4), o_cnt = take(4);
+               o_sk = take(p * 4), o_done = take(p * 4), o_last = take(p * 4), o_cnt = take(4);
   if ((rc = ensure_track(s, off))) return rc;
   char* b = (char*)s->d_track;
   hpt_paths S;
@@ -235,6 +237,7 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
   S.rejects = (int32_t*)(b + o_rj);
   S.streak = (int32_t*)(b + o_sk);
   int32_t* done = (int32_t*)(b + o_done);
+  float* last = (float*)(b + o_last);
   int32_t* cnt = (int32_t*)(b + o_cnt);
   if ((rc = hpt_paths_init(s, p, y0, prm, &S, stream))) return rc;
   const int every = prm->check_every > 0 ? prm->check_every : 32;
@@ -250,7 +253,7 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
   }
   cudaError_t e = launch_finish_track(s, p, S, x_out, status_out, steps_out, done, st);
   if (e != cudaSuccess) return cuda_fail(e, "track output");
-  if ((rc = polish_impl(s, p, x_out, done, *prm, st))) return rc;
+  if ((rc = polish_impl(s, p, x_out, done, last, *prm, st))) return rc;
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "track");
   return HPT_OK;
@@ -264,11 +267,12 @@ hpt_status hpt_polish(hpt_system s, int64_t p, void* x, const int32_t* status, c
   if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
   if (p == 0) return HPT_OK;
   if (!x) { set_error("x is NULL"); return HPT_EINVAL; }
-  if ((rc = ensure_track(s, (size_t)p * 4))) return rc;
+  const size_t done_bytes = ((size_t)p * 4 + 255) / 256 * 256;
+  if ((rc = ensure_track(s, done_bytes + (size_t)p * 4))) return rc;
   int32_t* done = (int32_t*)s->d_track;
   cudaError_t e = launch_init_done(p, status, done, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "polish init");
-  return polish_impl(s, p, x, done, *prm, (cudaStream_t)stream);
+  return polish_impl(s, p, x, done, (float*)((char*)s->d_track + done_bytes), *prm, (cudaStream_t)stream);
 }
 
 hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, void* gc, void* stream) {

@@ -176,7 +176,7 @@ struct Problem {
   int64_t cap_bucket[kBuckets] = {0, 0, 0, 0};
   int64_t pmax = 0;              // largest paths[s]
   // byte offsets in d_state
-  size_t o_y, o_ya, o_de, o_tau, o_dt, o_ta, o_st, o_sp, o_ac, o_rj, o_sk, o_done, o_vofs, o_pb, o_np, o_tmp,
+  size_t o_y, o_ya, o_de, o_tau, o_dt, o_ta, o_st, o_sp, o_ac, o_rj, o_sk, o_done, o_last, o_vofs, o_pb, o_np, o_tmp,
       o_cnt, o_tb, o_list, o_tsys, o_ctl, o_rc, o_rl, o_ext, total;
 };
 
@@ -213,6 +213,7 @@ Problem plan(const hpt_batch_s* b, const int64_t* paths) {
   q.o_rj = take(P * 4);
   q.o_sk = take(P * 4);
   q.o_done = take(P * 4);
+  q.o_last = take(P * 4);
   q.o_vofs = take(P * 8);
   q.o_pb = take((size_t)b->nsys * 8);
   q.o_np = take((size_t)b->nsys * 4);
@@ -429,6 +430,7 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
   }
   // outputs, then the FP64 polish per system
   int32_t* done = (int32_t*)(d + q.o_done);
+  float* last = (float*)(d + q.o_last);
   for (int s = 0; s < b->nsys && e == cudaSuccess; ++s) {
     if (!paths[s]) continue;
     e = launch_finish_track(b->sys[s], paths[s], sub_state(S, q.pb[s], q.vb[s]), (char*)x_out + q.vb[s] * 16,
@@ -446,6 +448,8 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
   pm.sys_n = b->d_sys_n;
   pm.vofs = (const int64_t*)(d + q.o_vofs);
   pm.nmax = b->nmax;
+  e = cudaMemsetAsync(last, 0, (size_t)q.P * sizeof(float), st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch polish init");
   for (int it = 0; it < prm.polish_iters; ++it) {
     e = enqueue_compaction(b, q, done, 0, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_ctl, ctl, kCtlWords * 4, cudaMemcpyDeviceToHost, st);
@@ -459,7 +463,7 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
       const int sh = bk < 2 ? bk : 2;   // FP64: n <= 8, <= 16, <= 32 lane groups
       e = launch_eval_fp64_map(sh, b->d_f64, q.cap_bucket[bk], x_out, nullptr, pm, d + q.o_ext, st);
       if (e == cudaSuccess)
-        e = launch_newton_map(sh, q.cap_bucket[bk], d + q.o_ext, x_out, done, prm.polish_tol, pm, st);
+        e = launch_newton_map(sh, q.cap_bucket[bk], d + q.o_ext, x_out, done, last, prm.polish_tol, pm, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batch polish");
   }

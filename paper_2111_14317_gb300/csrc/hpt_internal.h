@@ -214,16 +214,18 @@ int solve_shape_of(int n);
 constexpr int kShape8x3 = 3;   // FP32 solve only: 8 lanes x 3 rows per path, n <= 24
 // FP64 Newton polish update over the position range [*pm.pos_begin,
 // *pm.npos) of a map (shape as above; cap bounds the range's length); x is
-// complex128 at pm.vofs, done per path.
-cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, int32_t* done, double tol,
-                              const PathMap& pm, cudaStream_t st);
+// complex128 at pm.vofs, done and last (the previous relative correction)
+// per path.
+cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, int32_t* done, float* last,
+                              double tol, const PathMap& pm, cudaStream_t st);
 cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st);
 cudaError_t launch_redo_fp64_shape(int shape, const StepArgs& a, cudaStream_t st);
 
-// Newton update at t = 1 for the polish: x += dN where the relative
-// correction is still above tol; done[q] set once it is below.
+// Newton update at t = 1 for the polish: x += dN where the path is not done;
+// done[q] set once the error left is below tol (last[q]: the previous
+// relative correction, 0 before the first).
 cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void* x,
-                                 int32_t* done, double tol, cudaStream_t st);
+                                 int32_t* done, float* last, double tol, cudaStream_t st);
 
 // Adjoint: per-solution lambda and the per-block partial sums of the
 // coefficient gradient (two kernels).
@@ -233,9 +235,9 @@ cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void*
 
 // FP64 Newton polish at t = 1 of p solutions x (complex128) whose done flag
 // is 0, polish_iters rounds over chunks of `chunk` paths; ext holds the
-// extended Jacobian of a chunk (FP64).
-hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, const hpt_params& prm, void* ext,
-                        int64_t chunk, cudaStream_t st);
+// extended Jacobian of a chunk (FP64), last p floats of scratch.
+hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
+                        void* ext, int64_t chunk, cudaStream_t st);
 hpt_status check_params(const hpt_params* prm);
 hpt_status cuda_fail(cudaError_t e, const char* what);
 

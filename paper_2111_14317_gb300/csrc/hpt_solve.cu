@@ -715,14 +715,17 @@ redo_fp64_kernel(int n0, const void* __restrict__ ext, hpt_paths S, hpt_params p
   }
 }
 
-// Newton polish update at t = 1 (FP64): x += dN until |dN|/max(1,|x|) <= tol.
+// Newton polish update at t = 1 (FP64): x += dN until the error left is below
+// tol: |dN|/max(1,|x|) <= tol, or, once the corrections shrink quadratically,
+// the error after this update, about r_k^3 / r_{k-1}^2 for the relative
+// corrections r of the last two iterations (last[] keeps r_{k-1}; 0: none).
 // MAP: positions [*pm.pos_begin, *pm.npos) of a position map (a warp's
 // positions lie in one tile, so n is warp-uniform); otherwise the p paths of
 // one system.
 template <int G, int R, bool MAP>
 __global__ void __launch_bounds__(kSolveThreads)
 newton_kernel(int n0, int64_t p, const void* __restrict__ ext, double2* __restrict__ x,
-              int32_t* __restrict__ done, double tol, PathMap pm) {
+              int32_t* __restrict__ done, float* __restrict__ last, double tol, PathMap pm) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & (G - 1);
   const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G + (MAP ? (int64_t)*pm.pos_begin : 0);
@@ -783,7 +786,12 @@ newton_kernel(int n0, int64_t p, const void* __restrict__ ext, double2* __restri
     const int j = lane + G * s;
     if (j < n) st<double>(x, vbase + j, y[s]);
   }
-  if (lane == 0 && nd / fmax(1.0, ny) <= tol) done[path] = 1;
+  if (lane == 0) {
+    const double r = nd / fmax(1.0, ny), rp = (double)last[path];
+    const bool settled = rp > 0.0 && r <= 0.1 * rp && r * r * r <= tol * rp * rp;
+    if (r <= tol || settled) done[path] = 1;
+    last[path] = (float)r;
+  }
 }
 
 // Adjoint, part 1: per solution, lambda from J^H lambda = gx (J from the
@@ -978,20 +986,20 @@ cudaError_t launch_redo_shape(const StepArgs& a, cudaStream_t st) {
 }
 
 template <int G, int R>
-cudaError_t launch_newton_shape(int n, int64_t p, const void* ext, void* x, int32_t* done, double tol,
-                                const PathMap* pm, cudaStream_t st) {
+cudaError_t launch_newton_shape(int n, int64_t p, const void* ext, void* x, int32_t* done, float* last,
+                                double tol, const PathMap* pm, cudaStream_t st) {
   const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
   if (pm) {
     cudaError_t e = set_smem(newton_kernel<G, R, true>, smem);
     if (e != cudaSuccess) return e;
     newton_kernel<G, R, true><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(
-        n, p, ext, (double2*)x, done, tol, *pm);
+        n, p, ext, (double2*)x, done, last, tol, *pm);
     return cudaGetLastError();
   }
   cudaError_t e = set_smem(newton_kernel<G, R, false>, smem);
   if (e != cudaSuccess) return e;
   newton_kernel<G, R, false><<<blocks_for(p * G, kSolveThreads), kSolveThreads, smem, st>>>(
-      n, p, ext, (double2*)x, done, tol, PathMap());
+      n, p, ext, (double2*)x, done, last, tol, PathMap());
   return cudaGetLastError();
 }
 
@@ -1040,13 +1048,13 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
 
 int solve_shape_of(int n) { return shape_of(n); }
 
-cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, int32_t* done, double tol,
-                              const PathMap& pm, cudaStream_t st) {
+cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, int32_t* done, float* last,
+                              double tol, const PathMap& pm, cudaStream_t st) {
   if (cap <= 0) return cudaSuccess;
   if (!pm.list || !pm.tile_sys || !pm.sys_n || !pm.vofs || !pm.npos || !pm.pos_begin) return cudaErrorInvalidValue;
-  return shape == 0 ? launch_newton_shape<8, 1>(0, cap, ext, x, done, tol, &pm, st)
-       : shape == 1 ? launch_newton_shape<8, 2>(0, cap, ext, x, done, tol, &pm, st)
-                    : launch_newton_shape<32, 1>(0, cap, ext, x, done, tol, &pm, st);
+  return shape == 0 ? launch_newton_shape<8, 1>(0, cap, ext, x, done, last, tol, &pm, st)
+       : shape == 1 ? launch_newton_shape<8, 2>(0, cap, ext, x, done, last, tol, &pm, st)
+                    : launch_newton_shape<32, 1>(0, cap, ext, x, done, last, tol, &pm, st);
 }
 
 cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st) {
@@ -1065,13 +1073,13 @@ cudaError_t launch_redo_fp64_shape(int shape, const StepArgs& a, cudaStream_t st
 }
 
 cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void* x, int32_t* done,
-                                 double tol, cudaStream_t st) {
+                                 float* last, double tol, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
   const int shape = shape_of(s->n);
   int pi = prof_begin(s, "newton_fp64", st);
-  cudaError_t e = shape == 0 ? launch_newton_shape<8, 1>(s->n, p, ext, x, done, tol, nullptr, st)
-                : shape == 1 ? launch_newton_shape<8, 2>(s->n, p, ext, x, done, tol, nullptr, st)
-                             : launch_newton_shape<32, 1>(s->n, p, ext, x, done, tol, nullptr, st);
+  cudaError_t e = shape == 0 ? launch_newton_shape<8, 1>(s->n, p, ext, x, done, last, tol, nullptr, st)
+                : shape == 1 ? launch_newton_shape<8, 2>(s->n, p, ext, x, done, last, tol, nullptr, st)
+                             : launch_newton_shape<32, 1>(s->n, p, ext, x, done, last, tol, nullptr, st);
   prof_end(s, pi, st);
   return e;
 }
