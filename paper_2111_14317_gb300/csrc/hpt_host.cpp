@@ -343,11 +343,14 @@ static MixedLayout mixed_layout(int n, int max_m) {
   L.KX = round_up(3 * n, 16);
   L.NJ = round_up(2 * (n + 2), 16);
   L.KC = 2 * L.MP;
+  // exponent part (operand and t-exponents) first, coefficient part after,
+  // each starting on a 128-byte boundary, so that the evaluation can copy
+  // them separately
   L.off_bexp = 0;
-  L.off_bhi = L.MP * L.KX * 2;
+  L.off_texp = L.MP * L.KX * 2;
+  L.off_bhi = round_up(L.off_texp + L.MP * 4, 128);
   L.off_blo = L.off_bhi + L.NJ * L.KC * 2;
-  L.off_texp = L.off_blo + L.NJ * L.KC * 2;
-  L.chunk_bytes = round_up(L.off_texp + L.MP * 4, 128);
+  L.chunk_bytes = round_up(L.off_blo + L.NJ * L.KC * 2, 128);
   int cols = 4 * L.MP + L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
   while (t < cols) t *= 2;
   L.tmem_cols = t;

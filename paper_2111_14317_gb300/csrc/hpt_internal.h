@@ -16,12 +16,14 @@ constexpr int kMixedMaxM = 128;    // monomials per equation in the mixed form
 constexpr int kTile = 128;         // paths per tensor-core tile (MMA M)
 
 // Per-equation constant image of the mixed form, laid out exactly as the
-// kernel's shared-memory operands (bulk-copied per equation).
+// kernel's shared-memory operands (bulk-copied per equation), in two parts:
+// the exponent part [bexp | texp] and, from off_bhi (128-byte aligned), the
+// coefficient part [bhi | blo].
 //   bexp : MP x KX bf16, exponent operand, K index s*n + j holds a_j for the
 //          three splits s of log y (K-major, 8x8 core matrices, no swizzle)
+//   texp : MP floats, t-exponent numerators e (0 on padding)
 //   bhi  : NJ x KC bf16, high part of the realified B_k^T
 //   blo  : NJ x KC bf16, low part
-//   texp : MP floats, t-exponent numerators e (0 on padding)
 struct MixedLayout {
   int MP = 0;   // monomials per equation, padded to 16
   int KX = 0;   // 3n padded to 16

@@ -40,9 +40,11 @@ struct MixedArgs {
   MixedSys sys;   // the system of a single-system launch
   int tmem_cols;
   int nbuf;   // constant-image buffers: 2 (prefetch next equation) or 1
+  int split;  // 1: the buffers hold only the exponent part; the coefficient part
+              // has one buffer of its own (s_cpart), refilled once its GEMM is done
   int wbuf;   // exponent accumulators W in tensor memory: 2 (next GEMM under the epilogue) or 1
   // shared-memory carve-up (bytes from the 1024-aligned base)
-  int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_bar;
+  int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_cpart, s_bar;
   int64_t p;
   int ntiles;
 };
@@ -168,10 +170,14 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
 }
 
 // Barriers in shared memory: [0], [1] constant buffers; [2], [3] exponent
-// accumulators W[0], W[1]; [4] coefficient accumulator J.
+// accumulators W[0], W[1]; [4] coefficient accumulator J; [5] coefficient
+// part buffer (split mode).
 // MAP: positions come from a position map (many systems); otherwise position
 // = path of the single system described by P.sys.
-template <bool MAP>
+// SPLIT: the constant buffers hold only the exponent parts; the coefficient
+// part has a buffer of its own (large shapes; a compile-time choice, so that
+// the other form carries none of its code).
+template <bool MAP, bool SPLIT>
 __global__ void __launch_bounds__(kEvalThreads, 2)
 eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __restrict__ tin, int tau_is_t,
                   const uint8_t* __restrict__ chunks, float2* __restrict__ ext, float2* __restrict__ oH,
@@ -201,7 +207,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   auto sys_of = [&](int tile) { return pm.tile_sys ? pm.tile_sys[tile] : 0; };
 
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) mbar_init(su32(&bars[i]), 1);
+    for (int i = 0; i < (SPLIT ? 6 : 5); ++i) mbar_init(su32(&bars[i]), 1);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -237,21 +243,39 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   };
 
   // constant images for the first nbuf work items; (lit, lk) is the next
-  // item to load, `issued` the number of items loaded so far (thread 0)
+  // item to load, `issued` the number of items loaded so far (thread 0).  In
+  // split mode these loads carry the exponent part only and a second cursor
+  // (cit, ck, cissued) loads the coefficient parts, one item ahead.
   int lit = 0, lk = 0, issued = 0;
-  auto load_next = [&]() {
-    if (lit >= my_tiles) return;
-    const int ls = sys_of(tile_of(lit));
+  int cit = 0, ck = 0, cissued = 0;
+  auto load_item = [&](int& xit, int& xk, bool cpart) {
+    const int ls = sys_of(tile_of(xit));
     const int ln = pm.sys_tab ? pm.sys_tab[ls].n : P.sys.n;
     const int lbytes = pm.sys_tab ? pm.sys_tab[ls].chunk_bytes : P.sys.chunk_bytes;
+    const int lsplit = pm.sys_tab ? pm.sys_tab[ls].off_bhi : P.sys.off_bhi;
     const int64_t loff = pm.sys_tab ? pm.sys_tab[ls].chunk_off : P.sys.chunk_off;
-    bulk_load(su32(cbuf(issued)), chunks + loff + (size_t)lk * lbytes, lbytes,
-              su32(&bars[P.nbuf == 2 ? (issued & 1) : 0]));
-    ++issued;
-    if (++lk >= ln) { lk = 0; ++lit; }
+    const uint8_t* src = chunks + loff + (size_t)xk * lbytes;
+    if (cpart) {
+      bulk_load(su32(sm + P.s_cpart), src + lsplit, lbytes - lsplit, su32(&bars[5]));
+    } else {
+      bulk_load(su32(cbuf(issued)), src, SPLIT ? lsplit : lbytes, su32(&bars[P.nbuf == 2 ? (issued & 1) : 0]));
+    }
+    if (++xk >= ln) { xk = 0; ++xit; }
   };
-  if (tid == 0)
+  auto load_next = [&]() {
+    if (lit >= my_tiles) return;
+    load_item(lit, lk, false);
+    ++issued;
+  };
+  auto load_cnext = [&]() {
+    if (!SPLIT || cit >= my_tiles) return;
+    load_item(cit, ck, true);
+    ++cissued;
+  };
+  if (tid == 0) {
     for (int q = 0; q < P.nbuf; ++q) load_next();
+    load_cnext();
+  }
   int g = 0;
 
   for (int it = 0; it < my_tiles; ++it) {
@@ -401,8 +425,11 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       if (*sAbort) goto teardown;
       // ---- op. 2b: [D_z h | D_tau h | h] = E_k B_k^T, split passes
       if (tid == 0) {
+        // split mode: the coefficient part of item g in its own buffer
+        if (SPLIT && !mbar_wait(su32(&bars[5]), (uint32_t)g & 1u)) atomicExch(sAbort, 1);
         tc_fence_after();
-        const uint32_t cb = su32(cbuf(g));
+        // cb + off_bhi addresses the coefficient part in either layout
+        const uint32_t cb = SPLIT ? su32(sm + P.s_cpart) - (uint32_t)S.off_bhi : su32(cbuf(g));
         const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
         const uint32_t tj = t_j;
         for (int s = 0; s < S.KC / 16; ++s) {
@@ -423,7 +450,8 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       // operand are free
       if (tid == 0 && ok) {
         proxy_fence();
-        load_next();   // item g + nbuf into this buffer
+        load_next();    // item g + nbuf into this buffer
+        load_cnext();   // split mode: coefficient part of item g + 1
       }
       if (ok) write_row(k);
       tc_fence_before();
@@ -438,6 +466,8 @@ teardown:
       atomicExch(err, 1);
       // let copies and MMAs still in flight land before the CTA's resources go away
       for (int q = g; q < issued; ++q) mbar_wait(su32(&bars[P.nbuf == 2 ? (q & 1) : 0]), cpar(q));
+      if (SPLIT)
+        for (int q = g; q < cissued; ++q) mbar_wait(su32(&bars[5]), (uint32_t)q & 1u);
       mbar_wait(su32(&bars[2 + (g & 1)]), (uint32_t)(g >> 1) & 1u);
       mbar_wait(su32(&bars[2 + ((g + 1) & 1)]), (uint32_t)((g + 1) >> 1) & 1u);
     }
@@ -469,33 +499,39 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
                         int32_t* err, const PathMap& pm, int ctas_per_sm, cudaStream_t st) {
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
   const bool map = pm.list != nullptr;
-  auto kern = map ? eval_mixed_kernel<true> : eval_mixed_kernel<false>;
+  auto pick = [map](bool split) {
+    return map ? (split ? eval_mixed_kernel<true, true> : eval_mixed_kernel<true, false>)
+               : (split ? eval_mixed_kernel<false, true> : eval_mixed_kernel<false, false>);
+  };
   int dev = 0, max_smem = 0, sm_smem = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   // Configurations in order of preference, the first that fits wins:
-  // (nbuf, wbuf) = (2, 2) prefetches the next equation's constants and
-  // issues its exponent GEMM into the second W accumulator under the current
-  // epilogue; (1, 2) is that without the prefetch; (1, 1) drops both and
-  // needs the least shared and tensor memory (it is the one that serves
-  // m_k up to 128).  At n = 16 the overlap is worth more than residency:
+  // (nbuf, wbuf, split) = (2, 2, 0) prefetches the next equation's constants
+  // and issues its exponent GEMM into the second W accumulator under the
+  // current epilogue; (2, 2, 1) prefetches only the exponent parts and loads
+  // each coefficient part once the previous coefficient GEMM is done (in time
+  // for its own GEMM after the epilogue: large shapes); (1, 2, 0) has no
+  // prefetch; (1, 1, 0) needs the least shared and tensor memory (it is the
+  // one that serves m_k up to 128).  At n = 16 the overlap is worth more than residency:
   // (1, 1) with three CTAs per SM measured 177 us against 117 us for (2, 2)
   // with two.  Residency is bounded by shared memory, registers and the 512
   // tensor-memory columns of an SM; a persistent grid above it would run in
   // two waves.
   MixedArgs best{};
   int best_smem = 0, best_per_sm = 0;
-  cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-  if (e != cudaSuccess) return e;
-  const int regs_per_cta = (fa.numRegs + 7) / 8 * 8 * kEvalThreads;
-  const int cfg[3][2] = {{2, 2}, {1, 2}, {1, 1}};
+  cudaError_t e = cudaSuccess;
+  const int cfg[4][3] = {{2, 2, 0}, {2, 2, 1}, {1, 2, 0}, {1, 1, 0}};
+  auto r128 = [](int v) { return (v + 127) / 128 * 128; };
+  const int xpart = r128(maxs.MP * maxs.KX * 2 + maxs.MP * 4);   // largest exponent part
+  const int cpart = r128(2 * maxs.NJ * maxs.KC * 2);             // largest coefficient part
   for (const auto& c : cfg) {
     MixedArgs a;
     a.sys = sys;
     a.nbuf = c[0];
     a.wbuf = c[1];
+    a.split = c[2];
     int cols = a.wbuf * 2 * maxs.MP + maxs.NJ, t = 32;
     while (t < cols) t *= 2;
     if (t > 512) continue;
@@ -511,13 +547,19 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.s_invy = take(out.Hy ? 128 * maxs.n * 8 : 0);   // 1/y only for the caller's H_y
     a.s_achi = take(128 * maxs.KC * 2);
     a.s_aclo = take(128 * maxs.KC * 2);
-    a.s_const0 = take(maxs.chunk_bytes);
-    a.s_const1 = a.nbuf == 2 ? take(maxs.chunk_bytes) : a.s_const0;
+    const int cbytes = a.split ? xpart : maxs.chunk_bytes;
+    a.s_const0 = take(cbytes);
+    a.s_const1 = a.nbuf == 2 ? take(cbytes) : a.s_const0;
+    a.s_cpart = a.split ? take(cpart) : a.s_const0;
     a.s_bar = take(128);
     a.p = p;
     a.ntiles = (int)ntiles;
     const int smem = off + 1024;   // slack for aligning the dynamic base
     if (smem > max_smem) continue;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, pick(a.split));
+    if (e != cudaSuccess) return e;
+    const int regs_per_cta = (fa.numRegs + 7) / 8 * 8 * kEvalThreads;
     // 1 KB of shared memory per CTA is reserved by the system
     const int per_sm = std::min({sm_smem / (smem + 1024), 65536 / regs_per_cta, 512 / a.tmem_cols});
     if (per_sm >= 1) {
@@ -528,6 +570,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     }
   }
   if (best_per_sm < 1) return cudaErrorInvalidConfiguration;
+  auto kern = pick(best.split);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, best_smem);
   if (e != cudaSuccess) return e;
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, best_per_sm) : best_per_sm;
