@@ -108,3 +108,75 @@ def test_fp64_resolve_path(hpt, n, m):
     rel = np.abs(ya - yb).max(-1) / np.maximum(1.0, np.abs(yb).max(-1))
     assert np.median(rel) < 1e-5 and (rel < 1e-3).mean() > 0.97
     h.close()
+
+
+def _config4_in(lo, hi):
+    for idx in range(400):
+        s, pairs = W.config4_system(idx)
+        if lo <= s.n <= hi:
+            return s, pairs
+    raise RuntimeError("no system")
+
+
+@pytest.mark.parametrize("band", [(4, 8), (9, 16), (17, 24)], ids=["n<=8", "n<=16", "n<=24"])
+def test_fp64_step_matches_oracle_larger_n(hpt, oracle_mod, band):
+    """Every FP64 solve shape (8 lanes x 1 row, 8 x 2, 32 x 1) on real paths of
+    many-systems workload systems: after 6 oracle steps from the start
+    points, one more step on the GPU gives the oracle's accept decisions and
+    new state (relative 1e-10) on the paths where the decisions agree."""
+    s, pairs = _config4_in(*band)
+    cell = {"kind": "pairs", "pairs": pairs}
+    te = cells.t_exponents(s, cell)
+    osys = oracle_mod.System(s, te["e"], te["D"])
+    P = oracle_mod.Params()
+    ks = np.zeros((96, s.n), np.int64)
+    ks[:, 0] = np.arange(96)
+    ost = oracle_mod.PathState.start(cells.start_points_at(s, pairs, ks), cells.tau0(te["e"], te["D"]),
+                                     P.dtau_init)
+    osys.step(P, ost, 6)
+    h = hpt.System.from_laurent(s, cell, 0)
+    g = _to_gpu(hpt, ost, 0)
+    h.step(g, 1)
+    osys.step(P, ost, 1)
+    torch.cuda.synchronize()
+    gh = g.to_host()
+    same = (gh["accepts"].numpy() == ost.accepts) & (gh["status"].numpy() == ost.status)
+    assert same.mean() >= 0.97
+    assert (ost.accepts[same] > 1).mean() > 0.5      # real steps, not only rejections
+    for a, b in (("y", "y"), ("yacc", "y_acc"), ("dEacc", "dE_acc")):
+        ref = getattr(ost, a)[same]
+        got = gh[b].numpy()[same]
+        err = np.abs(got - ref).max(-1) / np.maximum(1.0, np.abs(ref).max(-1))
+        assert err.max() < 1e-10, (a, np.sort(err)[-3:])
+    h.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_step_over_several_chunks(hpt, prec):
+    """More paths than one evaluate/solve round takes (65,536): the step over
+    66,000 paths equals the steps of its first 65,536 and last 464 paths
+    taken separately, bit for bit."""
+    sysm, alpha = W.config3(6, 8)
+    cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
+    h = hpt.System.from_laurent(sysm, cell, prec)
+    y, t = W.random_points(13, 66000, 6)
+
+    def state(lo, hi):
+        st = hpt.PathState(hi - lo, 6, prec)
+        yd = torch.from_numpy(y[lo:hi]).cuda().to(st.y.dtype)
+        st.y.copy_(yd)
+        st.y_acc.copy_(yd)
+        st.tau.copy_(torch.from_numpy(np.log(t[lo:hi])))
+        st.tau_acc.copy_(st.tau)
+        st.dtau.fill_(1e-3)
+        st.accepts.fill_(1)
+        return st
+
+    whole, a, b = state(0, 66000), state(0, 65536), state(65536, 66000)
+    for st in (whole, a, b):
+        h.step(st, 2)
+    torch.cuda.synchronize()
+    hw, ha, hb = whole.to_host(), a.to_host(), b.to_host()
+    for k in hw:
+        assert torch.equal(hw[k], torch.cat([ha[k], hb[k]])), k
+    h.close()
