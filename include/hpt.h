@@ -334,7 +334,7 @@ hpt_status hpt_batch_track(hpt_batch b, const int64_t* paths, const void* y0, co
 /* The project's autotuner: times whole hpt_batch_track calls on the given
  * problem, one knob at a time from the current tuning (coordinate descent):
  * the mid-size solve shape (8 or 32 lanes), then eval CTAs/SM (1, 2 where
- * tensor memory allows), then K in {4, 8, 16, 32}; keeps the fastest as the
+ * tensor memory allows), then K in {2, 4, 8, 16, 32}; keeps the fastest as the
  * batch's tuning.  Writes the chosen tuning to *best, and, where not NULL,
  * each timed candidate's tuning and milliseconds to cand[] / ms[] (capacity
  * *ncand in, count out). */

@@ -679,7 +679,7 @@ hpt_status hpt_batch_autotune(hpt_batch b, const int64_t* paths, const void* y0,
     if ((rc = trial(t))) { b->tune = start; return rc; }
   }
   t = win;
-  for (int K : {4, 8, 16, 32}) {
+  for (int K : {2, 4, 8, 16, 32}) {
     if (K == win.steps_per_round) continue;
     t.steps_per_round = K;
     if ((rc = trial(t))) { b->tune = start; return rc; }
