@@ -1,8 +1,9 @@
 // Mixed-precision evaluation of the homotopy and its extended Jacobian on the
 // fifth-generation tensor cores (tcgen05, accumulators in tensor memory).
 //
-// Algorithm 2 (Section 5) for a tile of 128 points, one CTA of 128 threads,
-// thread r <-> point r <-> tensor-memory lane r:
+// Algorithm 2 (Section 5) for tiles of 128 points: a persistent CTA of 256
+// threads walks its tiles; point r of a tile is tensor-memory lane r, served
+// by thread r of each of the two warpgroups, which split the columns:
 //   op. 1   z = log y in FP32 (principal branch), Re z and Im z each split into
 //           three BF16 parts (hi + mid + lo carries the full FP32 value);
 //   op. 2a  per equation k: W = Z A_k by tcgen05.mma kind::f16 with FP32
@@ -19,9 +20,10 @@
 //   op. 3   D_y h_k = D_z h_k diag(1/y) for the caller's H_y.  The step's
 //           scratch keeps D_z h_k instead: the solve applies diag(1/y) to
 //           its two n-vector solutions (n products per path, not n^2).
-// The per-equation constants (exponent operand, B_k hi/lo, e) are one
+// The per-equation constants (exponent operand and e, then B_k hi/lo) are one
 // contiguous image per equation, double-buffered into shared memory with
-// cp.async.bulk (the bulk-copy engine) while the previous equation computes.
+// cp.async.bulk (the bulk-copy engine) while the previous equation computes;
+// large shapes prefetch only the exponent part (see launch_core).
 // Operands use the canonical K-major layout without swizzle (8 x 16-byte core
 // matrices; K-adjacent cores 128 bytes apart, 8-row groups K*16 bytes apart).
 // Every wait on an mbarrier is bounded (about two seconds of global time);
