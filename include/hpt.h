@@ -206,6 +206,42 @@ hpt_status hpt_create_system(int32_t n, const int32_t* support_sizes, const int3
 
 hpt_status hpt_destroy(hpt_system sys);
 
+/* Projective formulation (Section 2.2, eq. (3)): a new handle of the same
+ * precision and device for the homogenized homotopy of sys, n equations in
+ * nv = n + 1 homogeneous coordinates y = (y_0 .. y_{n-1}, y_n), the
+ * homogenizing coordinate last.  Every exponent a of equation k becomes
+ * (a, deg_k - 1^T a) with deg_k = max over S_k of 1^T a (the total degree of
+ * a polynomial f_k; for a Laurent support the least degree that keeps the
+ * new exponent non-negative), so h_k(lambda y) = lambda^deg_k h_k(y) and
+ * h_k((x, 1), t) = H_k(x, t).  sys is not referenced afterwards (the new
+ * handle keeps its own copy of the affine constants for the polish and the
+ * adjoint).  On the new handle:
+ *   - hpt_eval takes y_dev[p*nv] and writes H[p*n], Hy[p*n*nv], Ht[p*n];
+ *   - hpt_euler_newton gives the projective directions (below);
+ *   - hpt_paths_init takes AFFINE start points y0_dev[p*n] complex128 and
+ *     stores (x0, 1)/|(x0, 1)|; the state holds p*nv entries per array;
+ *   - hpt_step runs the projective step: Algorithm 3 by QR, then the step
+ *     control of hpt_params with two changes: after every Newton correction
+ *     the point (and the stored Euler direction, by the same factor) is
+ *     scaled to unit Euclidean norm, and a path is HPT_PATH_DIVERGED when a
+ *     dehomogenized coordinate |y_j / y_n| leaves [1/div_bound, div_bound],
+ *     tested before the end-of-path test (a path may reach t = 1 at
+ *     infinity);
+ *   - hpt_track takes affine start points, tracks in homogeneous coordinates
+ *     (both precisions step through hpt_step's launches, not a batch) and
+ *     writes dehomogenized end points x = y'/y_n, FP64-polished;
+ *   - hpt_polish and hpt_adjoint work on affine points x[p*n];
+ *   - hpt_step_static and hpt_batch_create return HPT_ENOTSUP.
+ * HPT_ENOTSUP for n > 31; HPT_ERANGE when a homogenized monomial of an
+ * HPT_MIXED system breaks its exponent limits (below); HPT_EINVAL when sys is
+ * already projective. */
+hpt_status hpt_homogenize(hpt_system sys, hpt_system* out);
+
+/* Variables per point (nv = n, or n + 1 for a projective handle), whether the
+ * handle is projective, and for a projective handle the degrees deg_k
+ * (degrees[n] int64, may be NULL). */
+hpt_status hpt_get_nvars(hpt_system sys, int32_t* nv, int32_t* projective, int64_t* degrees);
+
 /* Host getters: sizes, form, tau0 for params->eps0 (NULL = default), and the
  * exact integer data the handle was built from (arrays may be NULL). */
 hpt_status hpt_get_info(hpt_system sys, int32_t* n, int32_t* M, int32_t* prec, double eps0,
@@ -219,6 +255,21 @@ hpt_status hpt_get_texp(hpt_system sys, int64_t* texp, int64_t* denom, int64_t* 
  * precision.  Any output pointer may be NULL.  p = 0 is a no-op. */
 hpt_status hpt_eval(hpt_system sys, int64_t p, const void* y_dev, const double* t_dev,
                     void* H_dev, void* Hy_dev, void* Ht_dev, void* stream);
+
+/* Algorithm 3 (EulerNewton, Section 6) for p points y_dev[p*nv] (complex of
+ * the handle's precision) at tau_dev[p] (tau = ln t <= 0): the consolidated
+ * matrix J = [[dH/dy, dH/dtau, H], [y^*, 0, 0]] (N = nv rows; an affine
+ * handle has no y^* row, N = n) is factored as J^T = Q [R; 0] by Householder
+ * reflections; the two rightmost columns of Q give the null space of J, and
+ * the reduction that turns their last two entries into the 2 x 2 identity
+ * gives the Euler direction dE (dH/dy dE + dH/dtau = 0, eq. (4)) and the
+ * Newton direction dN (dH/dy dN + H = 0, eq. (5)), both with y^* d = 0 in the
+ * projective form.  Writes dE_dev[p*nv], dN_dev[p*nv] (the handle's complex
+ * type) and ok_dev[p] int32 (1 when every reflector norm is nonzero, the
+ * 2 x 2 block is invertible and all values are finite).  HPT_MIXED: FP32
+ * factorisation of the tensor-core evaluation.  Asynchronous on `stream`. */
+hpt_status hpt_euler_newton(hpt_system sys, int64_t p, const void* y_dev, const double* tau_dev, void* dE_dev,
+                            void* dN_dev, int32_t* ok_dev, void* stream);
 
 /* Prepares a path state for tracking from start points y0_dev[p*n] complex128
  * at tau0 (from params->eps0): y = y_acc = y0, tau = tau_acc = tau0,

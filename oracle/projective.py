@@ -149,6 +149,12 @@ class ProjectiveSystem:
         n = self.n
         return H[:, :n], Hy[:, :n, :], Ht[:, :n]
 
+    def scale(self, y, tau):
+        """Sums of term magnitudes matching eval's outputs (tolerance scales)."""
+        SH, SHy, SHt = self._sq.scale(y, tau)
+        n = self.n
+        return SH[:, :n], SHy[:, :n, :], SHt[:, :n]
+
     def consolidated(self, y, tau):
         """J = [[H_y, H_tau, H], [y^*, 0, 0]] (p, n+1, n+3) (Section 6)."""
         y = np.asarray(y, np.complex128)

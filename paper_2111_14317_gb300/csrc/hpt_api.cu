@@ -1,5 +1,5 @@
 // Entry points of libhpt that enqueue device work: hpt_eval, hpt_paths_init,
-// hpt_step, hpt_track, hpt_polish, hpt_adjoint.
+// hpt_step, hpt_track, hpt_polish, hpt_adjoint, hpt_euler_newton.
 #include <string.h>
 
 #include <algorithm>
@@ -40,10 +40,10 @@ cudaError_t eval_form(hpt_system s, int64_t p, const void* y, const double* tau,
 
 hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps,
                      const hpt_params& prm, cudaStream_t st) {
-  const int n = s->n;
+  const int n = s->n, nv = s->nv;
   const int64_t chunk = std::min<int64_t>(p, kChunk);
   // scratch: extended Jacobian of a chunk, then the FP64 re-solve list
-  const size_t ext_bytes = (ext_entries(chunk, n) * csize(s) + 255) / 256 * 256;
+  const size_t ext_bytes = (ext_entries(chunk, nv) * csize(s) + 255) / 256 * 256;
   hpt_status rc = ensure_scratch(s, ext_bytes + 256 + (size_t)chunk * sizeof(int64_t));
   if (rc) return rc;
   int32_t* redo_count = (int32_t*)((char*)s->d_scratch + ext_bytes);
@@ -51,11 +51,16 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
   for (int r = 0; r < nsteps; ++r) {
     for (int64_t q0 = 0; q0 < p; q0 += chunk) {
       const int64_t cnt = std::min(chunk, p - q0);
-      hpt_paths sub = offset_paths(S, q0, n, csize(s));
+      hpt_paths sub = offset_paths(S, q0, nv, csize(s));
       EvalOut out;
       out.ext = s->d_scratch;
       cudaError_t e = eval_form(s, cnt, sub.y, sub.tau, 0, out, st);
       if (e != cudaSuccess) return cuda_fail(e, "evaluation launch");
+      if (s->proj) {   // Algorithm 3 by QR, projective step control
+        e = launch_qr_step(s, cnt, s->d_scratch, sub, prm, st);
+        if (e != cudaSuccess) return cuda_fail(e, "QR step launch");
+        continue;
+      }
       StepArgs a;
       a.n = n;
       a.p = cnt;
@@ -72,12 +77,15 @@ hpt_status step_impl(hpt_system s, int64_t p, const hpt_paths& S, int32_t nsteps
   return HPT_OK;
 }
 
+// The polish runs on the affine system (a projective handle keeps its FP64
+// constants in s->affine) with the scratch of s.
 hpt_status polish_impl(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
                        cudaStream_t st) {
+  const hpt_system a = s->affine ? s->affine : s;
   const int64_t chunk = std::min<int64_t>(p, kChunk);
-  hpt_status rc = ensure_scratch(s, ext_entries(chunk, s->n) * 16);
+  hpt_status rc = ensure_scratch(s, ext_entries(chunk, a->n) * 16);
   if (rc) return rc;
-  return polish_paths(s, p, x, done, last, prm, s->d_scratch, chunk, st);
+  return polish_paths(a, p, x, done, last, prm, s->d_scratch, chunk, st);
 }
 
 }  // namespace
@@ -169,7 +177,8 @@ hpt_status hpt_paths_init(hpt_system s, int64_t p, const void* y0, const hpt_par
   }
   double tau0 = 0;
   hpt_get_info(s, nullptr, nullptr, nullptr, prm->eps0, &tau0);
-  cudaError_t e = launch_paths_init(s, p, y0, tau0, *prm, *S, (cudaStream_t)stream);
+  cudaError_t e = s->proj ? launch_paths_init_proj(s, p, y0, tau0, *prm, *S, (cudaStream_t)stream)
+                          : launch_paths_init(s, p, y0, tau0, *prm, *S, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "init launch");
   return HPT_OK;
 }
@@ -197,7 +206,7 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
   if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
   if (p == 0) return HPT_OK;
   if (!y0 || !x_out) { set_error("y0 or x_out is NULL"); return HPT_EINVAL; }
-  if (s->prec == HPT_MIXED) {
+  if (s->prec == HPT_MIXED && !s->proj) {
     // the mixed form tracks through a one-system batch (cached in the handle):
     // finished paths leave the launches after every round instead of being
     // evaluated until the last path ends; per path the arithmetic is the same
@@ -209,7 +218,7 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
     return hpt_batch_track(s->self_batch, &p, y0, prm, x_out, status_out, steps_out, stream);
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const int n = s->n;
+  const int n = s->nv;   // state entries per path (homogeneous coordinates in the projective form)
   const size_t cs = csize(s);
   // state layout inside the library's track scratch
   size_t off = 0;
@@ -251,7 +260,8 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
     if (e != cudaSuccess) return cuda_fail(e, "active-path count");
     if (*s->h_count == 0 || total > (int64_t)prm->max_steps + every) break;
   }
-  cudaError_t e = launch_finish_track(s, p, S, x_out, status_out, steps_out, done, st);
+  cudaError_t e = s->proj ? launch_finish_track_proj(s, p, S, x_out, status_out, steps_out, done, st)
+                          : launch_finish_track(s, p, S, x_out, status_out, steps_out, done, st);
   if (e != cudaSuccess) return cuda_fail(e, "track output");
   if ((rc = polish_impl(s, p, x_out, done, last, *prm, st))) return rc;
   e = cudaStreamSynchronize(st);
@@ -284,7 +294,8 @@ hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, v
   if (e != cudaSuccess) return cuda_fail(e, "adjoint init");
   if (p == 0) return HPT_OK;
   if (!x || !gx) { set_error("x or gx is NULL"); return HPT_EINVAL; }
-  const int n = s->n;
+  const hpt_system a = s->affine ? s->affine : s;   // solutions are affine points
+  const int n = a->n;
   const int64_t chunk = std::min<int64_t>(p, 8192);
   const size_t ext_bytes = (ext_entries(chunk, n) * 16 + 255) / 256 * 256;
   if ((rc = ensure_scratch(s, ext_bytes + (size_t)chunk * s->M * 16))) return rc;
@@ -294,10 +305,34 @@ hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, v
     EvalOut out;
     out.ext = s->d_scratch;
     const void* xq = (const char*)x + q0 * n * 16;
-    e = launch_eval_fp64(s, cnt, xq, nullptr, 0, out, st);
+    e = launch_eval_fp64(a, cnt, xq, nullptr, 0, out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint evaluation launch");
-    e = launch_adjoint(s, cnt, s->d_scratch, xq, (const char*)gx + q0 * n * 16, contrib, 0, gc, st);
+    e = launch_adjoint(a, cnt, s->d_scratch, xq, (const char*)gx + q0 * n * 16, contrib, 0, gc, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+  }
+  return HPT_OK;
+}
+
+hpt_status hpt_euler_newton(hpt_system s, int64_t p, const void* y, const double* tau, void* dE, void* dN,
+                            int32_t* ok, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  if (p < 0) { set_error("p < 0"); return HPT_EINVAL; }
+  if (p == 0) return HPT_OK;
+  if (!y || !tau || !dE || !dN || !ok) { set_error("NULL pointer argument"); return HPT_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t chunk = std::min<int64_t>(p, kChunk);
+  if ((rc = ensure_scratch(s, ext_entries(chunk, s->nv) * csize(s)))) return rc;
+  const size_t cs = csize(s);
+  for (int64_t q0 = 0; q0 < p; q0 += chunk) {
+    const int64_t cnt = std::min(chunk, p - q0);
+    const size_t vo = (size_t)q0 * s->nv * cs;
+    EvalOut out;
+    out.ext = s->d_scratch;
+    cudaError_t e = eval_form(s, cnt, (const char*)y + vo, tau + q0, 0, out, st);
+    if (e != cudaSuccess) return cuda_fail(e, "evaluation launch");
+    e = launch_qr_directions(s, cnt, s->d_scratch, (const char*)y + vo, (char*)dE + vo, (char*)dN + vo, ok + q0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "QR launch");
   }
   return HPT_OK;
 }

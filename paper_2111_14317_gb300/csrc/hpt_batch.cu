@@ -516,6 +516,7 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
   for (int s = 0; s < nsys; ++s) {
     if (!systems[s]) { set_error("system %d is NULL", s); return HPT_EINVAL; }
     if (systems[s]->prec != HPT_MIXED) { set_error("system %d is not HPT_MIXED", s); return HPT_ENOTSUP; }
+    if (systems[s]->proj) { set_error("system %d is projective (batches hold affine systems)", s); return HPT_ENOTSUP; }
     if (systems[s]->device != dev) { set_error("system %d belongs to another device", s); return HPT_EINVAL; }
   }
   hpt_batch b = new hpt_batch_s();

@@ -6,6 +6,10 @@
 // equation k is sum_i E_i B_k[:, i] = [D_z h_k | D_tau h_k | h_k] (eq. (8) and
 // the extended-Jacobian identity), and D_y h_k = D_z h_k diag(e^{-z}).
 //
+// The same kernel serves the projective form (Section 2.2): n equations in nv
+// = n + 1 homogeneous coordinates, exponents (a, deg_k - 1^T a); the extended
+// Jacobian row is then [D_z h_k (nv entries) | D_tau h_k | h_k].
+//
 // Mapping: a block owns 32 points (one per lane) and its four warps take the
 // equations k = warp, warp + 4, ...; all lanes of a warp read the same
 // monomial constants (broadcast), z is staged in shared memory transposed so
@@ -19,7 +23,7 @@ namespace {
 
 // MAP: 32 consecutive positions of a position map per block (inside one
 // 128-position tile, so one system: S from the per-system table); otherwise
-// positions are the paths of the single system S.
+// positions are the paths of the single system S.  NMAX bounds the variables.
 template <int NMAX, bool MAP>
 __global__ void __launch_bounds__(128)
 eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const double* __restrict__ tin,
@@ -31,14 +35,14 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
   __shared__ double tinv[32];
   __shared__ int64_t spath[32];
   int64_t base = (int64_t)blockIdx.x * 32;
-  int nmax = S.n;
+  int nmax = S.nv;
   if (MAP) {
     base += *pm.pos_begin;
     if (base >= *pm.npos) return;
     S = tab[pm.tile_sys[base >> 7]];
     nmax = pm.nmax;
   }
-  const int n = S.n;
+  const int n = S.n, nv = S.nv;
   const int32_t* __restrict__ msz = S.msz;
   const int32_t* __restrict__ off = S.off;
   const double* __restrict__ ahat = S.ahat;
@@ -51,11 +55,11 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
 
   // op. 1 of Algorithm 2: Z <- log Y (principal branch), and 1/y for the
   // final diag(e^{-z}) scaling.
-  for (int idx = threadIdx.x; idx < 32 * n; idx += blockDim.x) {
-    const int q = idx / n, j = idx - q * n;
+  for (int idx = threadIdx.x; idx < 32 * nv; idx += blockDim.x) {
+    const int q = idx / nv, j = idx - q * nv;
     const int64_t path = spath[q];
     double2 v = make_double2(1.0, 0.0);
-    if (path >= 0) v = y[(MAP ? (size_t)pm.vofs[path] : (size_t)path * n) + j];
+    if (path >= 0) v = y[(MAP ? (size_t)pm.vofs[path] : (size_t)path * nv) + j];
     const double r2 = v.x * v.x + v.y * v.y;
     zs[j][q] = make_double2(log(hypot(v.x, v.y)), atan2(v.y, v.x));
     iys[j][q] = make_double2(v.x / r2, -v.y / r2);
@@ -73,7 +77,7 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
   const int64_t path = spath[lane];
   const int64_t pos = base + lane;
   const double tau = taus[lane];
-  const int np2 = n + 2;
+  const int np2 = nv + 2;
   for (int k = warp; k < n; k += 4) {
     double2 accJ[NMAX];
 #pragma unroll
@@ -82,11 +86,11 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
     const int i0 = off[k], i1 = off[k] + msz[k];
     for (int i = i0; i < i1; ++i) {
       // op. 2 of Algorithm 2, one monomial: W = [z, tau] . A[:, i]
-      const double* a = ahat + (size_t)i * (n + 1);
-      double wr = a[n] * tau, wi = 0.0;
+      const double* a = ahat + (size_t)i * (nv + 1);
+      double wr = a[nv] * tau, wi = 0.0;
 #pragma unroll
       for (int j = 0; j < NMAX; ++j) {
-        if (j < n) {
+        if (j < nv) {
           const double aj = a[j];
           const double2 z = zs[j][lane];
           wr = fma(aj, z.x, wr);
@@ -101,13 +105,13 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
       const double2* bb = bcol + (size_t)i * np2;
 #pragma unroll
       for (int u = 0; u < NMAX; ++u) {
-        if (u < n) {
+        if (u < nv) {
           const double2 c = bb[u];
           accJ[u].x = fma(er, c.x, fma(-ei, c.y, accJ[u].x));
           accJ[u].y = fma(er, c.y, fma(ei, c.x, accJ[u].y));
         }
       }
-      const double2 ct = bb[n], ch = bb[n + 1];
+      const double2 ct = bb[nv], ch = bb[nv + 1];
       accT.x = fma(er, ct.x, fma(-ei, ct.y, accT.x));
       accT.y = fma(er, ct.y, fma(ei, ct.x, accT.y));
       accH.x = fma(er, ch.x, fma(-ei, ch.y, accH.x));
@@ -120,16 +124,16 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
     if (ext) {
 #pragma unroll
       for (int u = 0; u < NMAX; ++u)
-        if (u < n) ext[ext_index(pos, k, u, nmax)] = accJ[u];
-      ext[ext_index(pos, k, n, nmax)] = accT;
-      ext[ext_index(pos, k, n + 1, nmax)] = accH;
+        if (u < nv) ext[ext_index(pos, k, u, nmax)] = accJ[u];
+      ext[ext_index(pos, k, nv, nmax)] = accT;
+      ext[ext_index(pos, k, nv + 1, nmax)] = accH;
     }
     // op. 3 of Algorithm 2 for the caller's H_y: D_y h_k = D_z h_k diag(e^{-z})
     if (oHy) {
-      double2* row = oHy + ((size_t)path * n + k) * n;
+      double2* row = oHy + ((size_t)path * n + k) * nv;
 #pragma unroll
       for (int u = 0; u < NMAX; ++u) {
-        if (u < n) {
+        if (u < nv) {
           const double2 iy = iys[u][lane];
           row[u] = make_double2(accJ[u].x * iy.x - accJ[u].y * iy.y, accJ[u].x * iy.y + accJ[u].y * iy.x);
         }
@@ -148,7 +152,7 @@ eval_fp64_kernel(Fp64Sys S, int64_t p, const double2* __restrict__ y, const doub
 Fp64Sys fp64_sys_of(const hpt_system s) {
   Fp64Sys f;
   f.n = s->n;
-  f.pad_ = 0;
+  f.nv = s->nv;
   f.msz = s->d_msz;
   f.off = s->d_off;
   f.ahat = s->d_ahat;
@@ -169,9 +173,9 @@ cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const doubl
   double2* Ht = (double2*)out.Ht;
   const Fp64Sys f = fp64_sys_of(s);
   const PathMap none;
-  if (s->n <= 8)
+  if (s->nv <= 8)
     eval_fp64_kernel<8, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
-  else if (s->n <= 16)
+  else if (s->nv <= 16)
     eval_fp64_kernel<16, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   else
     eval_fp64_kernel<32, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);

@@ -357,6 +357,95 @@ static MixedLayout mixed_layout(int n, int max_m) {
   return L;
 }
 
+// Uploads the device constants of s: the FP64 form (A_hat columns (a; e/D)
+// and B_k columns [c a; c e/D; c], eq. (8)) and, for HPT_MIXED, the
+// split-BF16 operand images.  ex holds M exponent vectors of s->nv entries
+// (the system's own, or the homogenized ones of the projective form); the
+// n equations come from s->msz / s->off.
+#define CUU(call)                                                             \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));              \
+      return e_ == cudaErrorMemoryAllocation ? HPT_ENOMEM : HPT_ECUDA;        \
+    }                                                                         \
+  } while (0)
+static hpt_status upload_constants(hpt_system s, const int32_t* ex) {
+  const int n = s->n, nv = s->nv, M = s->M;
+  const double* coeffs = s->coef.data();
+  std::vector<double> ahat((size_t)M * (nv + 1)), b((size_t)M * (nv + 2) * 2);
+  for (int i = 0; i < M; ++i) {
+    const double sexp = (double)s->texp[i] / (double)s->D;
+    const double cr = coeffs[2 * i], ci = coeffs[2 * i + 1];
+    for (int j = 0; j < nv; ++j) {
+      const double a = (double)ex[(size_t)i * nv + j];
+      ahat[(size_t)i * (nv + 1) + j] = a;
+      b[((size_t)i * (nv + 2) + j) * 2] = cr * a;
+      b[((size_t)i * (nv + 2) + j) * 2 + 1] = ci * a;
+    }
+    ahat[(size_t)i * (nv + 1) + nv] = sexp;
+    b[((size_t)i * (nv + 2) + nv) * 2] = cr * sexp;
+    b[((size_t)i * (nv + 2) + nv) * 2 + 1] = ci * sexp;
+    b[((size_t)i * (nv + 2) + nv + 1) * 2] = cr;
+    b[((size_t)i * (nv + 2) + nv + 1) * 2 + 1] = ci;
+  }
+  CUU(cudaMalloc(&s->d_msz, n * sizeof(int32_t)));
+  CUU(cudaMalloc(&s->d_off, n * sizeof(int32_t)));
+  CUU(cudaMalloc(&s->d_ahat, ahat.size() * sizeof(double)));
+  CUU(cudaMalloc(&s->d_b, b.size() * sizeof(double)));
+  CUU(cudaMemcpy(s->d_msz, s->msz.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUU(cudaMemcpy(s->d_off, s->off.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CUU(cudaMemcpy(s->d_ahat, ahat.data(), ahat.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CUU(cudaMemcpy(s->d_b, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (s->prec != HPT_MIXED) return HPT_OK;
+
+  MixedLayout& ml = s->ml;
+  ml = mixed_layout(nv, s->max_m);
+  int max_smem = 0;
+  CUU(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+  if (!eval_mixed_fits(nv, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, max_smem)) {
+    set_error("%d variables with m_k up to %d exceed the mixed form's on-chip memory", nv, s->max_m);
+    return HPT_ENOTSUP;
+  }
+  std::vector<uint8_t> img((size_t)n * ml.chunk_bytes, 0);
+  for (int k = 0; k < n; ++k) {
+    uint8_t* ch = img.data() + (size_t)k * ml.chunk_bytes;
+    uint16_t* bexp = (uint16_t*)(ch + ml.off_bexp);
+    uint16_t* bhi = (uint16_t*)(ch + ml.off_bhi);
+    uint16_t* blo = (uint16_t*)(ch + ml.off_blo);
+    float* tf = (float*)(ch + ml.off_texp);
+    for (int i = 0; i < s->msz[k]; ++i) {
+      const int idx = s->off[k] + i;
+      for (int sp = 0; sp < 3; ++sp)
+        for (int j = 0; j < nv; ++j)
+          bexp[canon_offset(i, sp * nv + j, ml.KX) / 2] = bf16_bits((float)ex[(size_t)idx * nv + j]);
+      tf[i] = (float)s->texp[idx];
+      // realified B_k^T: output column 2u = Re J_u, 2u+1 = Im J_u; K index
+      // i = Re E_i, MP + i = Im E_i.
+      for (int u = 0; u < nv + 2; ++u) {
+        const double br = b[((size_t)idx * (nv + 2) + u) * 2], bi = b[((size_t)idx * (nv + 2) + u) * 2 + 1];
+        uint16_t h, l;
+        split2(br, h, l);
+        bhi[canon_offset(2 * u, i, ml.KC) / 2] = h;
+        blo[canon_offset(2 * u, i, ml.KC) / 2] = l;
+        split2(-bi, h, l);
+        bhi[canon_offset(2 * u, ml.MP + i, ml.KC) / 2] = h;
+        blo[canon_offset(2 * u, ml.MP + i, ml.KC) / 2] = l;
+        split2(bi, h, l);
+        bhi[canon_offset(2 * u + 1, i, ml.KC) / 2] = h;
+        blo[canon_offset(2 * u + 1, i, ml.KC) / 2] = l;
+        split2(br, h, l);
+        bhi[canon_offset(2 * u + 1, ml.MP + i, ml.KC) / 2] = h;
+        blo[canon_offset(2 * u + 1, ml.MP + i, ml.KC) / 2] = l;
+      }
+    }
+  }
+  CUU(cudaMalloc(&s->d_chunks, img.size()));
+  CUU(cudaMemcpy(s->d_chunks, img.data(), img.size(), cudaMemcpyHostToDevice));
+  return HPT_OK;
+}
+#undef CUU
+
 }  // namespace hpt
 
 using namespace hpt;
@@ -690,87 +779,113 @@ hpt_status hpt_create_system(int32_t n, const int32_t* msz, const int32_t* exps,
   s->D = L.D;
   s->alpha_num = L.alpha;
   s->beta_num = L.beta;
+  s->nv = n;
   CU(cudaGetDevice(&s->device));
-
-  // FP64 constants: A_hat columns (a; e/D) and B_k columns [c a; c e/D; c].
-  std::vector<double> ahat((size_t)M * (n + 1)), b((size_t)M * (n + 2) * 2);
-  for (int i = 0; i < M; ++i) {
-    const double sexp = (double)L.e[i] / (double)L.D;
-    const double cr = coeffs[2 * i], ci = coeffs[2 * i + 1];
-    for (int j = 0; j < n; ++j) {
-      const double a = (double)exps[(size_t)i * n + j];
-      ahat[(size_t)i * (n + 1) + j] = a;
-      b[((size_t)i * (n + 2) + j) * 2] = cr * a;
-      b[((size_t)i * (n + 2) + j) * 2 + 1] = ci * a;
-    }
-    ahat[(size_t)i * (n + 1) + n] = sexp;
-    b[((size_t)i * (n + 2) + n) * 2] = cr * sexp;
-    b[((size_t)i * (n + 2) + n) * 2 + 1] = ci * sexp;
-    b[((size_t)i * (n + 2) + n + 1) * 2] = cr;
-    b[((size_t)i * (n + 2) + n + 1) * 2 + 1] = ci;
-  }
-  CU(cudaMalloc(&s->d_msz, n * sizeof(int32_t)));
-  CU(cudaMalloc(&s->d_off, n * sizeof(int32_t)));
-  CU(cudaMalloc(&s->d_ahat, ahat.size() * sizeof(double)));
-  CU(cudaMalloc(&s->d_b, b.size() * sizeof(double)));
   CU(cudaMalloc(&s->d_err, sizeof(int32_t)));
-  CU(cudaMemcpy(s->d_msz, msz, n * sizeof(int32_t), cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(s->d_off, s->off.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(s->d_ahat, ahat.data(), ahat.size() * sizeof(double), cudaMemcpyHostToDevice));
-  CU(cudaMemcpy(s->d_b, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice));
   CU(cudaMemset(s->d_err, 0, sizeof(int32_t)));
   CU(cudaMallocHost(&s->h_count, sizeof(int32_t)));
-
-  if (prec == HPT_MIXED) {
-    MixedLayout& ml = s->ml;
-    ml = mixed_layout(n, max_m);
-    int max_smem = 0;
-    CU(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
-    if (!eval_mixed_fits(n, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, max_smem)) {
-      set_error("n=%d with m_k up to %d exceeds the mixed form's on-chip memory", n, max_m);
-      hpt_destroy(s);
-      return HPT_ENOTSUP;
-    }
-    std::vector<uint8_t> img((size_t)n * ml.chunk_bytes, 0);
-    for (int k = 0; k < n; ++k) {
-      uint8_t* ch = img.data() + (size_t)k * ml.chunk_bytes;
-      uint16_t* bexp = (uint16_t*)(ch + ml.off_bexp);
-      uint16_t* bhi = (uint16_t*)(ch + ml.off_bhi);
-      uint16_t* blo = (uint16_t*)(ch + ml.off_blo);
-      float* tf = (float*)(ch + ml.off_texp);
-      for (int i = 0; i < msz[k]; ++i) {
-        const int idx = s->off[k] + i;
-        for (int sp = 0; sp < 3; ++sp)
-          for (int j = 0; j < n; ++j)
-            bexp[canon_offset(i, sp * n + j, ml.KX) / 2] = bf16_bits((float)exps[(size_t)idx * n + j]);
-        tf[i] = (float)L.e[idx];
-        // realified B_k^T: output column 2u = Re J_u, 2u+1 = Im J_u; K index
-        // i = Re E_i, MP + i = Im E_i.
-        for (int u = 0; u < n + 2; ++u) {
-          const double br = b[((size_t)idx * (n + 2) + u) * 2], bi = b[((size_t)idx * (n + 2) + u) * 2 + 1];
-          uint16_t h, l;
-          split2(br, h, l);
-          bhi[canon_offset(2 * u, i, ml.KC) / 2] = h;
-          blo[canon_offset(2 * u, i, ml.KC) / 2] = l;
-          split2(-bi, h, l);
-          bhi[canon_offset(2 * u, ml.MP + i, ml.KC) / 2] = h;
-          blo[canon_offset(2 * u, ml.MP + i, ml.KC) / 2] = l;
-          split2(bi, h, l);
-          bhi[canon_offset(2 * u + 1, i, ml.KC) / 2] = h;
-          blo[canon_offset(2 * u + 1, i, ml.KC) / 2] = l;
-          split2(br, h, l);
-          bhi[canon_offset(2 * u + 1, ml.MP + i, ml.KC) / 2] = h;
-          blo[canon_offset(2 * u + 1, ml.MP + i, ml.KC) / 2] = l;
-        }
-      }
-    }
-    CU(cudaMalloc(&s->d_chunks, img.size()));
-    CU(cudaMemcpy(s->d_chunks, img.data(), img.size(), cudaMemcpyHostToDevice));
+  if ((rc = upload_constants(s, s->exps.data()))) {
+    hpt_destroy(s);
+    return rc;
   }
   *out = s;
   return HPT_OK;
 }
 #undef CU
+
+static hpt_system clone_host_data(const hpt_system a, hpt_precision prec) {
+  hpt_system s = new hpt_system_s();
+  s->n = a->n;
+  s->M = a->M;
+  s->prec = prec;
+  s->device = a->device;
+  s->max_m = a->max_m;
+  s->msz = a->msz;
+  s->off = a->off;
+  s->exps = a->exps;
+  s->coef = a->coef;
+  s->texp = a->texp;
+  s->D = a->D;
+  s->alpha_num = a->alpha_num;
+  s->beta_num = a->beta_num;
+  s->nv = a->n;
+  return s;
+}
+
+hpt_status hpt_homogenize(hpt_system a, hpt_system* out) {
+  if (!out) { set_error("out is NULL"); return HPT_EINVAL; }
+  *out = nullptr;
+  if (!a) { set_error("NULL handle"); return HPT_EINVAL; }
+  if (a->proj) { set_error("the handle is already projective"); return HPT_EINVAL; }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != a->device) {
+    set_error("the handle belongs to device %d, current device is %d", a->device, dev);
+    return HPT_EINVAL;
+  }
+  const int n = a->n, nv = n + 1, M = a->M;
+  if (nv > kMaxN) { set_error("the projective form supports n <= %d", kMaxN - 1); return HPT_ENOTSUP; }
+  // deg_k = the largest 1^T a over S_k; a_hat = (a, deg_k - 1^T a) (Section 2.2)
+  std::vector<int64_t> deg(n);
+  std::vector<int32_t> ex((size_t)M * nv);
+  for (int k = 0; k < n; ++k) {
+    int64_t d = INT64_MIN;
+    for (int i = a->off[k]; i < a->off[k] + a->msz[k]; ++i) {
+      int64_t t = 0;
+      for (int j = 0; j < n; ++j) t += a->exps[(size_t)i * n + j];
+      d = std::max(d, t);
+    }
+    deg[k] = d;
+    for (int i = a->off[k]; i < a->off[k] + a->msz[k]; ++i) {
+      int64_t t = 0, s1 = 0;
+      for (int j = 0; j < n; ++j) {
+        const int32_t v = a->exps[(size_t)i * n + j];
+        ex[(size_t)i * nv + j] = v;
+        t += v;
+        s1 += v < 0 ? -(int64_t)v : v;
+      }
+      const int64_t last = d - t;   // >= 0
+      if (last > INT32_MAX) { set_error("homogenizing exponent overflows int32"); return HPT_ERANGE; }
+      ex[(size_t)i * nv + n] = (int32_t)last;
+      if (a->prec == HPT_MIXED && (last > 256 || s1 + last > 64)) {
+        set_error("homogenized monomial %d: the mixed form needs |a_j| <= 256 and sum |a_j| <= 64", i);
+        return HPT_ERANGE;
+      }
+    }
+  }
+  hpt_system s = clone_host_data(a, a->prec);
+  s->nv = nv;
+  s->proj = 1;
+  s->deg = deg;
+  hpt_system f = clone_host_data(a, HPT_FP64);
+  s->affine = f;   // freed with s
+  hpt_status rc = HPT_OK;
+  cudaError_t e = cudaSuccess;
+  for (hpt_system h : {s, f}) {
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_count, sizeof(int32_t));
+  }
+  if (e != cudaSuccess) {
+    set_error("allocation failed: %s", cudaGetErrorString(e));
+    rc = e == cudaErrorMemoryAllocation ? HPT_ENOMEM : HPT_ECUDA;
+  }
+  if (!rc) rc = upload_constants(s, ex.data());
+  if (!rc) rc = upload_constants(f, f->exps.data());
+  if (rc) {
+    hpt_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return HPT_OK;
+}
+
+hpt_status hpt_get_nvars(hpt_system s, int32_t* nv, int32_t* projective, int64_t* degrees) {
+  if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
+  if (nv) *nv = s->nv;
+  if (projective) *projective = s->proj;
+  if (degrees && s->proj) memcpy(degrees, s->deg.data(), s->n * sizeof(int64_t));
+  return HPT_OK;
+}
 
 hpt_status hpt_destroy(hpt_system s) {
   if (!s) return HPT_EINVAL;
@@ -778,6 +893,7 @@ hpt_status hpt_destroy(hpt_system s) {
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
   if (s->self_batch) hpt_batch_destroy(s->self_batch);
+  if (s->affine) hpt_destroy(s->affine);
   cudaFree(s->d_msz);
   cudaFree(s->d_off);
   cudaFree(s->d_ahat);

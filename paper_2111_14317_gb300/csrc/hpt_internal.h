@@ -11,7 +11,7 @@
 
 namespace hpt {
 
-constexpr int kMaxN = 32;          // variables (= equations)
+constexpr int kMaxN = 32;          // variables (equations = variables, or one fewer: projective form)
 constexpr int kMixedMaxM = 128;    // monomials per equation in the mixed form
 constexpr int kTile = 128;         // paths per tensor-core tile (MMA M)
 
@@ -37,18 +37,22 @@ struct MixedLayout {
 
 // One system's operand shapes as the mixed evaluation kernel reads them
 // (from its launch arguments for a single system, from a device table per
-// tile for many systems).
+// tile for many systems).  n counts the variables (the K dimension of the
+// exponent GEMM and the first columns of the extended Jacobian), ne the
+// equations (one constant image each): ne = n, or n - 1 in the projective
+// form.
 struct MixedSys {
   int n, MP, KX, NJ, KC;
   int chunk_bytes, off_bexp, off_bhi, off_blo, off_texp;
   float inv_D;
-  int pad_;
+  int ne;
   int64_t chunk_off;   // byte offset of the system's constant images
 };
 
-// One system's FP64 constants as the FP64 evaluation kernel reads them.
+// One system's FP64 constants as the FP64 evaluation kernel reads them: n
+// equations in nv variables (nv = n, or n + 1 in the projective form).
 struct Fp64Sys {
-  int n, pad_;
+  int n, nv;
   const int32_t* msz;
   const int32_t* off;
   const double* ahat;
@@ -104,6 +108,13 @@ void set_error(const char* fmt, ...);
 
 struct hpt_system_s {
   int n = 0, M = 0;
+  // variables: nv = n (affine), or n + 1 homogeneous coordinates (projective
+  // form, proj = 1: exponents (a, deg_k - 1^T a), Section 2.2); the device
+  // constants below then describe the homogenized system, and `affine` holds
+  // the FP64 constants of the affine one for the polish and the adjoint
+  int nv = 0, proj = 0;
+  std::vector<int64_t> deg;
+  hpt_system_s* affine = nullptr;
   hpt_precision prec = HPT_FP64;
   int device = 0;
   std::vector<int32_t> msz, off, exps;
@@ -252,5 +263,24 @@ cudaError_t launch_finish_track(hpt_system s, int64_t p, const hpt_paths& st, vo
                                 int32_t* status_out, int32_t* steps_out, int32_t* done,
                                 cudaStream_t stm);
 cudaError_t launch_init_done(int64_t p, const int32_t* status, int32_t* done, cudaStream_t st);
+
+// Algorithm 3 (QR null-space form) for the points of one system: from the
+// extended Jacobian in log coordinates (ext, rows k < n, columns u < nv + 2)
+// and, in the projective form, the y^* row built from y.  mode 0 writes the
+// Euler and Newton directions (dE, dN: p x nv complex of the state precision)
+// and ok (p int32) for positions [0, p); mode 1 is one projective step of
+// the path state (step control of the projective form).  Shapes: N = rows of
+// J (n + proj) <= 8, 16, 24 (FP32), 32.
+cudaError_t launch_qr_directions(hpt_system s, int64_t p, const void* ext, const void* y, void* dE, void* dN,
+                                 int32_t* ok, cudaStream_t st);
+cudaError_t launch_qr_step(hpt_system s, int64_t p, const void* ext, const hpt_paths& S, const hpt_params& prm,
+                           cudaStream_t st);
+// Projective form: start points x0 (p x n complex128) become
+// (x0, 1)/|(x0, 1)| in the state (p x nv); the end points y_acc are
+// dehomogenized into x_out (p x n complex128).
+cudaError_t launch_paths_init_proj(hpt_system s, int64_t p, const void* x0, double tau0, const hpt_params& prm,
+                                   const hpt_paths& st, cudaStream_t stm);
+cudaError_t launch_finish_track_proj(hpt_system s, int64_t p, const hpt_paths& st, void* x_out,
+                                     int32_t* status_out, int32_t* steps_out, int32_t* done, cudaStream_t stm);
 
 }  // namespace hpt

@@ -252,7 +252,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   int cit = 0, ck = 0, cissued = 0;
   auto load_item = [&](int& xit, int& xk, bool cpart) {
     const int ls = sys_of(tile_of(xit));
-    const int ln = pm.sys_tab ? pm.sys_tab[ls].n : P.sys.n;
+    const int ln = pm.sys_tab ? pm.sys_tab[ls].ne : P.sys.ne;   // one image per equation
     const int lbytes = pm.sys_tab ? pm.sys_tab[ls].chunk_bytes : P.sys.chunk_bytes;
     const int lsplit = pm.sys_tab ? pm.sys_tab[ls].off_bhi : P.sys.off_bhi;
     const int64_t loff = pm.sys_tab ? pm.sys_tab[ls].chunk_off : P.sys.chunk_off;
@@ -283,7 +283,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   for (int it = 0; it < my_tiles; ++it) {
     const int tile = tile_of(it);
     const MixedSys S = pm.sys_tab ? pm.sys_tab[sys_of(tile)] : P.sys;
-    const int n = S.n;
+    const int n = S.n, ne = S.ne;   // variables, equations
     const uint32_t t_j = tbase + (uint32_t)(P.wbuf * 2 * S.MP);
     const int64_t pos = (int64_t)tile * 128 + row;   // position of this row
     const int64_t path = pm.list ? pm.list[pos] : pos;
@@ -344,22 +344,22 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
           if (u < n) {
             if (oHy) {
               const float2 iy = sInvY[u * 128 + row];
-              oHy[((size_t)path * n + kk) * n + u] = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
+              oHy[((size_t)path * ne + kk) * n + u] = make_float2(v.x * iy.x - v.y * iy.y, v.x * iy.y + v.y * iy.x);
             }
           } else if (u == n) {
-            if (oHt) oHt[(size_t)path * n + kk] = make_float2(v.x * t_inv, v.y * t_inv);
+            if (oHt) oHt[(size_t)path * ne + kk] = make_float2(v.x * t_inv, v.y * t_inv);
           } else if (u == n + 1) {
-            if (oH) oH[(size_t)path * n + kk] = v;
+            if (oH) oH[(size_t)path * ne + kk] = v;
           }
         }
       }
     };
 
-    for (int k = 0; k < n; ++k, ++g) {
+    for (int k = 0; k < ne; ++k, ++g) {
       // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
       // GEMM of equation k+1 is issued now and runs under this epilogue
       if (tid == 0) {
-        const bool ok1 = lookahead ? (k + 1 < n ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
+        const bool ok1 = lookahead ? (k + 1 < ne ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
         if (!ok1) atomicExch(sAbort, 1);
       }
       bool ok = mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g));   // e of equation k visible
@@ -601,7 +601,8 @@ int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }
 MixedSys mixed_sys_of(const hpt_system s) {
   const MixedLayout& L = s->ml;
   MixedSys m;
-  m.n = s->n;
+  m.n = s->nv;
+  m.ne = s->n;
   m.MP = L.MP;
   m.KX = L.KX;
   m.NJ = L.NJ;
@@ -612,7 +613,6 @@ MixedSys mixed_sys_of(const hpt_system s) {
   m.off_blo = L.off_blo;
   m.off_texp = L.off_texp;
   m.inv_D = (float)(1.0 / (double)s->D);
-  m.pad_ = 0;
   m.chunk_off = 0;
   return m;
 }

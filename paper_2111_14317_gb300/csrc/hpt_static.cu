@@ -58,6 +58,7 @@ extern "C" hpt_status hpt_step_static(hpt_system s, int64_t p, const hpt_paths* 
                                       const hpt_params* prm, void* stream) {
   if (!s) { set_error("NULL handle"); return HPT_EINVAL; }
   if (!prm || !S || p < 0 || nsteps < 0) { set_error("bad params, state, p or nsteps"); return HPT_EINVAL; }
+  if (s->proj) { set_error("hpt_step_static: the projective form is not supported"); return HPT_ENOTSUP; }
   const int n = s->n;
   const size_t cs = s->prec == HPT_FP64 ? 16 : 8;
   // layout: [re-solve counter, 256 B][re-solve list, p int64][extended

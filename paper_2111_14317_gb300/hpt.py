@@ -32,7 +32,8 @@ EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lif
            "hpt_paths_init", "hpt_step", "hpt_step_static", "hpt_track", "hpt_polish", "hpt_adjoint",
            "hpt_device_error", "hpt_profile_enable", "hpt_profile_read", "hpt_binomial_points",
            "hpt_batch_create", "hpt_batch_destroy", "hpt_batch_get_tuning", "hpt_batch_set_tuning",
-           "hpt_batch_track", "hpt_batch_autotune", "hpt_batch_stats"]
+           "hpt_batch_track", "hpt_batch_autotune", "hpt_batch_stats", "hpt_homogenize", "hpt_get_nvars",
+           "hpt_euler_newton"]
 
 
 class HptError(RuntimeError):
@@ -108,6 +109,9 @@ for _name, _args in {
     "hpt_batch_track": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "hpt_batch_autotune": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "hpt_batch_stats": [_VP, _VP, _VP, _VP],
+    "hpt_homogenize": [_VP, _VP],
+    "hpt_get_nvars": [_VP, _VP, _VP, _VP],
+    "hpt_euler_newton": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int
@@ -264,10 +268,28 @@ class System:
                "hpt_create_system")
         self._h = h
         self.cdtype = torch.complex128 if self.precision == HPT_FP64 else torch.complex64
+        self.nv, self.projective, self.degrees = self.n, False, None
 
     @classmethod
     def from_laurent(cls, sysm, cell, precision=HPT_FP64):
         return cls(sysm.n, sysm.m, sysm.exponents, sysm.coeffs, sysm.lifting, cell, precision)
+
+    def homogenize(self):
+        """The projective form of this system (hpt_homogenize): n equations in
+        nv = n + 1 homogeneous coordinates, the homogenizing one last."""
+        h = ctypes.c_void_p()
+        _check(_lib.hpt_homogenize(self._h, ctypes.byref(h)), "hpt_homogenize")
+        o = System.__new__(System)
+        o._h, o.n, o.M, o.precision, o.cdtype = h, self.n, self.M, self.precision, self.cdtype
+        nv, pj = ctypes.c_int32(0), ctypes.c_int32(0)
+        deg = np.zeros(self.n, np.int64)
+        _check(_lib.hpt_get_nvars(h, ctypes.byref(nv), ctypes.byref(pj), _np_ptr(deg)), "hpt_get_nvars")
+        o.nv, o.projective, o.degrees = int(nv.value), bool(pj.value), deg
+        return o
+
+    def new_state(self, p, device="cuda", pin=False):
+        """A PathState for p paths of this system (nv entries per path)."""
+        return PathState(p, self.nv, self.precision, device=device, pin=pin)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -302,17 +324,29 @@ class System:
 
     # ----------------------------------------------------------- device work
     def eval(self, y, t, stream=None, out=None):
-        """H (p,n), H_y (p,n,n), H_t (p,n) at y (p,n) complex, t (p,) float64."""
+        """H (p,n), H_y (p,n,nv), H_t (p,n) at y (p,nv) complex, t (p,) float64."""
         p = y.shape[0]
         assert y.dtype == self.cdtype and y.is_contiguous() and t.dtype == torch.float64
         if out is None:
             out = (torch.empty(p, self.n, dtype=self.cdtype, device=y.device),
-                   torch.empty(p, self.n, self.n, dtype=self.cdtype, device=y.device),
+                   torch.empty(p, self.n, self.nv, dtype=self.cdtype, device=y.device),
                    torch.empty(p, self.n, dtype=self.cdtype, device=y.device))
         H, Hy, Ht = out
         _check(_lib.hpt_eval(self._h, p, _t_ptr(y), _t_ptr(t), _t_ptr(H), _t_ptr(Hy), _t_ptr(Ht),
                              _stream(stream)), "hpt_eval")
         return H, Hy, Ht
+
+    def euler_newton(self, y, tau, stream=None):
+        """Algorithm 3 at y (p,nv) complex, tau (p,) float64: the Euler and
+        Newton directions (p,nv) each and ok (p,) int32."""
+        p = y.shape[0]
+        assert y.dtype == self.cdtype and y.is_contiguous() and tau.dtype == torch.float64
+        dE = torch.empty(p, self.nv, dtype=self.cdtype, device=y.device)
+        dN = torch.empty(p, self.nv, dtype=self.cdtype, device=y.device)
+        ok = torch.empty(p, dtype=torch.int32, device=y.device)
+        _check(_lib.hpt_euler_newton(self._h, p, _t_ptr(y), _t_ptr(tau.contiguous()), _t_ptr(dE), _t_ptr(dN),
+                                     _t_ptr(ok), _stream(stream)), "hpt_euler_newton")
+        return dE, dN, ok
 
     def paths_init(self, state, y0, params=None, stream=None):
         params = params or Params()
