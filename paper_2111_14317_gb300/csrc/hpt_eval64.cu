@@ -177,6 +177,8 @@ cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const doubl
     eval_fp64_kernel<8, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   else if (s->nv <= 16)
     eval_fp64_kernel<16, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
+  else if (s->nv <= 24)
+    eval_fp64_kernel<24, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   else
     eval_fp64_kernel<32, false><<<(unsigned)blocks, 128, 0, st>>>(f, p, yy, tau, tau_is_t, ext, H, Hy, Ht, none, nullptr);
   prof_end(s, pi, st);

@@ -27,7 +27,7 @@
 // not change).
 //
 // Mapping (as the LU solve): a group of G lanes owns one path, lane l holds
-// rows l + G s (s < R) in registers, "shifted" so that register 0 is the
+// R rows in registers (row_in_slot), "shifted" so that register 0 is the
 // current column; row k's owner writes g_k (live width, padded with zeros to
 // a multiple of four) into the group's shared memory, packed row after row,
 // from where all lanes read it for the dot products <row, g> and the
@@ -44,12 +44,17 @@ namespace {
 constexpr int kQrThreads = 128;
 
 // Shared memory of one group: the reflectors g_k packed (row k holds
-// round_up(C - k, 4) complex) and beta_k; padded so that consecutive groups
-// start 8 banks apart.
+// round_up(C - k, 4) complex, C = N + 2 <= CM) and beta_k; padded so that
+// consecutive groups start 8 banks apart.
+constexpr int packed_entries(int CM) {
+  int e = 0;
+  for (int w = 3; w <= CM; ++w) e += (w + 3) / 4 * 4;   // widths C - k for N = CM - 2 rows
+  return e;
+}
 template <typename T, int G, int R, int CM>
 struct QrSmem {
   static constexpr int NR = G * R;
-  static constexpr int entries = NR * CM + 4 * NR;   // >= sum_k round_up(C - k, 4) + CM slack
+  static constexpr int entries = packed_entries(CM);
   static constexpr int raw_words = (entries * 2 * (int)sizeof(T) + NR * (int)sizeof(T)) / 4;
   static constexpr int words = (raw_words + 31) / 32 * 32 + 8;
   static constexpr int bytes = words * 4;
@@ -57,37 +62,74 @@ struct QrSmem {
 
 __device__ __forceinline__ int round4(int v) { return (v + 3) & ~3; }
 
+// Two consecutive complex entries of a group's reflector storage (an even
+// index: 16-byte aligned for complex64, one 16-byte load).
+__device__ __forceinline__ void ld_pair(const cx<float>* U, int i, cx<float>& g0, cx<float>& g1) {
+  const float4 v = *(const float4*)(U + i);
+  g0 = mk<float>(v.x, v.y);
+  g1 = mk<float>(v.z, v.w);
+}
+__device__ __forceinline__ void ld_pair(const cx<double>* U, int i, cx<double>& g0, cx<double>& g1) {
+  g0 = U[i];
+  g1 = U[i + 1];
+}
+
+// Row order.  The rows are factored in index order, and slot s of every lane
+// holds a block of consecutive rows, so that whole slots finish early and are
+// skipped (a warp-uniform test): the first r0 = N - G (R - 1) rows sit in the
+// last slot (lanes 0 .. r0-1; the rest of that slot is zero padding), the next
+// G in slot 0, then slot 1, ..  Returns the row of (slot s, lane) or N (padding).
+template <int G, int R>
+__device__ __forceinline__ int row_in_slot(int N, int s, int lane) {
+  const int r0 = N - G * (R - 1);
+  return s == R - 1 ? (lane < r0 ? lane : N) : r0 + G * s + lane;
+}
+// The largest row index of slot s (the slot is done once k passes it).
+template <int G, int R>
+__device__ __forceinline__ int slot_last_row(int N, int s) {
+  const int r0 = N - G * (R - 1);
+  return s == R - 1 ? r0 - 1 : r0 + G * s + G - 1;
+}
+
 // Loads the rows of one path (rows < n from the scratch, the y^* row in log
 // coordinates if proj), scales each by a power of two; returns whether every
 // entry is finite (group-uniform).
 template <typename T, typename S, int G, int R, int CM>
 __device__ __forceinline__ bool qr_load(int n, int nv, int proj, const void* __restrict__ ext, int64_t q,
                                         const void* __restrict__ y, size_t vbase, bool valid, cx<T> (&a)[R][CM]) {
+  typedef typename cplx_t<S>::type V;
   const int lane = threadIdx.x & (G - 1);
   const int C = nv + 2;
+  // entry (q, r, c) of the scratch sits at tile base + (r C + c) 128 (ext_index)
+  const V* tile = (const V*)ext + ((size_t)(q >> 7) * (size_t)(nv * C)) * 128 + (size_t)(q & 127);
+  // all loads first (independent, so they overlap), then the checks
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int r = row_in_slot<G, R>(nv, s, lane);
+    const bool eq = valid && r < n;
+    const bool ystar = valid && proj && r == n;
+    const V* row = tile + (size_t)(eq ? r : 0) * C * 128;
+#pragma unroll
+    for (int c = 0; c < CM; ++c) {
+      V v = V{0, 0};
+      if (c < C && eq) v = row[(size_t)c * 128];
+      if (c < nv && ystar) {
+        const V w = ((const V*)y)[vbase + c];
+        v.x = w.x * w.x + w.y * w.y;
+        v.y = 0;
+      }
+      a[s][c] = mk<T>((T)v.x, (T)v.y);
+    }
+  }
   T chk = T(0);
 #pragma unroll
   for (int s = 0; s < R; ++s) {
-    const int r = lane + G * s;
-    const bool eq = valid && r < n;
-    const bool ystar = valid && proj && r == n;
-#pragma unroll
-    for (int c = 0; c < CM; ++c) {
-      a[s][c] = mk<T>(0, 0);
-      if (c < C) {
-        if (eq) {
-          const cx<S> v = ld<S>(ext, ext_index(q, r, c, nv));
-          a[s][c] = mk<T>((T)v.x, (T)v.y);
-        } else if (ystar && c < nv) {
-          const cx<S> v = ld<S>(y, vbase + c);
-          a[s][c] = mk<T>((T)v.x * (T)v.x + (T)v.y * (T)v.y, T(0));
-        }
-      }
-      chk += t_abs(a[s][c].x) + t_abs(a[s][c].y);
-    }
     T m = T(0);
 #pragma unroll
-    for (int c = 0; c < CM; ++c) m = t_max(m, cmag(a[s][c]));
+    for (int c = 0; c < CM; ++c) {
+      chk += t_abs(a[s][c].x) + t_abs(a[s][c].y);
+      m = t_max(m, cmag(a[s][c]));
+    }
     const T d = pow2_inv(m);
 #pragma unroll
     for (int c = 0; c < CM; ++c) a[s][c] = cscale(a[s][c], d);
@@ -109,80 +151,78 @@ __device__ __forceinline__ bool qr_null(int nv, cx<T> (&a)[R][CM], cx<T> (&wE)[R
   const int N = nv, C = nv + 2;
   cx<T>* U = (cx<T>*)sm;
   T* beta = (T*)(sm + QrSmem<T, G, R, CM>::entries * sizeof(cx<T>));
-  bool used[R];
+  int rowi[R];
 #pragma unroll
-  for (int s = 0; s < R; ++s) used[s] = false;
+  for (int s = 0; s < R; ++s) rowi[s] = row_in_slot<G, R>(N, s, lane);
+  const int r0 = N - G * (R - 1);
   bool ok = true;
   int off = 0;   // packed offset of row k's reflector
 #pragma unroll 1
   for (int k = 0; k < N; ++k) {
     const int width = C - k, len = round4(width);
-    const int ol = k & (G - 1), os = k / G;
+    const int ol = k < r0 ? k : (k - r0) & (G - 1), os = k < r0 ? R - 1 : (k - r0) / G;
+    // the owner forms the reflector of row k from its registers (os is
+    // warp-uniform, so one copy runs): sigma = |live part|, g = r +
+    // e^{i arg r_0} sigma e_0 (phase 1 when r_0 = 0), beta = 1 / (sigma (sigma
+    // + |r_0|)); it stores g (zero-padded to len) and beta for the group
     if (lane == ol) {
-      // the owner's slot chosen entry by entry (static register indices)
-      T s2 = T(0);
 #pragma unroll
-      for (int c = 0; c < CM; ++c) {
-        cx<T> v = a[0][c];
+      for (int s = 0; s < R; ++s) {
+        if (s == os) {
+          T s2 = T(0);
 #pragma unroll
-        for (int s = 1; s < R; ++s) v = (os == s) ? a[s][c] : v;
-        if (c < width) s2 += abs2(v);
+          for (int c = 0; c < CM; ++c)
+            if (c < width) s2 += abs2(a[s][c]);
+          const cx<T> r0v = a[s][0];
+          const T sigma = t_sqrt(s2), m0 = t_sqrt(abs2(r0v));
+          const T im0 = t_rcp(m0);   // m0 flushed to zero: any unit phase will do
+          const cx<T> ph = (m0 > T(0) && isfinite(im0)) ? cscale(r0v, sigma * im0) : mk<T>(sigma, T(0));
+          beta[k] = sigma > T(0) ? t_rcp(sigma * (sigma + m0)) : T(0);
+          U[off] = mk<T>(r0v.x + ph.x, r0v.y + ph.y);
+#pragma unroll
+          for (int c = 1; c < CM; ++c)
+            if (c < len) U[off + c] = c < width ? a[s][c] : mk<T>(0, 0);
+        }
       }
-      const T sigma = t_sqrt(s2);
-      cx<T> r0 = a[0][0];
-#pragma unroll
-      for (int s = 1; s < R; ++s) r0 = (os == s) ? a[s][0] : r0;
-      const T m0 = cabs_t(r0);
-      // e^{i arg r0} sigma (phase 1 when r0 = 0)
-      const cx<T> ph = m0 > T(0) ? cscale(r0, sigma / m0) : mk<T>(sigma, T(0));
-      const T b = sigma > T(0) ? T(1) / (sigma * (sigma + m0)) : T(0);
-#pragma unroll
-      for (int c = 0; c < CM; ++c) {
-        cx<T> v = a[0][c];
-#pragma unroll
-        for (int s = 1; s < R; ++s) v = (os == s) ? a[s][c] : v;
-        if (c == 0) v = mk<T>(v.x + ph.x, v.y + ph.y);
-        if (c < len) U[off + c] = c < width ? v : mk<T>(0, 0);
-      }
-      beta[k] = b;
-#pragma unroll
-      for (int s = 0; s < R; ++s) used[s] = used[s] || (os == s);
     }
     __syncwarp();
     const T b = beta[k];
     if (!(b > T(0)) || !isfinite(b)) ok = false;
-    // t_s = beta <row_s, g> over the live width (rows already used: 0)
-    cx<T> t[R];
+    // per slot whose rows are not all done (a warp-uniform test): t = beta
+    // <row, g> over the live width (two partial sums, even and odd columns,
+    // for independent chains; rows up to k get t = 0), then the shifted
+    // update a[c-1] = a[c] - t g[c] (column k leaves the rows: it is L's)
 #pragma unroll
-    for (int s = 0; s < R; ++s) t[s] = mk<T>(0, 0);
+    for (int s = 0; s < R; ++s) {
+      if (slot_last_row<G, R>(N, s) > k) {
+        cx<T> t0 = mk<T>(0, 0), t1 = mk<T>(0, 0);
 #pragma unroll
-    for (int c0 = 0; c0 < CM; c0 += 4) {
-      if (c0 < width) {
+        for (int c0 = 0; c0 < CM; c0 += 4) {
+          if (c0 < width) {
 #pragma unroll
-        for (int c = c0; c < c0 + 4; ++c) {
-          if (c < CM) {
-            const cx<T> g = U[off + c];
-#pragma unroll
-            for (int s = 0; s < R; ++s) {   // t += row conj(g)
-              t[s].x += a[s][c].x * g.x + a[s][c].y * g.y;
-              t[s].y += a[s][c].y * g.x - a[s][c].x * g.y;
+            for (int c = c0; c < c0 + 4 && c < CM; c += 2) {
+              cx<T> g0, g1;
+              ld_pair(U, off + c, g0, g1);
+              t0.x += a[s][c].x * g0.x + a[s][c].y * g0.y;
+              t0.y += a[s][c].y * g0.x - a[s][c].x * g0.y;
+              if (c + 1 < CM) {
+                t1.x += a[s][c + 1].x * g1.x + a[s][c + 1].y * g1.y;
+                t1.y += a[s][c + 1].y * g1.x - a[s][c + 1].x * g1.y;
+              }
             }
           }
         }
-      }
-    }
+        const cx<T> ts = rowi[s] <= k ? mk<T>(0, 0) : cscale(mk<T>(t0.x + t1.x, t0.y + t1.y), b);
 #pragma unroll
-    for (int s = 0; s < R; ++s) t[s] = used[s] ? mk<T>(0, 0) : cscale(t[s], b);
-    // shifted update: a[c-1] = a[c] - t g[c] (column k leaves the rows: it is L's)
+        for (int c0 = 0; c0 < CM; c0 += 4) {
+          if (c0 < width) {
 #pragma unroll
-    for (int c0 = 0; c0 < CM; c0 += 4) {
-      if (c0 < width) {
-#pragma unroll
-        for (int c = c0; c < c0 + 4; ++c) {
-          if (c >= 1 && c < CM) {
-            const cx<T> g = U[off + c];
-#pragma unroll
-            for (int s = 0; s < R; ++s) a[s][c - 1] = csub_mul(a[s][c], t[s], g);
+            for (int c = c0; c < c0 + 4 && c < CM; c += 2) {
+              cx<T> g0, g1;
+              ld_pair(U, off + c, g0, g1);
+              if (c >= 1) a[s][c - 1] = csub_mul(a[s][c], ts, g0);
+              if (c + 1 < CM) a[s][c] = csub_mul(a[s][c + 1], ts, g1);
+            }
           }
         }
       }
@@ -279,8 +319,8 @@ __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t 
     dEacc[s] = mine ? ld<T>(S.dE_acc, vbase + j) : mk<T>(0, 0);
     if (mine) {
       solfin = solfin && finite(xE[s]) && finite(xN[s]);
-      ny = t_max(ny, cabs_t(y[s]));
-      nd = t_max(nd, cabs_t(xN[s]));
+      ny = t_max(ny, t_sqrt(abs2(y[s])));   // unit-norm points, small corrections: no overflow
+      nd = t_max(nd, t_sqrt(abs2(xN[s])));
     }
   }
   solfin = (__ballot_sync(gmask, solfin) & gmask) == gmask;
@@ -324,12 +364,12 @@ __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t 
 #pragma unroll
     for (int s = 1; s < R; ++s)
       if (s == n / G) vh = yacc[s];
-    const T mh = __shfl_sync(gmask, cabs_t(vh), n & (G - 1), G);
+    const T mh = __shfl_sync(gmask, t_sqrt(abs2(vh)), n & (G - 1), G);
     bool div = false;
 #pragma unroll
     for (int s = 0; s < R; ++s) {
       if (lane + G * s < n) {
-        const T m = cabs_t(yacc[s]) / mh;
+        const T m = t_sqrt(abs2(yacc[s])) / mh;
         div = div || !(m < (T)prm.div_bound) || !(m > (T)(1.0 / prm.div_bound));
       }
     }
@@ -403,7 +443,7 @@ __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t 
 // points y (p x nv), directions to dE, dN, regularity to ok.  STEP = true:
 // one projective step of every ACTIVE path of the state.
 template <typename T, int G, int R, int CM, bool STEP>
-__global__ void __launch_bounds__(kQrThreads)
+__global__ void __launch_bounds__(kQrThreads, (sizeof(T) == 4 && R == 3 && CM == 20) ? 3 : 1)
 qr_kernel(int n, int nv, int proj, int64_t p, const void* __restrict__ ext, const void* __restrict__ yin,
           void* __restrict__ dE, void* __restrict__ dN, int32_t* __restrict__ okout, hpt_paths S, hpt_params prm) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -511,8 +551,10 @@ cudaError_t launch_qr_shape(hpt_system s, int64_t p, const void* ext, const void
   return cudaGetLastError();
 }
 
-// Shapes by N = nv: (G, R, CM) = (8, 1, 10) for N <= 8, (8, 2, 18) for
-// N <= 16, (8, 3, 26) for N <= 24 (FP32), (32, 1, 34) otherwise.
+// Shapes by N = nv (CM >= N + 2 columns in registers): (G, R, CM) =
+// (8, 1, 10) for N <= 8, (8, 2, 18) for N <= 16; FP32: (8, 3, 20) for N <= 18,
+// (8, 3, 26) for N <= 24, (32, 1, 34) above; FP64 (whose rows take twice the
+// registers): (32, 1, 20), (32, 1, 26), (32, 1, 34).
 template <bool STEP>
 cudaError_t launch_qr_any(hpt_system s, int64_t p, const void* ext, const void* y, void* dE, void* dN, int32_t* ok,
                           const hpt_paths& S, const hpt_params& prm, cudaStream_t st) {
@@ -521,10 +563,13 @@ cudaError_t launch_qr_any(hpt_system s, int64_t p, const void* ext, const void* 
   if (s->prec == HPT_FP64) {
     if (N <= 8) return launch_qr_shape<double, 8, 1, 10, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
     if (N <= 16) return launch_qr_shape<double, 8, 2, 18, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
+    if (N <= 18) return launch_qr_shape<double, 32, 1, 20, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
+    if (N <= 24) return launch_qr_shape<double, 32, 1, 26, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
     return launch_qr_shape<double, 32, 1, 34, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
   }
   if (N <= 8) return launch_qr_shape<float, 8, 1, 10, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
   if (N <= 16) return launch_qr_shape<float, 8, 2, 18, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
+  if (N <= 18) return launch_qr_shape<float, 8, 3, 20, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
   if (N <= 24) return launch_qr_shape<float, 8, 3, 26, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
   return launch_qr_shape<float, 32, 1, 34, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
 }
