@@ -268,6 +268,7 @@ def run_gpu(args):
         out["batch"] = run_batch(args, dev)
     if args.workload == "all":
         out["track_adjoint"] = run_track_adjoint(args, dev)
+        out["projective"] = run_projective(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     return out, ws, rank
@@ -438,6 +439,83 @@ def run_track_adjoint(args, dev):
     return out
 
 
+PROJ_WORKLOAD = ("projective form (Section 2.2) of the n=16 throughput workload: 16 equations in 17 homogeneous "
+                 "coordinates, exponents (a, deg_k - 1^T a); 65,536 paths at (x, 1)/|(x, 1)|; one hpt_step "
+                 "(evaluation + Algorithm 3 by QR + projective step control) per step")
+# bytes one projective QR step moves per path: the extended Jacobian (16 rows x
+# 19 complex64), y, y_acc, dE_acc (17 complex64 each, read and written), three
+# doubles and five int32 (read and written)
+QR_BYTES_PATH = 16 * 19 * 8 + 3 * 17 * 8 * 2 + 3 * 8 * 2 + 5 * 4 * 2
+
+
+def run_projective(args, dev):
+    """hpt_step on projective handles of the n=16 workload, both forms, timed as
+    the headline step (state restored, L2 flushed before every timed step)."""
+    import torch
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+    sysm, cell = _workload()
+    x_np, t_np = W.random_points(shard_seed(0), PATHS, N_VARS)
+    y_np = np.concatenate([x_np, np.ones((PATHS, 1))], axis=1)
+    y_np /= np.linalg.norm(y_np, axis=1, keepdims=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks, peak_kind = _peaks()
+    out = {"workload": PROJ_WORKLOAD}
+    for form, prec in (("mixed", hpt.HPT_MIXED), ("fp64", hpt.HPT_FP64)):
+        ha = hpt.System.from_laurent(sysm, cell, prec)
+        h = ha.homogenize()
+        prm = hpt.Params(tol_accept=3e-3 if prec == hpt.HPT_MIXED else 1e-3)
+        st = h.new_state(PATHS, device=dev)
+        yd = torch.from_numpy(y_np).to(dev, h.cdtype)
+        st.y.copy_(yd)
+        st.y_acc.copy_(yd)
+        st.tau.copy_(torch.from_numpy(np.log(t_np)))
+        st.tau_acc.copy_(st.tau)
+        st.dtau.fill_(0.01)
+        st.accepts.fill_(1)
+        pristine = st.arena.clone()
+        steps = args.steps if form == "mixed" else max(3, min(args.steps, args.fp64_steps))
+        for _ in range(args.warmup):
+            st.arena.copy_(pristine)
+            h.step(st, 1, prm)
+        torch.cuda.synchronize()
+        res = {}
+        for profile in (False, True):
+            h.profile(profile)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            for i in range(steps):
+                st.arena.copy_(pristine)
+                flush.zero_()
+                ev[i][0].record()
+                h.step(st, 1, prm)
+                ev[i][1].record()
+            torch.cuda.synchronize()
+            h.profile(False)
+            if not profile:
+                res["ms_per_step"] = sum(a.elapsed_time(b) for a, b in ev) / steps
+        kern = h.profile_read()
+        assert h.device_error() == 0, "device-side wait timed out"
+        res["value"] = PATHS / (res["ms_per_step"] * 1e-3)
+        res["unit"] = UNIT
+        res["kernels"] = {k: {"launches": v[0], "ms_avg": v[1] / max(v[0], 1)} for k, v in kern.items()}
+        qr = kern.get("qr_step")
+        if qr:
+            avg_s = qr[1] / max(qr[0], 1) * 1e-3
+            ach = PATHS * QR_BYTES_PATH / avg_s / 1e9
+            res["roofline_qr"] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                  "frac": ach / peaks["hbm_gbs"], "bytes_per_path": QR_BYTES_PATH,
+                                  "peak_source": f"{peak_kind} (MEASURED_PEAKS.json)",
+                                  "traffic": _traffic("qr_step") if form == "mixed" else None}
+        out[form] = res
+        h.close()
+        ha.close()
+        del st, pristine
+        torch.cuda.empty_cache()
+    out["mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def cpu_baseline(seconds=12.0, max_paths=PATHS):
     """Times the oracle's step (as it stands) on growing slices of the same
     workload until about `seconds` of work is done."""
@@ -477,9 +555,10 @@ def main():
     ap.add_argument("--batch-paths", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default tuning")
-    ap.add_argument("--workload", default="all", choices=["all", "step", "batch"],
-                    help="step: the n=16 hpt_step line only; batch: the many-systems batch only "
-                         "(prints its own JSON object, for profiling)")
+    ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective"],
+                    help="step: the n=16 hpt_step line only; batch: the many-systems batch only; "
+                         "projective: the projective-form step only (the last two print their own JSON "
+                         "object, for profiling)")
     args = ap.parse_args()
     ws, rank, _ = _dist()
 
@@ -511,6 +590,13 @@ def main():
         hbuild.build()
         torch.cuda.set_device(0)
         print(json.dumps({"batch": run_batch(args, torch.device("cuda", 0))}))
+        return
+    if args.workload == "projective":
+        import torch
+        from paper_2111_14317_gb300 import build as hbuild
+        hbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"projective": run_projective(args, torch.device("cuda", 0))}))
         return
     if args.workload == "step":
         args.batch_systems = 0
@@ -575,6 +661,8 @@ def main():
         line["batch"] = out["batch"]
     if "track_adjoint" in out:
         line["track_adjoint"] = out["track_adjoint"]
+    if "projective" in out:
+        line["projective"] = out["projective"]
     print(json.dumps(line))
 
 
