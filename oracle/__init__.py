@@ -77,7 +77,7 @@ class _Params(ctypes.Structure):
                 ("grow", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("grow_after", ctypes.c_int32), ("max_steps", ctypes.c_int32),
                 ("div_bound", ctypes.c_double), ("polish_tol", ctypes.c_double),
-                ("polish_iters", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("polish_iters", ctypes.c_int32), ("predictor", ctypes.c_int32)]
 
 
 @dataclass
@@ -94,11 +94,12 @@ class Params:
     div_bound: float = 1e8
     polish_tol: float = 1e-13
     polish_iters: int = 8
+    predictor: int = 0          # 0: Euler; 1: cubic Hermite (two accepted points)
 
     def _c(self):
         return _Params(self.tol_accept, self.dtau_init, self.dtau_min, self.dtau_max,
                        self.grow, self.shrink, self.grow_after, self.max_steps,
-                       self.div_bound, self.polish_tol, self.polish_iters, 0)
+                       self.div_bound, self.polish_tol, self.polish_iters, self.predictor)
 
 
 def _ptr(a):
@@ -175,7 +176,8 @@ class System:
         _load().ora_step(ctypes.byref(self._c), ctypes.byref(params._c()), ctypes.c_int64(s.p),
                          ctypes.c_int32(nsteps), _ptr(s.y), _ptr(s.tau), _ptr(s.dtau),
                          _ptr(s.yacc), _ptr(s.tauacc), _ptr(s.dEacc), _ptr(s.status),
-                         _ptr(s.steps), _ptr(s.accepts), _ptr(s.rejects), _ptr(s.streak))
+                         _ptr(s.steps), _ptr(s.accepts), _ptr(s.rejects), _ptr(s.streak),
+                         _ptr(s.yprev), _ptr(s.tauprev), _ptr(s.dEprev))
         return state
 
     def track(self, params, y0, tau0):
@@ -238,10 +240,17 @@ class PathState:
     accepts: np.ndarray
     rejects: np.ndarray
     streak: np.ndarray
+    yprev: np.ndarray = None      # the accepted point before the last one (Hermite predictor)
+    tauprev: np.ndarray = None
+    dEprev: np.ndarray = None
     p: int = field(init=False)
 
     def __post_init__(self):
         self.p = self.y.shape[0]
+        if self.yprev is None:
+            self.yprev = np.zeros_like(self.y)
+            self.dEprev = np.zeros_like(self.y)
+            self.tauprev = np.zeros(self.p)
 
     @classmethod
     def start(cls, y0, tau0, dtau0):
@@ -257,4 +266,4 @@ class PathState:
     def copy(self):
         return PathState(**{k: getattr(self, k).copy() for k in
                             ("y", "tau", "dtau", "yacc", "tauacc", "dEacc", "status", "steps",
-                             "accepts", "rejects", "streak")})
+                             "accepts", "rejects", "streak", "yprev", "tauprev", "dEprev")})

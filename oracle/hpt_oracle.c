@@ -71,7 +71,7 @@ typedef struct {
     double div_bound;      /* |y_j| > bound or |y_j| < 1/bound: diverged */
     double polish_tol;     /* final Newton stop: |dN|_inf/max(1,|y|_inf) */
     int32_t polish_iters;
-    int32_t pad_;
+    int32_t predictor;     /* 0: Euler; 1: cubic Hermite through the last two accepted points */
 } ora_params;
 
 enum { ORA_ACTIVE = 0, ORA_CONVERGED = 1, ORA_DIVERGED = 2, ORA_UNDERFLOW = 3,
@@ -215,7 +215,27 @@ static int directions(const ora_sys* s, const cplx* y, double tau, cplx* dE, cpl
 typedef struct {
     cplx* y; double* tau; double* dtau; cplx* yacc; double* tauacc; cplx* dEacc;
     int32_t* status; int32_t* steps; int32_t* accepts; int32_t* rejects; int32_t* streak;
+    cplx* yprev; double* tauprev; cplx* dEprev;   /* the accepted point before the last one */
 } ora_path;
+
+/* The prediction at tau_acc + h.  Euler (Section 2.3): y_acc + h dE_acc.
+ * Cubic Hermite (one of the predictors Section 2.3 names for the Euler
+ * direction): the cubic p with p(tau0) = y0, p'(tau0) = d0, p(tau1) = y1,
+ * p'(tau1) = d1 through the last two accepted points, evaluated at tau1 + h;
+ * with s = (tau - tau0)/(tau1 - tau0) its basis is h00 = 2s^3 - 3s^2 + 1,
+ * h10 = s^3 - 2s^2 + s, h01 = -2s^3 + 3s^2, h11 = s^3 - s^2 (the derivative
+ * terms scaled by tau1 - tau0).  Used once two accepted points exist. */
+static void predict(int n, const ora_params* P, const ora_path* q, double h, cplx* out) {
+    const double d = *q->tauacc - (q->tauprev ? *q->tauprev : 0.0);
+    if (P->predictor == 1 && *q->accepts >= 2 && d > 0.0) {
+        const double s = 1.0 + h / d, s2 = s * s, s3 = s2 * s;
+        const double h00 = 2 * s3 - 3 * s2 + 1, h10 = s3 - 2 * s2 + s, h01 = -2 * s3 + 3 * s2, h11 = s3 - s2;
+        for (int j = 0; j < n; ++j)
+            out[j] = h00 * q->yprev[j] + h10 * d * q->dEprev[j] + h01 * q->yacc[j] + h11 * d * q->dEacc[j];
+        return;
+    }
+    for (int j = 0; j < n; ++j) out[j] = q->yacc[j] + h * q->dEacc[j];
+}
 
 /* One Euler-Newton step (Section 8: one Euler prediction, one Newton
  * iteration) with step-size control.  The state holds the predicted point y
@@ -233,6 +253,10 @@ static void step_one(const ora_sys* s, const ora_params* P, ora_path* q) {
         accept = err <= P->tol_accept;
     }
     if (accept) {
+        if (P->predictor == 1 && *q->accepts >= 1) {   /* keep the accepted point being replaced */
+            for (int j = 0; j < n; ++j) { q->yprev[j] = q->yacc[j]; q->dEprev[j] = q->dEacc[j]; }
+            *q->tauprev = *q->tauacc;
+        }
         for (int j = 0; j < n; ++j) { q->yacc[j] = q->y[j] + dN[j]; q->dEacc[j] = dE[j]; }
         *q->tauacc = *q->tau;
         *q->accepts += 1;
@@ -260,7 +284,7 @@ static void step_one(const ora_sys* s, const ora_params* P, ora_path* q) {
         if (*q->dtau < P->dtau_min) { *q->status = ORA_UNDERFLOW; return; }
     }
     double h = fmin(*q->dtau, -*q->tauacc);
-    for (int j = 0; j < n; ++j) q->y[j] = q->yacc[j] + h * q->dEacc[j];
+    predict(n, P, q, h, q->y);
     *q->tau = *q->tauacc + h;
     if (*q->steps >= P->max_steps) *q->status = ORA_MAX_STEPS;
 }
@@ -350,13 +374,13 @@ int ora_directions(const ora_sys* s, int64_t p, const double* y, const double* t
 int ora_step(const ora_sys* s, const ora_params* P, int64_t p, int32_t nsteps,
              double* y, double* tau, double* dtau, double* yacc, double* tauacc,
              double* dEacc, int32_t* status, int32_t* steps, int32_t* accepts,
-             int32_t* rejects, int32_t* streak) {
+             int32_t* rejects, int32_t* streak, double* yprev, double* tauprev, double* dEprev) {
     const int n = s->n;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t q = 0; q < p; ++q) {
         ora_path st = {(cplx*)y + q * n, tau + q, dtau + q, (cplx*)yacc + q * n, tauacc + q,
                        (cplx*)dEacc + q * n, status + q, steps + q, accepts + q, rejects + q,
-                       streak + q};
+                       streak + q, (cplx*)yprev + q * n, tauprev + q, (cplx*)dEprev + q * n};
         for (int r = 0; r < nsteps; ++r) step_one(s, P, &st);
     }
     return 0;
@@ -370,13 +394,14 @@ int ora_track(const ora_sys* s, const ora_params* P, int64_t p, const double* y0
     const int n = s->n;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t q = 0; q < p; ++q) {
-        cplx y[ORA_NMAX], yacc[ORA_NMAX], dEacc[ORA_NMAX];
-        double tau = tau0, dtau = P->dtau_init, tauacc = tau0;
+        cplx y[ORA_NMAX], yacc[ORA_NMAX], dEacc[ORA_NMAX], yprev[ORA_NMAX], dEprev[ORA_NMAX];
+        double tau = tau0, dtau = P->dtau_init, tauacc = tau0, tauprev = tau0;
         int32_t st = ORA_ACTIVE, steps = 0, acc = 0, rej = 0, streak = 0;
         memcpy(y, (const cplx*)y0 + q * n, sizeof(cplx) * n);
         memcpy(yacc, y, sizeof(cplx) * n);
         for (int j = 0; j < n; ++j) dEacc[j] = 0.0;
-        ora_path ps = {y, &tau, &dtau, yacc, &tauacc, dEacc, &st, &steps, &acc, &rej, &streak};
+        ora_path ps = {y, &tau, &dtau, yacc, &tauacc, dEacc, &st, &steps, &acc, &rej, &streak,
+                       yprev, &tauprev, dEprev};
         while (st == ORA_ACTIVE) step_one(s, P, &ps);
         double perr = NAN;
         if (st == ORA_CONVERGED) perr = polish_one(s, P, yacc);

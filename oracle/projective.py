@@ -22,14 +22,15 @@ homotopy"):
   + H = 0, y^* dN = 0).  The same steps with no y^* row give the affine
   directions (N = n).
 * Tracking in homogeneous coordinates.  The paper gives the directions, not a
-  projective step rule; the rule here is the affine tracker's (one Euler
+  projective step rule; the rule here is the affine tracker's (one
   prediction, one Newton correction, Section 8, with the same step-size
-  control) plus two readings: after every Newton correction the point is
-  scaled back to unit Euclidean norm (and the stored Euler direction by the
-  same factor), and a path is divergent when a dehomogenized coordinate
-  |y_j / y_n| leaves (1/div_bound, div_bound), the affine test on x = y'/y_n,
-  checked before the end-of-path test (a path can reach tau = 0 at
-  infinity: y_n = 0 is an ordinary point of projective space).  Start
+  control and the same predictor choice) plus two readings: after every
+  Newton correction the point is scaled back to unit Euclidean norm (and the
+  stored Euler direction by the same factor), and a path is divergent when a
+  dehomogenized coordinate |y_j / y_n| leaves (1/div_bound, div_bound), the
+  affine test on x = y'/y_n, checked before the end-of-path test (a path can
+  reach tau = 0 at infinity: y_n = 0 is an ordinary point of projective
+  space).  Start
   points are (x0, 1)/|(x0, 1)|; end points are dehomogenized and then
   polished by the affine oracle.
 
@@ -119,6 +120,24 @@ def null_directions(J):
     return dE, dN, ok
 
 
+def _predict(P, s, q, h):
+    """Euler, or the cubic Hermite interpolant through the last two accepted
+    points (values and Euler directions) evaluated at tau_acc + h.  In
+    homogeneous coordinates the corrector leaves a point's phase free (y and
+    e^{i theta} y are one point), so the previous point and its direction are
+    first turned into the phase of the last one (y_acc^* y_prev real and
+    positive); otherwise the extrapolation amplifies phase differences."""
+    d = s.tauacc[q] - s.tauprev[q]
+    if P.predictor == 1 and s.accepts[q] >= 2 and d > 0:
+        t = 1.0 + h / d
+        h00, h10 = 2 * t**3 - 3 * t**2 + 1, t**3 - 2 * t**2 + t
+        h01, h11 = -2 * t**3 + 3 * t**2, t**3 - t**2
+        dot = np.vdot(s.yacc[q], s.yprev[q])
+        u = np.conj(dot) / abs(dot) if dot != 0 else 1.0
+        return h00 * u * s.yprev[q] + h10 * d * u * s.dEprev[q] + h01 * s.yacc[q] + h11 * d * s.dEacc[q]
+    return s.yacc[q] + h * s.dEacc[q]
+
+
 class ProjectiveSystem:
     """The homogenized homotopy of a Laurent system with its t-exponents."""
 
@@ -182,6 +201,8 @@ class ProjectiveSystem:
                 s.steps[q] += 1
                 err = np.abs(dN[r]).max() / max(1.0, np.abs(s.y[q]).max()) if ok[r] else np.inf
                 if ok[r] and err <= P.tol_accept:
+                    if P.predictor == 1 and s.accepts[q] >= 1:   # keep the point being replaced
+                        s.yprev[q], s.dEprev[q], s.tauprev[q] = s.yacc[q], s.dEacc[q], s.tauacc[q]
                     w = s.y[q] + dN[r]
                     nw = np.linalg.norm(w)
                     s.yacc[q] = w / nw
@@ -219,7 +240,7 @@ class ProjectiveSystem:
                         s.status[q] = UNDERFLOW
                         continue
                 h = min(s.dtau[q], -s.tauacc[q])
-                s.y[q] = s.yacc[q] + h * s.dEacc[q]
+                s.y[q] = _predict(P, s, q, h)
                 s.tau[q] = s.tauacc[q] + h
                 if s.steps[q] >= P.max_steps:
                     s.status[q] = MAX_STEPS
