@@ -132,6 +132,17 @@ typedef struct {
   double cond_max;      /* HPT_MIXED: pivot-ratio bound above which the solve is
                            redone in FP64, default 1e6 */
   double eps0;          /* tau0 = ln(eps0) / s_min (smallest positive e/D), default 1e-10 */
+  int32_t predictor;    /* 0 (default): Euler, y = y_acc + h dE_acc.  1: cubic Hermite, once a
+                           path has two accepted points (tau0, y0, d0), (tau1, y1, d1) (the state's
+                           *_prev arrays and y_acc, dE_acc): the cubic with those values and
+                           derivatives at tau0 and tau1, evaluated at tau1 + h (Section 2.3
+                           names it among the predictors built on the Euler direction).  In the
+                           projective form y0 and d0 are first multiplied by the unit phase that
+                           makes y1^* y0 real and positive.  A rejected cubic prediction is
+                           retried once with the Euler prediction at the same step size (the
+                           step shrinks only when an Euler prediction is rejected).  Needs the
+                           *_prev and hermite state arrays. */
+  int32_t pad_;
 } hpt_params;
 
 /* Structure-of-arrays path state (caller-owned device buffers, p paths).
@@ -148,6 +159,13 @@ typedef struct {
   int32_t* accepts;
   int32_t* rejects;
   int32_t* streak;    /* accepts in a row since the last growth or reject */
+  /* The accepted point before the last one (p x n complex, p doubles) and
+   * whether the pending prediction is a cubic Hermite one (p int32): read and
+   * written only with params->predictor == 1 (NULL otherwise). */
+  void* y_prev;
+  double* tau_prev;
+  void* dE_prev;
+  int32_t* hermite;
 } hpt_paths;
 
 /* Fills the defaults listed in hpt_params. */

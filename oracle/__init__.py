@@ -177,7 +177,7 @@ class System:
                          ctypes.c_int32(nsteps), _ptr(s.y), _ptr(s.tau), _ptr(s.dtau),
                          _ptr(s.yacc), _ptr(s.tauacc), _ptr(s.dEacc), _ptr(s.status),
                          _ptr(s.steps), _ptr(s.accepts), _ptr(s.rejects), _ptr(s.streak),
-                         _ptr(s.yprev), _ptr(s.tauprev), _ptr(s.dEprev))
+                         _ptr(s.yprev), _ptr(s.tauprev), _ptr(s.dEprev), _ptr(s.hflag))
         return state
 
     def track(self, params, y0, tau0):
@@ -243,6 +243,7 @@ class PathState:
     yprev: np.ndarray = None      # the accepted point before the last one (Hermite predictor)
     tauprev: np.ndarray = None
     dEprev: np.ndarray = None
+    hflag: np.ndarray = None      # 1 while the pending prediction is a cubic Hermite one
     p: int = field(init=False)
 
     def __post_init__(self):
@@ -251,6 +252,8 @@ class PathState:
             self.yprev = np.zeros_like(self.y)
             self.dEprev = np.zeros_like(self.y)
             self.tauprev = np.zeros(self.p)
+        if self.hflag is None:
+            self.hflag = np.zeros(self.p, np.int32)
 
     @classmethod
     def start(cls, y0, tau0, dtau0):
@@ -266,4 +269,4 @@ class PathState:
     def copy(self):
         return PathState(**{k: getattr(self, k).copy() for k in
                             ("y", "tau", "dtau", "yacc", "tauacc", "dEacc", "status", "steps",
-                             "accepts", "rejects", "streak", "yprev", "tauprev", "dEprev")})
+                             "accepts", "rejects", "streak", "yprev", "tauprev", "dEprev", "hflag")})

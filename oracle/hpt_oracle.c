@@ -216,6 +216,7 @@ typedef struct {
     cplx* y; double* tau; double* dtau; cplx* yacc; double* tauacc; cplx* dEacc;
     int32_t* status; int32_t* steps; int32_t* accepts; int32_t* rejects; int32_t* streak;
     cplx* yprev; double* tauprev; cplx* dEprev;   /* the accepted point before the last one */
+    int32_t* hflag;   /* 1 while the pending prediction is a cubic Hermite one */
 } ora_path;
 
 /* The prediction at tau_acc + h.  Euler (Section 2.3): y_acc + h dE_acc.
@@ -224,10 +225,14 @@ typedef struct {
  * p'(tau1) = d1 through the last two accepted points, evaluated at tau1 + h;
  * with s = (tau - tau0)/(tau1 - tau0) its basis is h00 = 2s^3 - 3s^2 + 1,
  * h10 = s^3 - 2s^2 + s, h01 = -2s^3 + 3s^2, h11 = s^3 - s^2 (the derivative
- * terms scaled by tau1 - tau0).  Used once two accepted points exist. */
-static void predict(int n, const ora_params* P, const ora_path* q, double h, cplx* out) {
+ * terms scaled by tau1 - tau0).  Used once two accepted points exist,
+ * except for the Euler retry of a rejected cubic prediction (cubic = 0);
+ * the flag records the choice. */
+static void predict(int n, const ora_params* P, const ora_path* q, double h, int cubic, cplx* out) {
     const double d = *q->tauacc - (q->tauprev ? *q->tauprev : 0.0);
-    if (P->predictor == 1 && *q->accepts >= 2 && d > 0.0) {
+    if (q->hflag) *q->hflag = 0;
+    if (cubic && P->predictor == 1 && *q->accepts >= 2 && d > 0.0) {
+        *q->hflag = 1;
         const double s = 1.0 + h / d, s2 = s * s, s3 = s2 * s;
         const double h00 = 2 * s3 - 3 * s2 + 1, h10 = s3 - 2 * s2 + s, h01 = -2 * s3 + 3 * s2, h11 = s3 - s2;
         for (int j = 0; j < n; ++j)
@@ -247,7 +252,7 @@ static void step_one(const ora_sys* s, const ora_params* P, ora_path* q) {
     cplx dE[ORA_NMAX], dN[ORA_NMAX];
     int bad = directions(s, q->y, *q->tau, dE, dN);
     *q->steps += 1;
-    int accept = 0;
+    int accept = 0, retry = 0;
     if (!bad) {
         double err = inf_norm(dN, n) / fmax(1.0, inf_norm(q->y, n));
         accept = err <= P->tol_accept;
@@ -280,11 +285,16 @@ static void step_one(const ora_sys* s, const ora_params* P, ora_path* q) {
             if (*q->steps >= P->max_steps) *q->status = ORA_MAX_STEPS;
             return;
         }
-        *q->dtau *= P->shrink;
-        if (*q->dtau < P->dtau_min) { *q->status = ORA_UNDERFLOW; return; }
+        /* a rejected cubic prediction is retried with Euler at the same step
+         * size; a rejected Euler prediction shrinks the step */
+        retry = P->predictor == 1 && q->hflag && *q->hflag;
+        if (!retry) {
+            *q->dtau *= P->shrink;
+            if (*q->dtau < P->dtau_min) { *q->status = ORA_UNDERFLOW; return; }
+        }
     }
     double h = fmin(*q->dtau, -*q->tauacc);
-    predict(n, P, q, h, q->y);
+    predict(n, P, q, h, !retry, q->y);
     *q->tau = *q->tauacc + h;
     if (*q->steps >= P->max_steps) *q->status = ORA_MAX_STEPS;
 }
@@ -374,13 +384,14 @@ int ora_directions(const ora_sys* s, int64_t p, const double* y, const double* t
 int ora_step(const ora_sys* s, const ora_params* P, int64_t p, int32_t nsteps,
              double* y, double* tau, double* dtau, double* yacc, double* tauacc,
              double* dEacc, int32_t* status, int32_t* steps, int32_t* accepts,
-             int32_t* rejects, int32_t* streak, double* yprev, double* tauprev, double* dEprev) {
+             int32_t* rejects, int32_t* streak, double* yprev, double* tauprev, double* dEprev,
+             int32_t* hflag) {
     const int n = s->n;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t q = 0; q < p; ++q) {
         ora_path st = {(cplx*)y + q * n, tau + q, dtau + q, (cplx*)yacc + q * n, tauacc + q,
                        (cplx*)dEacc + q * n, status + q, steps + q, accepts + q, rejects + q,
-                       streak + q, (cplx*)yprev + q * n, tauprev + q, (cplx*)dEprev + q * n};
+                       streak + q, (cplx*)yprev + q * n, tauprev + q, (cplx*)dEprev + q * n, hflag + q};
         for (int r = 0; r < nsteps; ++r) step_one(s, P, &st);
     }
     return 0;
@@ -396,12 +407,13 @@ int ora_track(const ora_sys* s, const ora_params* P, int64_t p, const double* y0
     for (int64_t q = 0; q < p; ++q) {
         cplx y[ORA_NMAX], yacc[ORA_NMAX], dEacc[ORA_NMAX], yprev[ORA_NMAX], dEprev[ORA_NMAX];
         double tau = tau0, dtau = P->dtau_init, tauacc = tau0, tauprev = tau0;
+        int32_t hflag = 0;
         int32_t st = ORA_ACTIVE, steps = 0, acc = 0, rej = 0, streak = 0;
         memcpy(y, (const cplx*)y0 + q * n, sizeof(cplx) * n);
         memcpy(yacc, y, sizeof(cplx) * n);
         for (int j = 0; j < n; ++j) dEacc[j] = 0.0;
         ora_path ps = {y, &tau, &dtau, yacc, &tauacc, dEacc, &st, &steps, &acc, &rej, &streak,
-                       yprev, &tauprev, dEprev};
+                       yprev, &tauprev, dEprev, &hflag};
         while (st == ORA_ACTIVE) step_one(s, P, &ps);
         double perr = NAN;
         if (st == ORA_CONVERGED) perr = polish_one(s, P, yacc);

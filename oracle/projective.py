@@ -120,15 +120,19 @@ def null_directions(J):
     return dE, dN, ok
 
 
-def _predict(P, s, q, h):
-    """Euler, or the cubic Hermite interpolant through the last two accepted
-    points (values and Euler directions) evaluated at tau_acc + h.  In
+def _predict(P, s, q, h, cubic):
+    """Euler, or (cubic set: not the Euler retry of a rejected cubic
+    prediction) the cubic Hermite interpolant through the last two accepted
+    points (values and Euler directions) evaluated at tau_acc + h; hflag
+    records the choice.  In
     homogeneous coordinates the corrector leaves a point's phase free (y and
     e^{i theta} y are one point), so the previous point and its direction are
     first turned into the phase of the last one (y_acc^* y_prev real and
     positive); otherwise the extrapolation amplifies phase differences."""
     d = s.tauacc[q] - s.tauprev[q]
-    if P.predictor == 1 and s.accepts[q] >= 2 and d > 0:
+    s.hflag[q] = 0
+    if cubic and P.predictor == 1 and s.accepts[q] >= 2 and d > 0:
+        s.hflag[q] = 1
         t = 1.0 + h / d
         h00, h10 = 2 * t**3 - 3 * t**2 + 1, t**3 - 2 * t**2 + t
         h01, h11 = -2 * t**3 + 3 * t**2, t**3 - t**2
@@ -200,7 +204,8 @@ class ProjectiveSystem:
             for r, q in enumerate(act):
                 s.steps[q] += 1
                 err = np.abs(dN[r]).max() / max(1.0, np.abs(s.y[q]).max()) if ok[r] else np.inf
-                if ok[r] and err <= P.tol_accept:
+                accepted = bool(ok[r] and err <= P.tol_accept)
+                if accepted:
                     if P.predictor == 1 and s.accepts[q] >= 1:   # keep the point being replaced
                         s.yprev[q], s.dEprev[q], s.tauprev[q] = s.yacc[q], s.dEacc[q], s.tauacc[q]
                     w = s.y[q] + dN[r]
@@ -235,12 +240,16 @@ class ProjectiveSystem:
                         if s.steps[q] >= P.max_steps:
                             s.status[q] = MAX_STEPS
                         continue
-                    s.dtau[q] *= P.shrink
-                    if s.dtau[q] < P.dtau_min:
-                        s.status[q] = UNDERFLOW
-                        continue
+                    # a rejected cubic prediction is retried with Euler at the
+                    # same step size; a rejected Euler prediction shrinks the step
+                    retry = P.predictor == 1 and bool(s.hflag[q])
+                    if not retry:
+                        s.dtau[q] *= P.shrink
+                        if s.dtau[q] < P.dtau_min:
+                            s.status[q] = UNDERFLOW
+                            continue
                 h = min(s.dtau[q], -s.tauacc[q])
-                s.y[q] = _predict(P, s, q, h)
+                s.y[q] = _predict(P, s, q, h, accepted or not retry)
                 s.tau[q] = s.tauacc[q] + h
                 if s.steps[q] >= P.max_steps:
                     s.status[q] = MAX_STEPS

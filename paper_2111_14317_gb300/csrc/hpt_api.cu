@@ -29,6 +29,10 @@ hpt_paths offset_paths(const hpt_paths& S, int64_t q0, int n, size_t cs) {
   o.accepts = S.accepts + q0;
   o.rejects = S.rejects + q0;
   o.streak = S.streak + q0;
+  if (S.y_prev) o.y_prev = (char*)S.y_prev + q0 * n * cs;
+  if (S.dE_prev) o.dE_prev = (char*)S.dE_prev + q0 * n * cs;
+  if (S.tau_prev) o.tau_prev = S.tau_prev + q0;
+  if (S.hermite) o.hermite = S.hermite + q0;
   return o;
 }
 
@@ -115,8 +119,21 @@ hpt_status check_params(const hpt_params* prm) {
   if (!(prm->tol_accept > 0) || !(prm->dtau_init > 0) || !(prm->dtau_min > 0) ||
       !(prm->dtau_max >= prm->dtau_min) || !(prm->grow >= 1) || !(prm->shrink > 0 && prm->shrink < 1) ||
       prm->grow_after < 1 || prm->max_steps < 1 || !(prm->div_bound > 1) || !(prm->polish_tol > 0) ||
-      prm->polish_iters < 0) {
+      prm->polish_iters < 0 || (prm->predictor != 0 && prm->predictor != 1)) {
     set_error("params out of range");
+    return HPT_EINVAL;
+  }
+  return HPT_OK;
+}
+
+hpt_status check_state(const hpt_paths* S, const hpt_params* prm) {
+  if (!S->y || !S->y_acc || !S->dE_acc || !S->tau || !S->dtau || !S->tau_acc || !S->status ||
+      !S->steps || !S->accepts || !S->rejects || !S->streak) {
+    set_error("NULL pointer in the path state");
+    return HPT_EINVAL;
+  }
+  if (prm->predictor == 1 && (!S->y_prev || !S->dE_prev || !S->tau_prev || !S->hermite)) {
+    set_error("the Hermite predictor needs y_prev, dE_prev, tau_prev and hermite in the path state");
     return HPT_EINVAL;
   }
   return HPT_OK;
@@ -170,11 +187,8 @@ hpt_status hpt_paths_init(hpt_system s, int64_t p, const void* y0, const hpt_par
   if ((rc = check_params(prm))) return rc;
   if (p < 0 || !S) { set_error("bad p or state"); return HPT_EINVAL; }
   if (p == 0) return HPT_OK;
-  if (!y0 || !S->y || !S->y_acc || !S->dE_acc || !S->tau || !S->dtau || !S->tau_acc ||
-      !S->status || !S->steps || !S->accepts || !S->rejects || !S->streak) {
-    set_error("NULL pointer in the path state");
-    return HPT_EINVAL;
-  }
+  if (!y0) { set_error("y0 is NULL"); return HPT_EINVAL; }
+  if ((rc = check_state(S, prm))) return rc;
   double tau0 = 0;
   hpt_get_info(s, nullptr, nullptr, nullptr, prm->eps0, &tau0);
   cudaError_t e = s->proj ? launch_paths_init_proj(s, p, y0, tau0, *prm, *S, (cudaStream_t)stream)
@@ -190,11 +204,7 @@ hpt_status hpt_step(hpt_system s, int64_t p, const hpt_paths* S, int32_t nsteps,
   if ((rc = check_params(prm))) return rc;
   if (p < 0 || !S || nsteps < 0) { set_error("bad p, state or nsteps"); return HPT_EINVAL; }
   if (p == 0 || nsteps == 0) return HPT_OK;
-  if (!S->y || !S->y_acc || !S->dE_acc || !S->tau || !S->dtau || !S->tau_acc || !S->status ||
-      !S->steps || !S->accepts || !S->rejects || !S->streak) {
-    set_error("NULL pointer in the path state");
-    return HPT_EINVAL;
-  }
+  if ((rc = check_state(S, prm))) return rc;
   return step_impl(s, p, *S, nsteps, *prm, (cudaStream_t)stream);
 }
 
@@ -228,6 +238,7 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
     return o;
   };
   const size_t o_y = take(p * n * cs), o_ya = take(p * n * cs), o_de = take(p * n * cs);
+  const size_t o_yp = take(p * n * cs), o_dp = take(p * n * cs), o_tp = take(p * 8), o_hf = take(p * 4);
   const size_t o_tau = take(p * 8), o_dt = take(p * 8), o_ta = take(p * 8);
   const size_t o_st = take(p * 4), o_sp = take(p * 4), o_ac = take(p * 4), o_rj = take(p * 4),
                o_sk = take(p * 4), o_done = take(p * 4), o_last = take(p * 4), o_cnt = take(4);
@@ -245,6 +256,10 @@ hpt_status hpt_track(hpt_system s, int64_t p, const void* y0, const hpt_params* 
   S.accepts = (int32_t*)(b + o_ac);
   S.rejects = (int32_t*)(b + o_rj);
   S.streak = (int32_t*)(b + o_sk);
+  S.y_prev = b + o_yp;
+  S.dE_prev = b + o_dp;
+  S.tau_prev = (double*)(b + o_tp);
+  S.hermite = (int32_t*)(b + o_hf);
   int32_t* done = (int32_t*)(b + o_done);
   float* last = (float*)(b + o_last);
   int32_t* cnt = (int32_t*)(b + o_cnt);

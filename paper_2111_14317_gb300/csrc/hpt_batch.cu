@@ -176,8 +176,8 @@ struct Problem {
   int64_t cap_bucket[kBuckets] = {0, 0, 0, 0};
   int64_t pmax = 0;              // largest paths[s]
   // byte offsets in d_state
-  size_t o_y, o_ya, o_de, o_tau, o_dt, o_ta, o_st, o_sp, o_ac, o_rj, o_sk, o_done, o_last, o_vofs, o_pb, o_np, o_tmp,
-      o_cnt, o_tb, o_list, o_tsys, o_ctl, o_rc, o_rl, o_ext, total;
+  size_t o_y, o_ya, o_de, o_yp, o_dp, o_tp, o_hf, o_tau, o_dt, o_ta, o_st, o_sp, o_ac, o_rj, o_sk, o_done, o_last, o_vofs,
+      o_pb, o_np, o_tmp, o_cnt, o_tb, o_list, o_tsys, o_ctl, o_rc, o_rl, o_ext, total;
 };
 
 Problem plan(const hpt_batch_s* b, const int64_t* paths) {
@@ -204,6 +204,10 @@ Problem plan(const hpt_batch_s* b, const int64_t* paths) {
   q.o_y = take(V * 8);
   q.o_ya = take(V * 8);
   q.o_de = take(V * 8);
+  q.o_yp = take(V * 8);   // the accepted point before the last one (Hermite predictor)
+  q.o_dp = take(V * 8);
+  q.o_tp = take(P * 8);
+  q.o_hf = take(P * 4);
   q.o_tau = take(P * 8);
   q.o_dt = take(P * 8);
   q.o_ta = take(P * 8);
@@ -246,6 +250,10 @@ hpt_paths state_of(const hpt_batch_s* b, const Problem& q) {
   S.accepts = (int32_t*)(d + q.o_ac);
   S.rejects = (int32_t*)(d + q.o_rj);
   S.streak = (int32_t*)(d + q.o_sk);
+  S.y_prev = d + q.o_yp;
+  S.dE_prev = d + q.o_dp;
+  S.tau_prev = (double*)(d + q.o_tp);
+  S.hermite = (int32_t*)(d + q.o_hf);
   return S;
 }
 
@@ -263,6 +271,10 @@ hpt_paths sub_state(const hpt_paths& S, int64_t pb, int64_t vb) {
   o.accepts = S.accepts + pb;
   o.rejects = S.rejects + pb;
   o.streak = S.streak + pb;
+  o.y_prev = (char*)S.y_prev + vb * 8;
+  o.dE_prev = (char*)S.dE_prev + vb * 8;
+  o.tau_prev = S.tau_prev + pb;
+  o.hermite = S.hermite + pb;
   return o;
 }
 

@@ -468,6 +468,8 @@ void hpt_default_params(hpt_params* o) {
   o->check_every = 32;
   o->cond_max = 1e6;
   o->eps0 = 1e-10;
+  o->predictor = 0;
+  o->pad_ = 0;
 }
 
 const char* hpt_status_string(hpt_status s) {

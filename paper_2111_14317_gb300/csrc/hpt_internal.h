@@ -252,6 +252,9 @@ cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void*
 hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
                         void* ext, int64_t chunk, cudaStream_t st);
 hpt_status check_params(const hpt_params* prm);
+// Every array of the state present (and the *_prev arrays for the Hermite
+// predictor).
+hpt_status check_state(const hpt_paths* S, const hpt_params* prm);
 hpt_status cuda_fail(cudaError_t e, const char* what);
 
 // State init / conversion helpers.

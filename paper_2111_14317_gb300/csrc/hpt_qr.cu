@@ -299,8 +299,9 @@ __device__ __forceinline__ bool qr_null(int nv, cx<T> (&a)[R][CM], cx<T> (&wE)[R
 }
 
 // Step control of one projective path (all lanes of its group), given the
-// directions in y coordinates: the affine rule with the point scaled back to
-// unit norm after every correction and divergence judged on y_j / y_n.
+// directions in y coordinates: the affine rule (and predictor choice) with
+// the point scaled back to unit norm after every correction and divergence
+// judged on y_j / y_n.
 template <typename T, int G, int R>
 __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t vbase, int32_t status, bool ok,
                                             const cx<T> (&xE)[R], const cx<T> (&xN)[R], const hpt_paths& S,
@@ -345,17 +346,24 @@ __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t 
     for (int o = G / 2; o > 0; o >>= 1) s2 += __shfl_xor_sync(gmask, s2, o, G);
     return T(1) / t_sqrt(s2);
   };
-  bool predict = true;
+  const bool herm = prm.predictor == 1;
+  bool predict = true, keep_prev = false, retry = false;
+  cx<T> yp[R], dp[R];   // the accepted point before the last one (Hermite predictor)
+  double taup = 0.0;
   if (accept) {
+    keep_prev = herm && accepts >= 1;
     cx<T> w[R];
 #pragma unroll
     for (int s = 0; s < R; ++s) w[s] = mk<T>(y[s].x + xN[s].x, y[s].y + xN[s].y);
     const T inv = unit(w);
 #pragma unroll
     for (int s = 0; s < R; ++s) {
+      yp[s] = yacc[s];
+      dp[s] = dEacc[s];
       yacc[s] = cscale(w[s], inv);
       dEacc[s] = cscale(xE[s], inv);
     }
+    taup = tauacc;
     tauacc = tau;
     accepts += 1;
     streak += 1;
@@ -404,19 +412,67 @@ __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t 
         if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
       }
     } else {
-      dtau *= prm.shrink;
-      if (dtau < prm.dtau_min) {
-        status = HPT_PATH_UNDERFLOW;
-        predict = false;
+      // a rejected cubic prediction is retried with Euler at the same step
+      // size; a rejected Euler prediction shrinks the step
+      retry = herm && S.hermite[path] != 0;
+      if (!retry) {
+        dtau *= prm.shrink;
+        if (dtau < prm.dtau_min) {
+          status = HPT_PATH_UNDERFLOW;
+          predict = false;
+        }
       }
     }
   }
   if (predict) {
     const double h = fmin(dtau, -tauacc);
+    bool cubic = false;
+    if (herm && !retry && accepts >= 2) {
+      if (!keep_prev) {   // a rejected step: the previous point from the state
 #pragma unroll
-    for (int s = 0; s < R; ++s) y[s] = mk<T>(yacc[s].x + (T)h * dEacc[s].x, yacc[s].y + (T)h * dEacc[s].y);
+        for (int s = 0; s < R; ++s) {
+          const bool mine = lane + G * s < nv;
+          yp[s] = mine ? ld<T>(S.y_prev, vbase + lane + G * s) : mk<T>(0, 0);
+          dp[s] = mine ? ld<T>(S.dE_prev, vbase + lane + G * s) : mk<T>(0, 0);
+        }
+        taup = S.tau_prev[path];
+      }
+      cubic = tauacc - taup > 0.0;
+    }
+    if (cubic) {
+      // the previous point turned into the phase of the last (y_acc^* y_prev
+      // real and positive): the corrector leaves a homogeneous point's phase
+      // free, and the extrapolation would amplify phase differences
+      cx<T> dot = mk<T>(0, 0);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        dot.x += yacc[s].x * yp[s].x + yacc[s].y * yp[s].y;
+        dot.y += yacc[s].x * yp[s].y - yacc[s].y * yp[s].x;
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) {
+        dot.x += __shfl_xor_sync(gmask, dot.x, o, G);
+        dot.y += __shfl_xor_sync(gmask, dot.y, o, G);
+      }
+      const T md = t_sqrt(abs2(dot));
+      const cx<T> ph = md > T(0) ? mk<T>(dot.x / md, -dot.y / md) : mk<T>(T(1), T(0));
+      // cubic Hermite through (taup, yp, dp) and (tauacc, yacc, dEacc) at tauacc + h
+      const double d = tauacc - taup, u = 1.0 + h / d, u2 = u * u, u3 = u2 * u;
+      const T h00 = (T)(2 * u3 - 3 * u2 + 1), h10 = (T)((u3 - 2 * u2 + u) * d);
+      const T h01 = (T)(-2 * u3 + 3 * u2), h11 = (T)((u3 - u2) * d);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        const cx<T> a0 = cmul(yp[s], ph), a1 = cmul(dp[s], ph);
+        y[s] = mk<T>(h00 * a0.x + h10 * a1.x + h01 * yacc[s].x + h11 * dEacc[s].x,
+                     h00 * a0.y + h10 * a1.y + h01 * yacc[s].y + h11 * dEacc[s].y);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < R; ++s) y[s] = mk<T>(yacc[s].x + (T)h * dEacc[s].x, yacc[s].y + (T)h * dEacc[s].y);
+    }
     tau = tauacc + h;
     if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
+    if (herm && lane == 0) S.hermite[path] = cubic ? 1 : 0;
   }
 #pragma unroll
   for (int s = 0; s < R; ++s) {
@@ -425,8 +481,13 @@ __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t 
       st<T>(S.y, vbase + j, y[s]);
       st<T>(S.y_acc, vbase + j, yacc[s]);
       st<T>(S.dE_acc, vbase + j, dEacc[s]);
+      if (keep_prev) {
+        st<T>(S.y_prev, vbase + j, yp[s]);
+        st<T>(S.dE_prev, vbase + j, dp[s]);
+      }
     }
   }
+  if (keep_prev && lane == 0) S.tau_prev[path] = taup;
   if (lane == 0) {
     S.tau[path] = tau;
     S.dtau[path] = dtau;
@@ -500,7 +561,13 @@ __global__ void paths_init_proj_kernel(int n, int64_t p, const double2* __restri
     st<T>(S.y, (size_t)i * nv + j, c);
     st<T>(S.y_acc, (size_t)i * nv + j, c);
     st<T>(S.dE_acc, (size_t)i * nv + j, mk<T>(0, 0));
+    if (S.y_prev) {
+      st<T>(S.y_prev, (size_t)i * nv + j, mk<T>(0, 0));
+      st<T>(S.dE_prev, (size_t)i * nv + j, mk<T>(0, 0));
+    }
   }
+  if (S.tau_prev) S.tau_prev[i] = tau0;
+  if (S.hermite) S.hermite[i] = 0;
   S.tau[i] = tau0;
   S.tau_acc[i] = tau0;
   S.dtau[i] = dtau0;

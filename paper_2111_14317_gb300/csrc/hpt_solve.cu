@@ -321,8 +321,10 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
 }
 
 // Step control of one path (all lanes of its group), given the directions:
-// accept/reject, then the next prediction.  TS is the state precision; lane l
-// handles the variables l + G s.
+// accept/reject, then the next prediction (Euler, or with prm.predictor = 1
+// and two accepted points the cubic Hermite interpolant through them; the
+// point being replaced by an accept is kept in the state's *_prev arrays).
+// TS is the state precision; lane l handles the variables l + G s.
 template <typename TS, int G, int R>
 __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, int32_t status, bool ok,
                                             const cx<TS> (&wE)[R], const cx<TS> (&wN)[R], const hpt_paths& S,
@@ -362,13 +364,20 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
           streak = S.streak[path];
   const TS err = nd / t_max(TS(1), ny);
   const bool accept = !bad && err <= (TS)prm.tol_accept;
-  bool predict = true;
+  const bool herm = prm.predictor == 1;
+  bool predict = true, keep_prev = false, retry = false;
+  cx<TS> yp[R], dp[R];   // the accepted point before the last one (Hermite predictor)
+  double taup = 0.0;
   if (accept) {
+    keep_prev = herm && accepts >= 1;
 #pragma unroll
     for (int s = 0; s < R; ++s) {
+      yp[s] = yacc[s];
+      dp[s] = dEacc[s];
       yacc[s] = mk<TS>(y[s].x + xN[s].x, y[s].y + xN[s].y);
       dEacc[s] = xE[s];
     }
+    taup = tauacc;
     tauacc = tau;
     accepts += 1;
     streak += 1;
@@ -409,19 +418,49 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
         if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
       }
     } else {
-      dtau *= prm.shrink;
-      if (dtau < prm.dtau_min) {
-        status = HPT_PATH_UNDERFLOW;
-        predict = false;
+      // a rejected cubic prediction is retried with Euler at the same step
+      // size; a rejected Euler prediction shrinks the step
+      retry = herm && S.hermite[path] != 0;
+      if (!retry) {
+        dtau *= prm.shrink;
+        if (dtau < prm.dtau_min) {
+          status = HPT_PATH_UNDERFLOW;
+          predict = false;
+        }
       }
     }
   }
   if (predict) {
     const double h = fmin(dtau, -tauacc);
+    bool cubic = false;
+    if (herm && !retry && accepts >= 2) {
+      if (!keep_prev) {   // a rejected step: the previous point from the state
 #pragma unroll
-    for (int s = 0; s < R; ++s) y[s] = mk<TS>(yacc[s].x + (TS)h * dEacc[s].x, yacc[s].y + (TS)h * dEacc[s].y);
+        for (int s = 0; s < R; ++s) {
+          const bool mine = lane + G * s < n;
+          yp[s] = mine ? ld<TS>(S.y_prev, vbase + lane + G * s) : mk<TS>(0, 0);
+          dp[s] = mine ? ld<TS>(S.dE_prev, vbase + lane + G * s) : mk<TS>(0, 0);
+        }
+        taup = S.tau_prev[path];
+      }
+      cubic = tauacc - taup > 0.0;
+    }
+    if (cubic) {
+      // cubic Hermite through (taup, yp, dp) and (tauacc, yacc, dEacc) at tauacc + h
+      const double d = tauacc - taup, u = 1.0 + h / d, u2 = u * u, u3 = u2 * u;
+      const TS h00 = (TS)(2 * u3 - 3 * u2 + 1), h10 = (TS)((u3 - 2 * u2 + u) * d);
+      const TS h01 = (TS)(-2 * u3 + 3 * u2), h11 = (TS)((u3 - u2) * d);
+#pragma unroll
+      for (int s = 0; s < R; ++s)
+        y[s] = mk<TS>(h00 * yp[s].x + h10 * dp[s].x + h01 * yacc[s].x + h11 * dEacc[s].x,
+                      h00 * yp[s].y + h10 * dp[s].y + h01 * yacc[s].y + h11 * dEacc[s].y);
+    } else {
+#pragma unroll
+      for (int s = 0; s < R; ++s) y[s] = mk<TS>(yacc[s].x + (TS)h * dEacc[s].x, yacc[s].y + (TS)h * dEacc[s].y);
+    }
     tau = tauacc + h;
     if (steps >= prm.max_steps) status = HPT_PATH_MAX_STEPS;
+    if (herm && lane == 0) S.hermite[path] = cubic ? 1 : 0;
   }
 #pragma unroll
   for (int s = 0; s < R; ++s) {
@@ -431,8 +470,13 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
       st<TS>(S.y, vi, y[s]);
       st<TS>(S.y_acc, vi, yacc[s]);
       st<TS>(S.dE_acc, vi, dEacc[s]);
+      if (keep_prev) {
+        st<TS>(S.y_prev, vi, yp[s]);
+        st<TS>(S.dE_prev, vi, dp[s]);
+      }
     }
   }
+  if (keep_prev && lane == 0) S.tau_prev[path] = taup;
   if (lane == 0) {
     S.tau[path] = tau;
     S.dtau[path] = dtau;
@@ -773,8 +817,14 @@ __global__ void paths_init_kernel(int n, int64_t p, const double2* __restrict__ 
     st<T>(S.y, i, c);
     st<T>(S.y_acc, i, c);
     st<T>(S.dE_acc, i, mk<T>(0, 0));
+    if (S.y_prev) {
+      st<T>(S.y_prev, i, mk<T>(0, 0));
+      st<T>(S.dE_prev, i, mk<T>(0, 0));
+    }
   }
   if (i < p) {
+    if (S.tau_prev) S.tau_prev[i] = tau0;
+    if (S.hermite) S.hermite[i] = 0;
     S.tau[i] = tau0;
     S.tau_acc[i] = tau0;
     S.dtau[i] = dtau0;

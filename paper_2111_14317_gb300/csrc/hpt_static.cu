@@ -73,16 +73,9 @@ extern "C" hpt_status hpt_step_static(hpt_system s, int64_t p, const hpt_paths* 
     return HPT_ERANGE;
   }
   if (p == 0 || nsteps == 0) return HPT_OK;
-  if (!S->y || !S->y_acc || !S->dE_acc || !S->tau || !S->dtau || !S->tau_acc || !S->status ||
-      !S->steps || !S->accepts || !S->rejects || !S->streak) {
-    set_error("NULL pointer in the path state");
-    return HPT_EINVAL;
-  }
-  if (!(prm->tol_accept > 0) || !(prm->dtau_min > 0) || !(prm->shrink > 0 && prm->shrink < 1) ||
-      prm->grow_after < 1 || prm->max_steps < 1 || !(prm->div_bound > 1)) {
-    set_error("params out of range");
-    return HPT_EINVAL;
-  }
+  hpt_status rc0 = check_params(prm);
+  if (rc0 == HPT_OK) rc0 = check_state(S, prm);
+  if (rc0) return rc0;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device) {
     set_error("the handle belongs to device %d, current device is %d", s->device, dev);

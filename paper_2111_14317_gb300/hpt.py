@@ -57,7 +57,8 @@ class Params(ctypes.Structure):
                 ("grow_after", ctypes.c_int32), ("max_steps", ctypes.c_int32),
                 ("div_bound", ctypes.c_double), ("polish_tol", ctypes.c_double),
                 ("polish_iters", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("cond_max", ctypes.c_double), ("eps0", ctypes.c_double)]
+                ("cond_max", ctypes.c_double), ("eps0", ctypes.c_double),
+                ("predictor", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
     def __init__(self, **kw):
         super().__init__()
@@ -69,7 +70,7 @@ class Params(ctypes.Structure):
 class _Paths(ctypes.Structure):
     _fields_ = [(f, ctypes.c_void_p) for f in
                 ("y", "tau", "dtau", "y_acc", "tau_acc", "dE_acc", "status", "steps", "accepts",
-                 "rejects", "streak")]
+                 "rejects", "streak", "y_prev", "tau_prev", "dE_prev", "hermite")]
 
 
 class Tuning(ctypes.Structure):
@@ -215,18 +216,24 @@ class PathState:
     """Caller-owned structure-of-arrays path state on a device (or in pinned
     host memory with device="cpu", pin=True): every field is a view into one
     contiguous byte arena, so the whole state moves between host and device
-    in one copy (`arena`)."""
+    in one copy (`arena`).  hermite=True adds the previous accepted point
+    (y_prev, tau_prev, dE_prev) and the pending-prediction flag (hermite)
+    that the cubic Hermite predictor needs."""
 
-    FIELDS = ("y", "tau", "dtau", "y_acc", "tau_acc", "dE_acc", "status", "steps", "accepts",
-              "rejects", "streak")
+    BASE = ("y", "tau", "dtau", "y_acc", "tau_acc", "dE_acc", "status", "steps", "accepts",
+            "rejects", "streak")
+    PREV = ("y_prev", "tau_prev", "dE_prev", "hermite")
 
-    def __init__(self, p, n, precision, device="cuda", pin=False):
+    def __init__(self, p, n, precision, device="cuda", pin=False, hermite=False):
         cdt = torch.complex128 if precision == HPT_FP64 else torch.complex64
         self.p, self.n, self.precision = p, n, precision
+        self.FIELDS = self.BASE + (self.PREV if hermite else ())
         shapes = {"y": ((p, n), cdt), "y_acc": ((p, n), cdt), "dE_acc": ((p, n), cdt),
                   "tau": ((p,), torch.float64), "dtau": ((p,), torch.float64), "tau_acc": ((p,), torch.float64),
                   "status": ((p,), torch.int32), "steps": ((p,), torch.int32), "accepts": ((p,), torch.int32),
-                  "rejects": ((p,), torch.int32), "streak": ((p,), torch.int32)}
+                  "rejects": ((p,), torch.int32), "streak": ((p,), torch.int32),
+                  "y_prev": ((p, n), cdt), "tau_prev": ((p,), torch.float64), "dE_prev": ((p, n), cdt),
+                  "hermite": ((p,), torch.int32)}
         offs, off = {}, 0
         for k in self.FIELDS:
             shp, dt = shapes[k]
@@ -242,7 +249,8 @@ class PathState:
             setattr(self, k, self.arena[o:o + nb].view(dt).view(*shp))
 
     def _c(self):
-        return _Paths(*[getattr(self, k).data_ptr() for k in self.FIELDS])
+        return _Paths(*[getattr(self, k).data_ptr() if hasattr(self, k) else None
+                        for k in self.BASE + self.PREV])
 
     def to_host(self):
         return {k: getattr(self, k).cpu() for k in self.FIELDS}
@@ -287,9 +295,9 @@ class System:
         o.nv, o.projective, o.degrees = int(nv.value), bool(pj.value), deg
         return o
 
-    def new_state(self, p, device="cuda", pin=False):
+    def new_state(self, p, device="cuda", pin=False, hermite=False):
         """A PathState for p paths of this system (nv entries per path)."""
-        return PathState(p, self.nv, self.precision, device=device, pin=pin)
+        return PathState(p, self.nv, self.precision, device=device, pin=pin, hermite=hermite)
 
     def close(self):
         if getattr(self, "_h", None):
