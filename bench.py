@@ -269,6 +269,7 @@ def run_gpu(args):
     if args.workload == "all":
         out["track_adjoint"] = run_track_adjoint(args, dev)
         out["projective"] = run_projective(args, dev)
+        out["paper_shapes"] = run_paper_shapes(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     return out, ws, rank
@@ -321,6 +322,22 @@ def run_batch(args, dev):
             torch.cuda.synchronize()
             ms.append((time.perf_counter() - t0) * 1e3)
     stats = b.stats()
+    # the same track with the cubic Hermite predictor at tol_accept 1e-3 (the
+    # tolerance the predictor is used with), and the Euler predictor at 1e-3
+    # for a like-for-like step count
+    pred = {}
+    for name, kw in (("euler_tol1e-3", dict(predictor=0)), ("hermite_tol1e-3", dict(predictor=1))):
+        prm_p = hpt.Params(tol_accept=1e-3, **kw)
+        b.track(y0, paths, prm_p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st_p, sp_p = b.track(y0, paths, prm_p)
+        torch.cuda.synchronize()
+        ms_p = (time.perf_counter() - t0) * 1e3
+        st_n_p, sp_n_p = st_p.cpu().numpy(), sp_p.cpu().numpy()
+        pred[name] = {"ms_per_track": ms_p, "path_steps": int(sp_n_p.sum()),
+                      "converged": int((st_n_p == hpt.CONVERGED).sum()),
+                      "paths_per_s": nsys * npaths / (ms_p * 1e-3)}
     # end to end: pinned host start points in, solutions and statuses out
     pinned = y0_host.pin_memory()
     x_host = torch.empty_like(y0_host).pin_memory()
@@ -359,6 +376,7 @@ def run_batch(args, dev):
         "steps_per_path": {"min": int(conv.min()) if conv.size else None,
                            "median": float(np.median(conv)) if conv.size else None,
                            "max": int(conv.max()) if conv.size else None},
+        "predictors": pred,
         "setup_s": setup_s, "clocks": clk.summary(),
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"],
                      "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops_sustained"],
@@ -516,6 +534,68 @@ def run_projective(args, dev):
     return out
 
 
+PAPER_SHAPES = {
+    # stand-ins for the paper's Table 1 (cyclic-14: 14 equations, 184 monomials)
+    # and Table 2 (chandra-24: 24 equations, 324 monomials); the systems
+    # themselves are not available, only their shapes are matched
+    "n14_m184": (14, 184, (10, 50, 250, 500, 1000), {10: 0.0222, 50: 0.0274, 250: 0.0296, 500: 0.0313, 1000: 0.0355}),
+    "n24_m324": (24, 324, (250, 500, 1000), {250: 0.0728, 500: 0.0757, 1000: 0.0852}),
+}
+
+
+def run_paper_shapes(args, dev):
+    """The protocol of the paper's Tables 1-2 on synthetic systems of the same
+    shapes: 100 consecutive Euler-Newton steps (one hpt_step call with
+    nsteps = 100) on p paths, wall-clock time with the start points copied
+    from pinned host memory and the accepted points copied back inside the
+    timed region (median of 3 runs), plus the device time of the steps."""
+    import torch
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+    out = {"protocol": "100 consecutive Euler-Newton steps per call on p paths of a planted cell (start "
+                       "points exp(V^-1(log b + 2 pi i j e_1))); wall = H2D of the start points + init + "
+                       "100 steps + D2H of y_acc, median of 3; paper_v100_s = the paper's V100 column "
+                       "(other hardware, other systems of the same shape: context only)"}
+    for name, (n, M, ps, paper) in PAPER_SHAPES.items():
+        s, pairs = W.paper_shape(n, M)
+        rec = {"n": n, "monomials": M, "paper_v100_s": {str(k): v for k, v in paper.items()}}
+        pmax = max(ps)
+        ks = np.zeros((pmax, n), np.int64)
+        ks[:, 0] = np.arange(pmax)
+        x0_all = hpt.binomial_points(n, s.m, s.exponents, s.coeffs, pairs, ks)
+        for form, prec in (("mixed", hpt.HPT_MIXED), ("fp64", hpt.HPT_FP64)):
+            h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": pairs}, prec)
+            prm = hpt.Params(tol_accept=3e-3 if prec == hpt.HPT_MIXED else 1e-3)
+            res = {}
+            for p in ps:
+                host = torch.from_numpy(np.ascontiguousarray(x0_all[:p])).pin_memory()
+                st = hpt.PathState(p, n, prec, device=dev)
+                back = torch.empty(st.y_acc.shape, dtype=st.y_acc.dtype).pin_memory()
+                walls, devs = [], []
+                for rep in range(4):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    x0 = host.to(dev, non_blocking=True)
+                    h.paths_init(st, x0, prm)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    h.step(st, 100, prm)
+                    e1.record()
+                    back.copy_(st.y_acc, non_blocking=True)
+                    torch.cuda.synchronize()
+                    if rep:   # the first run warms up
+                        walls.append(time.perf_counter() - t0)
+                        devs.append(e0.elapsed_time(e1) * 1e-3)
+                active = int((st.status == hpt.ACTIVE).sum().item())
+                done = int(st.steps.sum().item())
+                res[str(p)] = {"wall_s": statistics.median(walls), "device_s": statistics.median(devs),
+                               "path_steps": done, "active_after": active}
+            rec[form] = res
+            h.close()
+        out[name] = rec
+    return out
+
+
 def cpu_baseline(seconds=12.0, max_paths=PATHS):
     """Times the oracle's step (as it stands) on growing slices of the same
     workload until about `seconds` of work is done."""
@@ -555,7 +635,7 @@ def main():
     ap.add_argument("--batch-paths", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default tuning")
-    ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective"],
+    ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective", "paper_shapes"],
                     help="step: the n=16 hpt_step line only; batch: the many-systems batch only; "
                          "projective: the projective-form step only (the last two print their own JSON "
                          "object, for profiling)")
@@ -590,6 +670,13 @@ def main():
         hbuild.build()
         torch.cuda.set_device(0)
         print(json.dumps({"batch": run_batch(args, torch.device("cuda", 0))}))
+        return
+    if args.workload == "paper_shapes":
+        import torch
+        from paper_2111_14317_gb300 import build as hbuild
+        hbuild.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"paper_shapes": run_paper_shapes(args, torch.device("cuda", 0))}))
         return
     if args.workload == "projective":
         import torch
@@ -663,6 +750,8 @@ def main():
         line["track_adjoint"] = out["track_adjoint"]
     if "projective" in out:
         line["projective"] = out["projective"]
+    if "paper_shapes" in out:
+        line["paper_shapes"] = out["paper_shapes"]
     print(json.dumps(line))
 
 

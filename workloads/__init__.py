@@ -44,6 +44,7 @@ __all__ = [
     "config3",
     "config4_system",
     "config5",
+    "paper_shape",
 ]
 
 
@@ -195,6 +196,18 @@ def config4_system(index, attempt=0):
     m = [int(v) for v in rng.integers(n + 1, 4 * n + 1, size=n)]
     sysm = laurent_system(1000 + index, n, m, -3, 3, 0, attempt=attempt)
     lift, pairs = planted_lifting(2000 + index, m, 16, attempt=attempt)
+    return sysm.with_lifting(lift), pairs
+
+
+def paper_shape(n, total_m, attempt=0):
+    """A stand-in of the paper's test-system shapes (Section 8, Tables 1-2:
+    n equations and `total_m` monomials in all, about total_m / n per
+    equation, no monomial shared between equations): exponents in [-2,2]
+    with 4 nonzeros, coefficients e^{i theta}, planted-cell lifting.
+    Returns (system, pairs)."""
+    m = [total_m // n + (1 if k < total_m % n else 0) for k in range(n)]
+    sysm = laurent_system(7000 + n, n, m, -2, 2, 0, nnz=min(4, n), attempt=attempt)
+    lift, pairs = planted_lifting(7100 + n, m, 16, attempt=attempt)
     return sysm.with_lifting(lift), pairs
 
 
