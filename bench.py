@@ -270,6 +270,7 @@ def run_gpu(args):
         out["track_adjoint"] = run_track_adjoint(args, dev)
         out["projective"] = run_projective(args, dev)
         out["paper_shapes"] = run_paper_shapes(args, dev)
+        out["start_points"] = run_start_points(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     return out, ws, rank
@@ -596,6 +597,32 @@ def run_paper_shapes(args, dev):
     return out
 
 
+def run_start_points(args, dev):
+    """Start points of a large cell (the n = 24, 324-monomial stand-in):
+    hpt_binomial_start_device for 2^20 solutions (CUDA events) against the
+    host enumeration hpt_binomial_start for 2^16."""
+    import torch
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+    s, pairs = W.paper_shape(24, 324)
+    _, tot = hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, pairs, 0, 0)
+    nd, nh = min(tot, 1 << 20), min(tot, 1 << 16)
+    hpt.binomial_start_device(s.n, s.m, s.exponents, s.coeffs, pairs, 0, nd)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hpt.binomial_start_device(s.n, s.m, s.exponents, s.coeffs, pairs, 0, nd)
+    e1.record()
+    torch.cuda.synchronize()
+    dms = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, pairs, 0, nh)
+    hms = (time.perf_counter() - t0) * 1e3
+    return {"cell": "n=24, 324 monomials, planted pairs cell", "det_V": int(tot),
+            "device": {"points": int(nd), "ms": dms, "points_per_s": nd / (dms * 1e-3)},
+            "host_one_core": {"points": int(nh), "ms": hms, "points_per_s": nh / (hms * 1e-3)}}
+
+
 def cpu_baseline(seconds=12.0, max_paths=PATHS):
     """Times the oracle's step (as it stands) on growing slices of the same
     workload until about `seconds` of work is done."""
@@ -635,7 +662,8 @@ def main():
     ap.add_argument("--batch-paths", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default tuning")
-    ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective", "paper_shapes"],
+    ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective", "paper_shapes",
+                                                             "start_points"],
                     help="step: the n=16 hpt_step line only; batch: the many-systems batch only; "
                          "projective: the projective-form step only (the last two print their own JSON "
                          "object, for profiling)")
@@ -671,12 +699,13 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"batch": run_batch(args, torch.device("cuda", 0))}))
         return
-    if args.workload == "paper_shapes":
+    if args.workload in ("paper_shapes", "start_points"):
         import torch
         from paper_2111_14317_gb300 import build as hbuild
         hbuild.build()
         torch.cuda.set_device(0)
-        print(json.dumps({"paper_shapes": run_paper_shapes(args, torch.device("cuda", 0))}))
+        fn = run_paper_shapes if args.workload == "paper_shapes" else run_start_points
+        print(json.dumps({args.workload: fn(args, torch.device("cuda", 0))}))
         return
     if args.workload == "projective":
         import torch
@@ -752,6 +781,8 @@ def main():
         line["projective"] = out["projective"]
     if "paper_shapes" in out:
         line["paper_shapes"] = out["paper_shapes"]
+    if "start_points" in out:
+        line["start_points"] = out["start_points"]
     print(json.dumps(line))
 
 

@@ -187,16 +187,34 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* support_sizes, const int
 /* Host-only start points of a cell of kind PAIRS: the solutions in (C*)^n of
  * the binomial start system H(y, t=0) = 0, i.e. c_{k,p0} y^{a_{k,p0}} +
  * c_{k,p1} y^{a_{k,p1}} = 0 (Section 2 leaves this step to Huber and
- * Sturmfels).  With V_k = a_{k,p1} - a_{k,p0}, b_k = -c_{k,p0}/c_{k,p1} and an
- * integer diagonal form U V W = diag(d) (U, W unimodular), the |det V|
- * solutions are y = exp(W zeta), zeta_j = ((U log b)_j + 2 pi i m_j) / d_j,
- * m_j = 0..|d_j|-1.  Writes solutions first..first+count-1 (mixed-radix order
- * of m, last coordinate fastest) to y0[count*n] complex128 (interleaved) and
- * |det V| to *total (may be NULL).  HPT_ENOTCELL for a singular pair matrix,
- * HPT_ERANGE on integer overflow or a range beyond |det V|. */
+ * Sturmfels).  With V_k = a_{k,p1} - a_{k,p0} and b_k = -c_{k,p0}/c_{k,p1},
+ * the |det V| solutions are y = exp(V^{-1}(log b + 2 pi i k)) for k in the
+ * coset representatives 0 <= k_j < h_j of Z^n / V Z^n, h the diagonal of the
+ * Hermite normal form of the lattice V Z^n.  Exact integer work: det V and
+ * adj V from V^{-1} modulo two primes below 2^62 (Chinese remainder theorem,
+ * within Hadamard's bound), the Hermite diagonal modulo |det V|, and the phase
+ * V^{-1} k = adj(V) k / det V reduced modulo 1 exactly; V^{-1} log b in FP64.
+ * Writes solutions first..first+count-1 (mixed-radix order of k, last
+ * coordinate fastest) to y0[count*n] complex128 (interleaved) and |det V| to
+ * *total (may be NULL).  HPT_ENOTCELL for a singular pair matrix, HPT_ERANGE
+ * for |det V| >= 2^62, entries beyond the exact range, or a range beyond
+ * |det V|. */
 hpt_status hpt_binomial_start(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
                               const double* coeffs, const int32_t* pairs, int64_t first, int64_t count,
                               double* y0, int64_t* total);
+
+/* The start points of hpt_binomial_start computed on the device: host inputs
+ * as there (the exact diagonal form is formed on the host), solutions
+ * first..first+count-1 written by a kernel to y0_dev[count*n] complex128 (a
+ * device pointer owned by the caller), one thread per solution with exact
+ * 64-bit modular phase arithmetic (the constants travel as one kernel
+ * argument: no device allocation); asynchronous on `stream` (cudaStream_t as
+ * void*, NULL = legacy default stream).  *total (may be NULL) receives
+ * |det V|.  Same errors as hpt_binomial_start; HPT_ECUDA if the launch fails.
+ * Agrees with hpt_binomial_start to rounding (device exp/sincos). */
+hpt_status hpt_binomial_start_device(int32_t n, const int32_t* support_sizes, const int32_t* exponents,
+                                     const double* coeffs, const int32_t* pairs, int64_t first, int64_t count,
+                                     void* y0_dev, int64_t* total, void* stream);
 
 /* Host-only start points of a PAIRS cell for chosen lattice vectors: for each
  * k (kvec[count*n] int64, row q = k of solution q) writes y = exp(z) with

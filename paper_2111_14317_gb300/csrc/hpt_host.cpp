@@ -501,97 +501,171 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* msz, const int32_t* exps
   return HPT_OK;
 }
 
-hpt_status hpt_binomial_start(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,
-                               const int32_t* pairs, int64_t first, int64_t count, double* y0,
-                               int64_t* total) {
+}  // extern "C"
+
+namespace hpt {
+// The host part of the start points of a pairs cell: the integer diagonal
+// form U V W = diag(d) (exact), z0 = V^{-1} log b (FP64) and the phase
+// constants of every solution's 2 pi i W diag(1/d) m reduced modulo 1
+// (StartConsts).  Validates first/count against |det V| (= *total).
+hpt_status binomial_setup(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,
+                          const int32_t* pairs, int64_t first, int64_t count, bool need_out, StartConsts& S,
+                          int64_t* total) {
   int32_t M;
   hpt_status rc = check_shape(n, msz, &M);
   if (rc) return rc;
-  if (!exps || !coeffs || !pairs || first < 0 || count < 0 || (count > 0 && !y0)) {
+  if (!exps || !coeffs || !pairs || first < 0 || count < 0 || (count > 0 && !need_out)) {
     set_error("bad arguments");
     return HPT_EINVAL;
   }
   std::vector<int32_t> off(n);
   for (int k = 0, acc = 0; k < n; ++k) { off[k] = acc; acc += msz[k]; }
   // V_k = a_{k,p1} - a_{k,p0};  b_k = -c_{k,p0} / c_{k,p1}
-  std::vector<i128> A((size_t)n * n), U((size_t)n * n, 0), W((size_t)n * n, 0);
+  std::vector<int64_t> V((size_t)n * n);
   std::vector<double> br(n), bi(n);
   for (int k = 0; k < n; ++k) {
     const int p0 = pairs[2 * k], p1 = pairs[2 * k + 1];
     if (p0 < 0 || p1 < 0 || p0 >= msz[k] || p1 >= msz[k] || p0 == p1) { set_error("bad pair"); return HPT_EINVAL; }
     for (int j = 0; j < n; ++j)
-      A[k * n + j] = (i128)exps[(size_t)(off[k] + p1) * n + j] - exps[(size_t)(off[k] + p0) * n + j];
+      V[k * n + j] = (int64_t)exps[(size_t)(off[k] + p1) * n + j] - exps[(size_t)(off[k] + p0) * n + j];
     const double c0r = coeffs[2 * (off[k] + p0)], c0i = coeffs[2 * (off[k] + p0) + 1];
     const double c1r = coeffs[2 * (off[k] + p1)], c1i = coeffs[2 * (off[k] + p1) + 1];
     const double d = c1r * c1r + c1i * c1i;
     if (!(d > 0)) { set_error("zero coefficient in the cell"); return HPT_EINVAL; }
     br[k] = -(c0r * c1r + c0i * c1i) / d;
     bi[k] = -(c0i * c1r - c0r * c1i) / d;
-    U[k * n + k] = 1;
-    W[k * n + k] = 1;
   }
-  // integer diagonal form U V W = diag(dd): repeated pivot-and-reduce with
-  // the smallest nonzero entry of the trailing block as pivot
-  auto big = [](i128 v) { return v >= kLim || v <= -kLim; };
-  for (int t = 0; t < n; ++t) {
-    for (int guard = 0;; ++guard) {
-      if (guard > 100000) { set_error("diagonal form did not converge"); return HPT_ERANGE; }
-      int pi = -1, pj = -1;
-      i128 best = 0;
-      for (int i = t; i < n; ++i)
-        for (int j = t; j < n; ++j) {
-          const i128 v = iabs(A[i * n + j]);
-          if (v != 0 && (pi < 0 || v < best)) { best = v; pi = i; pj = j; }
+  // det V and adj V exactly, from V^{-1} modulo two primes below 2^62 and
+  // the Chinese remainder theorem: exact while Hadamard's bound prod |row_k|
+  // (which bounds |det V| and every (n-1)-minor) stays below p1 p2 / 2
+  double log2_h = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double r2 = 0;
+    for (int j = 0; j < n; ++j) r2 += (double)V[k * n + j] * (double)V[k * n + j];
+    if (r2 == 0) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
+    log2_h += 0.5 * log2(r2);
+  }
+  uint64_t pr[2];
+  std::vector<uint64_t> inv[2];
+  uint64_t detp[2];
+  uint64_t cand = ((uint64_t)1 << 62) - 1;
+  for (int t = 0; t < 2; ++t) {
+    for (;; cand -= 2) {
+      if (!is_prime64(cand)) continue;
+      const uint64_t p = cand;
+      // Gauss-Jordan inverse modulo p (fails when p divides det V)
+      std::vector<uint64_t> A((size_t)n * n), B((size_t)n * n, 0);
+      for (int q = 0; q < n * n; ++q) {
+        const int64_t v = V[q] % (int64_t)p;
+        A[q] = (uint64_t)(v < 0 ? v + (int64_t)p : v);
+      }
+      for (int q = 0; q < n; ++q) B[q * n + q] = 1;
+      uint64_t det = 1;
+      bool sing = false;
+      for (int c = 0; c < n && !sing; ++c) {
+        int piv = -1;
+        for (int r = c; r < n && piv < 0; ++r)
+          if (A[r * n + c]) piv = r;
+        if (piv < 0) { sing = true; break; }
+        if (piv != c) {
+          for (int x = 0; x < n; ++x) { std::swap(A[piv * n + x], A[c * n + x]); std::swap(B[piv * n + x], B[c * n + x]); }
+          det = (p - det) % p;
         }
-      if (pi < 0) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
-      if (pi != t)
-        for (int c = 0; c < n; ++c) { std::swap(A[pi * n + c], A[t * n + c]); std::swap(U[pi * n + c], U[t * n + c]); }
-      if (pj != t)
-        for (int r = 0; r < n; ++r) { std::swap(A[r * n + pj], A[r * n + t]); std::swap(W[r * n + pj], W[r * n + t]); }
-      bool done = true;
-      const i128 piv = A[t * n + t];
-      for (int i = t + 1; i < n; ++i) {
-        const i128 q = A[i * n + t] / piv;
-        if (q)
-          for (int c = 0; c < n; ++c) {
-            A[i * n + c] -= q * A[t * n + c];
-            U[i * n + c] -= q * U[t * n + c];
-            if (big(A[i * n + c]) || big(U[i * n + c])) { set_error("overflow in the diagonal form"); return HPT_ERANGE; }
+        det = mulmod(det, A[c * n + c], p);
+        const uint64_t iv = powmod(A[c * n + c], p - 2, p);
+        for (int x = 0; x < n; ++x) { A[c * n + x] = mulmod(A[c * n + x], iv, p); B[c * n + x] = mulmod(B[c * n + x], iv, p); }
+        for (int r = 0; r < n; ++r) {
+          if (r == c || !A[r * n + c]) continue;
+          const uint64_t f = A[r * n + c];
+          for (int x = 0; x < n; ++x) {
+            A[r * n + x] = (A[r * n + x] + p - mulmod(f, A[c * n + x], p)) % p;
+            B[r * n + x] = (B[r * n + x] + p - mulmod(f, B[c * n + x], p)) % p;
           }
-        if (A[i * n + t] != 0) done = false;
+        }
       }
-      for (int j = t + 1; j < n; ++j) {
-        const i128 q = A[t * n + j] / piv;
-        if (q)
-          for (int r = 0; r < n; ++r) {
-            A[r * n + j] -= q * A[r * n + t];
-            W[r * n + j] -= q * W[r * n + t];
-            if (big(A[r * n + j]) || big(W[r * n + j])) { set_error("overflow in the diagonal form"); return HPT_ERANGE; }
-          }
-        if (A[t * n + j] != 0) done = false;
-      }
-      if (done) break;
+      if (sing) continue;   // p divides det V: next prime
+      pr[t] = p;
+      detp[t] = det;
+      inv[t].resize((size_t)n * n);
+      for (int q = 0; q < n * n; ++q) inv[t][q] = mulmod(B[q], det, p);   // adj V mod p
+      cand -= 2;
+      break;
     }
   }
-  std::vector<int64_t> dd(n);
-  i128 tot = 1;
-  for (int j = 0; j < n; ++j) {
-    dd[j] = (int64_t)iabs(A[j * n + j]);
-    tot *= dd[j];
-    if (tot >= kLim) { set_error("too many start solutions"); return HPT_ERANGE; }
+  if (log2_h >= log2((double)pr[0]) + log2((double)pr[1]) - 2.0) {
+    set_error("the pair matrix's entries are too large for the exact enumeration");
+    return HPT_ERANGE;
   }
-  if (total) *total = (int64_t)tot;
-  if (first + count > (int64_t)tot) { set_error("solutions %lld..%lld requested of %lld", (long long)first, (long long)(first + count), (long long)tot); return HPT_ERANGE; }
-  // log y = V^{-1} log b + 2 pi i W diag(1/d) m: the first term by Gaussian
-  // elimination with partial pivoting on the original V; the second is a
-  // rational vector, reduced modulo 1 exactly (only its fractional part
-  // changes y), because forming W zeta in floating point cancels badly when
-  // the unimodular W has large entries.
+  const i128 P = (i128)pr[0] * (i128)pr[1];
+  const uint64_t m1 = powmod(pr[0] % pr[1], pr[1] - 2, pr[1]);   // p1^{-1} mod p2
+  auto crt = [&](uint64_t a1, uint64_t a2) -> i128 {   // symmetric residue mod p1 p2
+    const uint64_t t = mulmod((a2 + pr[1] - a1 % pr[1]) % pr[1], m1, pr[1]);
+    i128 x = (i128)a1 + (i128)pr[0] * (i128)t;
+    if (x > P / 2) x -= P;
+    return x;
+  };
+  const i128 det = crt(detp[0], detp[1]);
+  if (det == 0) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
+  const i128 D = det < 0 ? -det : det;
+  if (D >= kLim) { set_error("too many start solutions"); return HPT_ERANGE; }
+  if (total) *total = (int64_t)D;
+  if (first + count > (int64_t)D) {
+    set_error("solutions %lld..%lld requested of %lld", (long long)first, (long long)(first + count), (long long)D);
+    return HPT_ERANGE;
+  }
+  // coset representatives of Z^n / V Z^n: k_i in [0, h_i), h = the diagonal
+  // of the Hermite normal form of the lattice V Z^n, computed modulo D (the
+  // lattice contains D Z^n): column operations, rows from the last, the
+  // modulus divided by each diagonal entry found
+  std::vector<i128> H((size_t)n * n);
+  i128 R = D;
+  for (int q = 0; q < n * n; ++q) H[q] = ((i128)V[q] % R + R) % R;
+  auto egcd = [](i128 a, i128 b, i128& u, i128& v) -> i128 {
+    i128 r0 = a, r1 = b, u0 = 1, u1 = 0, v0 = 0, v1 = 1;
+    while (r1 != 0) {
+      const i128 qq = r0 / r1;
+      i128 t = r0 - qq * r1; r0 = r1; r1 = t;
+      t = u0 - qq * u1; u0 = u1; u1 = t;
+      t = v0 - qq * v1; v0 = v1; v1 = t;
+    }
+    u = u0; v = v0;
+    return r0;
+  };
+  std::vector<int64_t> h(n);
+  i128 prod = 1;
+  for (int i = n - 1; i >= 0; --i) {
+    const int k = i;
+    for (int jj = k - 1; jj >= 0; --jj) {
+      if (H[i * n + jj] == 0) continue;
+      i128 u, v;
+      const i128 a = H[i * n + k], b = H[i * n + jj];
+      const i128 g = egcd(a, b, u, v);
+      const i128 ag = a / g, bg = b / g;
+      u = (u % R + R) % R;
+      v = (v % R + R) % R;
+      for (int r = 0; r <= i; ++r) {
+        const i128 xk = H[r * n + k], xj = H[r * n + jj];
+        H[r * n + k] = ((u * xk) % R + (v * xj) % R) % R;
+        H[r * n + jj] = (((ag % R + R) % R) * xj % R + R - ((bg % R + R) % R) * xk % R) % R;
+      }
+    }
+    i128 u, v;
+    const i128 g = egcd(H[i * n + k], R, u, v);
+    const i128 gi = g < 0 ? -g : g;
+    h[i] = (int64_t)gi;
+    prod *= gi;
+    R /= gi;
+    if (R == 0) R = 1;
+    for (int r = 0; r < i; ++r)
+      for (int c = 0; c < i; ++c) H[r * n + c] %= R;
+  }
+  if (prod != D) { set_error("Hermite diagonal does not multiply to |det V|"); return HPT_ERANGE; }
+  // log y = V^{-1} log b + 2 pi i V^{-1} k: the first term by Gaussian
+  // elimination with partial pivoting in FP64; the second reduced modulo 1
+  // exactly, V^{-1} k = adj(V) k / det V, numerators modulo D
   std::vector<double> Vd((size_t)n * n), zr0(n), zi0(n);
   for (int k = 0; k < n; ++k) {
-    for (int j = 0; j < n; ++j)
-      Vd[k * n + j] = (double)exps[(size_t)(off[k] + pairs[2 * k + 1]) * n + j] -
-                      (double)exps[(size_t)(off[k] + pairs[2 * k]) * n + j];
+    for (int j = 0; j < n; ++j) Vd[k * n + j] = (double)V[k * n + j];
     zr0[k] = 0.5 * log(br[k] * br[k] + bi[k] * bi[k]);
     zi0[k] = atan2(bi[k], br[k]);
   }
@@ -599,7 +673,6 @@ hpt_status hpt_binomial_start(int32_t n, const int32_t* msz, const int32_t* exps
     int piv = j;
     for (int i = j + 1; i < n; ++i)
       if (fabs(Vd[i * n + j]) > fabs(Vd[piv * n + j])) piv = i;
-    if (Vd[piv * n + j] == 0.0) { set_error("the cell's pair matrix is singular"); return HPT_ENOTCELL; }
     if (piv != j) {
       for (int c = 0; c < n; ++c) std::swap(Vd[piv * n + c], Vd[j * n + c]);
       std::swap(zr0[piv], zr0[j]);
@@ -618,35 +691,42 @@ hpt_status hpt_binomial_start(int32_t n, const int32_t* msz, const int32_t* exps
     zr0[j] = sr / Vd[j * n + j];
     zi0[j] = si / Vd[j * n + j];
   }
-  i128 L = 1;
+  S.n = n;
+  S.D = (uint64_t)D;
   for (int j = 0; j < n; ++j) {
-    const i128 g = igcd(L, dd[j]);
-    L = L / g * dd[j];
-    if (L >= kLim) { set_error("common denominator overflow"); return HPT_ERANGE; }
+    S.h[j] = h[j];
+    S.zr0[j] = zr0[j];
+    S.zi0[j] = zi0[j];
   }
-  // W entries reduced mod L keep the products below 2^126
-  std::vector<i128> Wm((size_t)n * n);
-  for (int i = 0; i < n * n; ++i) Wm[i] = ((W[i] % L) + L) % L;
+  for (int q = 0; q < n * n; ++q) {
+    i128 a = crt(inv[0][q], inv[1][q]);   // adj V entry, exact
+    if (det < 0) a = -a;                  // V^{-1} = sign(det) adj V / D
+    S.adjm[q] = (uint64_t)((a % D + D) % D);
+  }
+  return HPT_OK;
+}
+}  // namespace hpt
+
+extern "C" {
+
+hpt_status hpt_binomial_start(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,
+                               const int32_t* pairs, int64_t first, int64_t count, double* y0,
+                               int64_t* total) {
+  StartConsts S;
+  hpt_status rc = binomial_setup(n, msz, exps, coeffs, pairs, first, count, y0 != nullptr, S, total);
+  if (rc) return rc;
   const double two_pi = 6.283185307179586476925286766559;
-  std::vector<int64_t> m(n);
+  std::vector<int64_t> k(n);
   for (int64_t q = 0; q < count; ++q) {
-    int64_t idx = first + q;   // mixed radix, last coordinate fastest
-    for (int j = n - 1; j >= 0; --j) { m[j] = idx % dd[j]; idx /= dd[j]; }
+    int64_t idx = first + q;   // mixed radix over the Hermite diagonal, last coordinate fastest
+    for (int j = n - 1; j >= 0; --j) { k[j] = idx % S.h[j]; idx /= S.h[j]; }
     for (int r = 0; r < n; ++r) {
       i128 num = 0;
-      for (int j = 0; j < n; ++j) {
-        if (!m[j]) continue;
-        // sign of d_j: W diag(1/d) uses the signed pivot
-        const i128 dj = A[j * n + j];
-        const i128 scale = L / (dj < 0 ? -dj : dj);
-        i128 t = (Wm[r * n + j] * (i128)m[j]) % L;
-        t = (t * scale) % L;
-        if (dj < 0) t = (L - t) % L;
-        num = (num + t) % L;
-      }
-      const double frac = (double)num / (double)L;
-      const double mag = exp(zr0[r]);
-      const double ang = zi0[r] + two_pi * frac;
+      for (int j = 0; j < n; ++j)
+        if (k[j]) num = (num + ((i128)S.adjm[r * n + j] * (i128)k[j]) % (i128)S.D) % (i128)S.D;
+      const double frac = (double)num / (double)S.D;
+      const double mag = exp(S.zr0[r]);
+      const double ang = S.zi0[r] + two_pi * frac;
       y0[(q * n + r) * 2] = mag * cos(ang);
       y0[(q * n + r) * 2 + 1] = mag * sin(ang);
     }

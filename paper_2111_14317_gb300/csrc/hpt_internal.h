@@ -104,6 +104,21 @@ struct KernelStat {
 
 void set_error(const char* fmt, ...);
 
+// Start points of a pairs cell (Section 2; the paper leaves this step to the
+// literature).  Every solution is log y = z0 + 2 pi i V^{-1} k, z0 = V^{-1}
+// log b, for k in a set of coset representatives of Z^n / V Z^n: k_j in
+// [0, h_j), h the diagonal of the Hermite normal form of V Z^n (product D =
+// |det V|), enumerated in mixed radix (last coordinate fastest).  The phase
+// V^{-1} k is reduced modulo 1 exactly: V^{-1} k = adjm k / D mod 1, adjm =
+// sign(det V) adj(V) mod D; all below 2^62.
+struct StartConsts {
+  int32_t n = 0, pad_ = 0;
+  uint64_t D = 1;
+  int64_t h[kMaxN];
+  double zr0[kMaxN], zi0[kMaxN];
+  uint64_t adjm[kMaxN * kMaxN];
+};
+
 }  // namespace hpt
 
 struct hpt_system_s {
@@ -252,6 +267,11 @@ cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void*
 hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
                         void* ext, int64_t chunk, cudaStream_t st);
 hpt_status check_params(const hpt_params* prm);
+// Host setup of the start points (exact diagonal form, z0, phase constants);
+// validates first + count <= |det V| (written to *total when not NULL).
+hpt_status binomial_setup(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,
+                          const int32_t* pairs, int64_t first, int64_t count, bool need_out, StartConsts& S,
+                          int64_t* total);
 // Every array of the state present (and the *_prev arrays for the Hermite
 // predictor).
 hpt_status check_state(const hpt_paths* S, const hpt_params* prm);

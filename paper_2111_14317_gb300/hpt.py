@@ -33,7 +33,7 @@ EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lif
            "hpt_device_error", "hpt_profile_enable", "hpt_profile_read", "hpt_binomial_points",
            "hpt_batch_create", "hpt_batch_destroy", "hpt_batch_get_tuning", "hpt_batch_set_tuning",
            "hpt_batch_track", "hpt_batch_autotune", "hpt_batch_stats", "hpt_homogenize", "hpt_get_nvars",
-           "hpt_euler_newton"]
+           "hpt_euler_newton", "hpt_binomial_start_device"]
 
 
 class HptError(RuntimeError):
@@ -113,6 +113,7 @@ for _name, _args in {
     "hpt_homogenize": [_VP, _VP],
     "hpt_get_nvars": [_VP, _VP, _VP, _VP],
     "hpt_euler_newton": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
+    "hpt_binomial_start_device": [_I32, _VP, _VP, _VP, _VP, _I64, _I64, _VP, _VP, _VP],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int
@@ -197,6 +198,23 @@ def binomial_start(n, m, exponents, coeffs, pairs, first=0, count=None):
     y0 = np.zeros((count, n), np.complex128)
     _check(_lib.hpt_binomial_start(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), int(first),
                                    int(count), _np_ptr(y0), ctypes.byref(tot)), "hpt_binomial_start")
+    return y0, int(tot.value)
+
+
+def binomial_start_device(n, m, exponents, coeffs, pairs, first=0, count=None, device="cuda", stream=None):
+    """The same start points computed on the device (hpt_binomial_start_device):
+    (y0 (count, n) complex128 tensor on `device`, |det V|)."""
+    msz, ex, co, _, M = _arrays(n, m, exponents, coeffs, np.zeros(sum(np.atleast_1d(m))))
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    tot = ctypes.c_int64(0)
+    _check(_lib.hpt_binomial_start(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), 0, 0, None,
+                                   ctypes.byref(tot)), "hpt_binomial_start")
+    if count is None:
+        count = int(tot.value) - first
+    y0 = torch.empty(count, n, dtype=torch.complex128, device=device)
+    _check(_lib.hpt_binomial_start_device(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), int(first),
+                                          int(count), _t_ptr(y0), ctypes.byref(tot), _stream(stream)),
+           "hpt_binomial_start_device")
     return y0, int(tot.value)
 
 
