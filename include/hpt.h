@@ -184,6 +184,24 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* support_sizes, const int
                               const int64_t* lifting, const hpt_cell* cell, int64_t* texp,
                               int64_t* denom, int64_t* alpha_num, int64_t* beta_num);
 
+/* Host-only fine mixed cells of the lifted supports (the cell step Section 2
+ * leaves to Huber and Sturmfels): every choice of one pair {p0, p1} per
+ * support S_k for which some inner normal alpha makes each pair the lowest
+ * points of its lifted support, <a_p0, alpha> + w(p0) = <a_p1, alpha> +
+ * w(p1) < <a, alpha> + w(a) for every other a in S_k.  A depth-first search
+ * fixes the pairs equation by equation among each support's lower edges and
+ * prunes a partial choice as soon as its conditions have no solution alpha
+ * (FP64 linear feasibility, Phase-I simplex); every complete choice is
+ * confirmed exactly as hpt_lift_exponents does for a PAIRS cell.  For a
+ * generic lifting these are the cells of the fine mixed subdivision and the
+ * sum of their |det V| is the mixed volume (the root count of Section 2).
+ * Inputs as hpt_lift_exponents (m_k >= 2).  Writes up to cap cells to
+ * pairs_out[cap * 2n] (local indices, the hpt_cell PAIRS layout), the number
+ * found to *ncells and sum |det V| to *mixed_volume (either may be NULL).
+ * HPT_ERANGE when a determinant or the volume leaves the exact range. */
+hpt_status hpt_mixed_cells(int32_t n, const int32_t* support_sizes, const int32_t* exponents, const int64_t* lifting,
+                           int64_t cap, int32_t* pairs_out, int64_t* ncells, int64_t* mixed_volume);
+
 /* Host-only start points of a cell of kind PAIRS: the solutions in (C*)^n of
  * the binomial start system H(y, t=0) = 0, i.e. c_{k,p0} y^{a_{k,p0}} +
  * c_{k,p1} y^{a_{k,p1}} = 0 (Section 2 leaves this step to Huber and

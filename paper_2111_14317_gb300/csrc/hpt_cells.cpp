@@ -1,0 +1,331 @@
+// Fine mixed cells of lifted supports by a pruned depth-first search (the
+// cell step that Section 2 leaves to the literature).  A fine mixed cell picks
+// one pair (edge) e_k = {p0, p1} of every support S_k such that some inner
+// normal alpha makes each pair the lowest points of its lifted support:
+//   <a_p0, alpha> + w(p0) = <a_p1, alpha> + w(p1) <= <a, alpha> + w(a), a in S_k.
+// The search fixes the pairs equation by equation and keeps a partial choice
+// only while these conditions, for the equations fixed so far, have a
+// solution alpha (a linear feasibility problem, dense Phase-I simplex in
+// FP64); candidate pairs of each support are its lower edges alone (the same
+// test with one equation), and a table of which edges of two supports can be
+// lowest together (the test with two equations) discards most branches
+// before any larger problem is solved.  Every complete choice is then confirmed exactly
+// (integer arithmetic: alpha solves the pair equations and every other point
+// of every support lies strictly above), and |det V| of the confirmed cells
+// sums to the mixed volume.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hpt_internal.h"
+
+namespace hpt {
+namespace {
+
+// Feasibility of {x : E x = f, G x >= h} (x free), Phase I of the simplex
+// method on x = u - v, G x - s = h, u, v, s >= 0 with one artificial per row,
+// Bland's rule.  Returns true when the artificial sum reaches (about) zero.
+bool lp_feasible(int n, const std::vector<double>& E, const std::vector<double>& f, const std::vector<double>& G,
+                 const std::vector<double>& h) {
+  const int me = (int)f.size(), mg = (int)h.size(), m = me + mg;
+  if (m == 0) return true;
+  const int nv = 2 * n + mg;          // u, v, s
+  const int cols = nv + m + 1;        // + artificials + rhs
+  std::vector<double> T((size_t)(m + 1) * cols, 0.0);
+  auto at = [&](int r, int c) -> double& { return T[(size_t)r * cols + c]; };
+  double scale = 1.0;
+  for (int r = 0; r < m; ++r) {
+    const bool eq = r < me;
+    const double* a = eq ? &E[(size_t)r * n] : &G[(size_t)(r - me) * n];
+    double b = eq ? f[r] : h[r - me];
+    for (int j = 0; j < n; ++j) {
+      at(r, j) = a[j];
+      at(r, n + j) = -a[j];
+    }
+    if (!eq) at(r, 2 * n + (r - me)) = -1.0;
+    const double sg = b < 0 ? -1.0 : 1.0;
+    if (sg < 0)
+      for (int c = 0; c < nv; ++c) at(r, c) = -at(r, c);
+    at(r, nv + r) = 1.0;
+    at(r, cols - 1) = sg * b;
+    scale = std::max(scale, fabs(b));
+  }
+  // objective row: minimise the sum of artificials (reduced costs in row m)
+  for (int c = 0; c < cols; ++c) {
+    double s = 0;
+    for (int r = 0; r < m; ++r) s += at(r, c);
+    at(m, c) = (c >= nv && c < nv + m) ? 0.0 : -s;
+  }
+  std::vector<int> basis(m);
+  for (int r = 0; r < m; ++r) basis[r] = nv + r;
+  const double eps = 1e-10;
+  for (int it = 0; it < 50 * (m + nv); ++it) {
+    int enter = -1;
+    for (int c = 0; c < nv + m; ++c)
+      if (at(m, c) < -eps) { enter = c; break; }   // Bland: lowest index
+    if (enter < 0) break;
+    int leave = -1;
+    double best = 0;
+    for (int r = 0; r < m; ++r) {
+      const double a = at(r, enter);
+      if (a > eps) {
+        const double ratio = at(r, cols - 1) / a;
+        if (leave < 0 || ratio < best - 1e-12 || (ratio <= best + 1e-12 && basis[r] < basis[leave])) {
+          leave = r;
+          best = ratio;
+        }
+      }
+    }
+    if (leave < 0) break;   // unbounded in Phase I cannot happen; stop
+    const double pv = at(leave, enter);
+    for (int c = 0; c < cols; ++c) at(leave, c) /= pv;
+    for (int r = 0; r <= m; ++r) {
+      if (r == leave) continue;
+      const double fct = at(r, enter);
+      if (fct == 0.0) continue;
+      for (int c = 0; c < cols; ++c) at(r, c) -= fct * at(leave, c);
+    }
+    basis[leave] = enter;
+  }
+  return -at(m, cols - 1) <= 1e-7 * scale;
+}
+
+struct Search {
+  int n;
+  std::vector<int32_t> msz, off;
+  const int32_t* exps;
+  const int64_t* lift;
+  std::vector<std::vector<std::pair<int, int>>> edges;   // lower edges per support
+  // rel[k * n + l][i * E_l + j]: edge i of support k and edge j of support l
+  // can be lowest together (the two-equation conditions are feasible)
+  std::vector<std::vector<uint8_t>> rel;
+  std::vector<int> pick;                                    // chosen edge index per equation
+  std::vector<int> order;                                   // equations in search order
+  std::vector<std::pair<int, int>> chosen;                  // per equation
+  int64_t cap, found = 0;
+  i128 volume = 0;
+  int32_t* out;
+  hpt_status err = HPT_OK;
+
+  // the conditions of equation k with pair (p0, p1), appended to E/f, G/h
+  void add(int k, int p0, int p1, std::vector<double>& E, std::vector<double>& f, std::vector<double>& G,
+           std::vector<double>& h) const {
+    const int32_t* a0 = exps + (size_t)(off[k] + p0) * n;
+    const int32_t* a1 = exps + (size_t)(off[k] + p1) * n;
+    for (int j = 0; j < n; ++j) E.push_back((double)a1[j] - a0[j]);
+    f.push_back((double)(lift[off[k] + p0] - lift[off[k] + p1]));
+    for (int l = 0; l < msz[k]; ++l) {
+      if (l == p0 || l == p1) continue;
+      const int32_t* al = exps + (size_t)(off[k] + l) * n;
+      for (int j = 0; j < n; ++j) G.push_back((double)al[j] - a0[j]);
+      h.push_back((double)(lift[off[k] + p0] - lift[off[k] + l]));
+    }
+  }
+
+  // The conditions of the equations fixed so far.  The d pair equations are
+  // eliminated first (alpha = alpha0 + N t, t in R^{n-d}); the inequalities
+  // in t are then a point test (d = n), an interval (d = n - 1) or a
+  // Phase-I problem in n - d variables.
+  bool feasible(int depth) const {
+    std::vector<double> E, f, G, h;
+    for (int d = 0; d < depth; ++d) {
+      const int k = order[d];
+      add(k, chosen[k].first, chosen[k].second, E, f, G, h);
+    }
+    const int me = (int)f.size(), mg = (int)h.size();
+    // row echelon form of [E | f] with partial pivoting
+    std::vector<double> A(E), b(f);
+    std::vector<int> pivc;
+    int r = 0;
+    for (int c = 0; c < n && r < me; ++c) {
+      int p = -1;
+      double best = 1e-9;
+      for (int i = r; i < me; ++i)
+        if (fabs(A[i * n + c]) > best) { best = fabs(A[i * n + c]); p = i; }
+      if (p < 0) continue;
+      for (int x = 0; x < n; ++x) std::swap(A[p * n + x], A[r * n + x]);
+      std::swap(b[p], b[r]);
+      const double pv = A[r * n + c];
+      for (int x = 0; x < n; ++x) A[r * n + x] /= pv;
+      b[r] /= pv;
+      for (int i = 0; i < me; ++i) {
+        if (i == r || A[i * n + c] == 0.0) continue;
+        const double fct = A[i * n + c];
+        for (int x = 0; x < n; ++x) A[i * n + x] -= fct * A[r * n + x];
+        b[i] -= fct * b[r];
+      }
+      pivc.push_back(c);
+      ++r;
+    }
+    for (int i = r; i < me; ++i)
+      if (fabs(b[i]) > 1e-7 * (1.0 + fabs(b[i]))) return false;   // inconsistent equations
+    // alpha = alpha0 + N t over the free columns
+    std::vector<int> freec;
+    std::vector<char> isp(n, 0);
+    for (int c : pivc) isp[c] = 1;
+    for (int c = 0; c < n; ++c)
+      if (!isp[c]) freec.push_back(c);
+    const int nf = (int)freec.size();
+    std::vector<double> a0(n, 0.0), N((size_t)n * nf, 0.0);
+    for (int i = 0; i < r; ++i) a0[pivc[i]] = b[i];
+    for (int q = 0; q < nf; ++q) {
+      N[(size_t)freec[q] * nf + q] = 1.0;
+      for (int i = 0; i < r; ++i) N[(size_t)pivc[i] * nf + q] = -A[i * n + freec[q]];
+    }
+    // inequalities in t: (G N) t >= h - G alpha0
+    std::vector<double> G2((size_t)mg * nf), h2(mg);
+    for (int i = 0; i < mg; ++i) {
+      double ga = 0.0;
+      for (int x = 0; x < n; ++x) ga += G[(size_t)i * n + x] * a0[x];
+      h2[i] = h[i] - ga;
+      for (int q = 0; q < nf; ++q) {
+        double s = 0.0;
+        for (int x = 0; x < n; ++x) s += G[(size_t)i * n + x] * N[(size_t)x * nf + q];
+        G2[(size_t)i * nf + q] = s;
+      }
+    }
+    const double tol = 1e-7;
+    if (nf == 0) {
+      for (int i = 0; i < mg; ++i)
+        if (h2[i] > tol * (1.0 + fabs(h2[i]))) return false;
+      return true;
+    }
+    if (nf == 1) {
+      double lo = -INFINITY, hi = INFINITY;
+      for (int i = 0; i < mg; ++i) {
+        const double g = G2[i];
+        if (fabs(g) < 1e-12) {
+          if (h2[i] > tol * (1.0 + fabs(h2[i]))) return false;
+        } else if (g > 0) {
+          lo = std::max(lo, h2[i] / g);
+        } else {
+          hi = std::min(hi, h2[i] / g);
+        }
+      }
+      return lo <= hi + tol * (1.0 + fabs(lo) + fabs(hi));
+    }
+    const std::vector<double> none;
+    return lp_feasible(nf, none, none, G2, h2);
+  }
+
+  void leaf() {
+    std::vector<int32_t> pairs(2 * n);
+    for (int k = 0; k < n; ++k) {
+      pairs[2 * k] = chosen[k].first;
+      pairs[2 * k + 1] = chosen[k].second;
+    }
+    hpt_cell cell;
+    memset(&cell, 0, sizeof(cell));
+    cell.kind = HPT_CELL_PAIRS;
+    cell.pairs = pairs.data();
+    int64_t D = 0;
+    if (hpt_lift_exponents(n, msz.data(), exps, lift, &cell, nullptr, &D, nullptr, nullptr) != HPT_OK) return;
+    // |det V| exactly (the pair matrix of a confirmed cell is nonsingular)
+    std::vector<int64_t> V((size_t)n * n);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        V[k * n + j] = (int64_t)exps[(size_t)(off[k] + pairs[2 * k + 1]) * n + j] -
+                       exps[(size_t)(off[k] + pairs[2 * k]) * n + j];
+    i128 det = 0;
+    hpt_status rc = exact_det(n, V, det);
+    if (rc) { err = rc; return; }
+    volume += det < 0 ? -det : det;
+    if (volume >= ((i128)1 << 62)) { set_error("mixed volume beyond 2^62"); err = HPT_ERANGE; return; }
+    if (found < cap && out) memcpy(out + (size_t)found * 2 * n, pairs.data(), 2 * n * sizeof(int32_t));
+    ++found;
+  }
+
+  bool compatible(int k, int i, int depth) const {
+    for (int d = 0; d < depth; ++d) {
+      const int l = order[d];
+      if (!rel[(size_t)k * n + l][(size_t)i * edges[l].size() + pick[l]]) return false;
+    }
+    return true;
+  }
+
+  void dfs(int depth) {
+    if (err) return;
+    if (depth == n) { leaf(); return; }
+    const int k = order[depth];
+    for (int i = 0; i < (int)edges[k].size(); ++i) {
+      if (!compatible(k, i, depth)) continue;   // a pair of edges that cannot be lowest together
+      chosen[k] = edges[k][i];
+      pick[k] = i;
+      if (depth < 1 || feasible(depth + 1)) dfs(depth + 1);
+      if (err) return;
+    }
+  }
+};
+
+}  // namespace
+}  // namespace hpt
+
+using namespace hpt;
+
+extern "C" hpt_status hpt_mixed_cells(int32_t n, const int32_t* msz, const int32_t* exps, const int64_t* lifting,
+                                      int64_t cap, int32_t* pairs_out, int64_t* ncells, int64_t* mixed_volume) {
+  if (n < 1 || n > kMaxN || !msz || !exps || !lifting || cap < 0 || (cap > 0 && !pairs_out)) {
+    set_error("bad arguments");
+    return HPT_EINVAL;
+  }
+  Search S;
+  S.n = n;
+  S.msz.assign(msz, msz + n);
+  S.off.resize(n);
+  int64_t M = 0;
+  for (int k = 0; k < n; ++k) {
+    if (msz[k] < 2 || msz[k] > 4096) { set_error("m_%d=%d outside [2,4096]", k, msz[k]); return HPT_EINVAL; }
+    S.off[k] = (int32_t)M;
+    M += msz[k];
+  }
+  for (int64_t i = 0; i < M * n; ++i)
+    if (exps[i] < -(1 << 20) || exps[i] > (1 << 20)) { set_error("exponent too large"); return HPT_ERANGE; }
+  S.exps = exps;
+  S.lift = lifting;
+  S.cap = cap;
+  S.out = pairs_out;
+  S.chosen.assign(n, {0, 1});
+  // lower edges of every lifted support alone
+  S.edges.resize(n);
+  for (int k = 0; k < n; ++k)
+    for (int i = 0; i < msz[k]; ++i)
+      for (int j = i + 1; j < msz[k]; ++j) {
+        std::vector<double> E, f, G, h;
+        S.add(k, i, j, E, f, G, h);
+        if (lp_feasible(n, E, f, G, h)) S.edges[k].push_back({i, j});
+      }
+  // relation table of every two supports' lower edges
+  S.rel.assign((size_t)n * n, {});
+  for (int k = 0; k < n; ++k)
+    for (int l = 0; l < n; ++l) {
+      if (l == k) continue;
+      auto& R = S.rel[(size_t)k * n + l];
+      R.assign(S.edges[k].size() * S.edges[l].size(), 0);
+      if (l < k) {   // symmetric: copy the transposed table
+        const auto& T = S.rel[(size_t)l * n + k];
+        for (size_t i = 0; i < S.edges[k].size(); ++i)
+          for (size_t j = 0; j < S.edges[l].size(); ++j) R[i * S.edges[l].size() + j] = T[j * S.edges[k].size() + i];
+        continue;
+      }
+      for (size_t i = 0; i < S.edges[k].size(); ++i)
+        for (size_t j = 0; j < S.edges[l].size(); ++j) {
+          std::vector<double> E, f, G, h;
+          S.add(k, S.edges[k][i].first, S.edges[k][i].second, E, f, G, h);
+          S.add(l, S.edges[l][j].first, S.edges[l][j].second, E, f, G, h);
+          R[i * S.edges[l].size() + j] = lp_feasible(n, E, f, G, h) ? 1 : 0;
+        }
+    }
+  S.pick.assign(n, 0);
+  // fewest candidate edges first
+  S.order.resize(n);
+  for (int k = 0; k < n; ++k) S.order[k] = k;
+  std::stable_sort(S.order.begin(), S.order.end(),
+                   [&](int a, int b) { return S.edges[a].size() < S.edges[b].size(); });
+  S.dfs(0);
+  if (S.err) return S.err;
+  if (ncells) *ncells = S.found;
+  if (mixed_volume) *mixed_volume = (int64_t)S.volume;
+  return HPT_OK;
+}

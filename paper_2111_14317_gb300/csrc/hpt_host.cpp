@@ -504,6 +504,38 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* msz, const int32_t* exps
 }  // extern "C"
 
 namespace hpt {
+// det V exactly (modular determinants over primes below 2^62, Chinese
+// remainder theorem on two of them within Hadamard's bound): HPT_ERANGE when
+// the bound exceeds the two primes' product / 4.
+hpt_status exact_det(int n, const std::vector<int64_t>& V, i128& det) {
+  double log2_h = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double r2 = 0;
+    for (int j = 0; j < n; ++j) r2 += (double)V[k * n + j] * (double)V[k * n + j];
+    if (r2 == 0) { det = 0; return HPT_OK; }
+    log2_h += 0.5 * log2(r2);
+  }
+  uint64_t p[2], d[2];
+  uint64_t cand = ((uint64_t)1 << 62) - 1;
+  for (int t = 0; t < 2; cand -= 2) {
+    if (!is_prime64(cand)) continue;
+    p[t] = cand;
+    d[t] = det_mod(n, V, cand);
+    ++t;
+  }
+  if (log2_h >= log2((double)p[0]) + log2((double)p[1]) - 2.0) {
+    set_error("pair matrix entries too large for the exact determinant");
+    return HPT_ERANGE;
+  }
+  const i128 P = (i128)p[0] * (i128)p[1];
+  const uint64_t m1 = powmod(p[0] % p[1], p[1] - 2, p[1]);
+  const uint64_t t = mulmod((d[1] + p[1] - d[0] % p[1]) % p[1], m1, p[1]);
+  i128 x = (i128)d[0] + (i128)p[0] * (i128)t;
+  if (x > P / 2) x -= P;
+  det = x;
+  return HPT_OK;
+}
+
 // The host part of the start points of a pairs cell: the integer diagonal
 // form U V W = diag(d) (exact), z0 = V^{-1} log b (FP64) and the phase
 // constants of every solution's 2 pi i W diag(1/d) m reduced modulo 1

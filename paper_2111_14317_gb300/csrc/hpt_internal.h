@@ -267,6 +267,10 @@ cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void*
 hpt_status polish_paths(hpt_system s, int64_t p, void* x, int32_t* done, float* last, const hpt_params& prm,
                         void* ext, int64_t chunk, cudaStream_t st);
 hpt_status check_params(const hpt_params* prm);
+typedef __int128 i128;
+// det V exactly for an n x n integer matrix (row-major): HPT_ERANGE when
+// Hadamard's bound is beyond the exact range (about 2^120).
+hpt_status exact_det(int n, const std::vector<int64_t>& V, i128& det);
 // Host setup of the start points (exact diagonal form, z0, phase constants);
 // validates first + count <= |det V| (written to *total when not NULL).
 hpt_status binomial_setup(int32_t n, const int32_t* msz, const int32_t* exps, const double* coeffs,

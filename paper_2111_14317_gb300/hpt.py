@@ -33,7 +33,7 @@ EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lif
            "hpt_device_error", "hpt_profile_enable", "hpt_profile_read", "hpt_binomial_points",
            "hpt_batch_create", "hpt_batch_destroy", "hpt_batch_get_tuning", "hpt_batch_set_tuning",
            "hpt_batch_track", "hpt_batch_autotune", "hpt_batch_stats", "hpt_homogenize", "hpt_get_nvars",
-           "hpt_euler_newton", "hpt_binomial_start_device"]
+           "hpt_euler_newton", "hpt_binomial_start_device", "hpt_mixed_cells"]
 
 
 class HptError(RuntimeError):
@@ -114,6 +114,7 @@ for _name, _args in {
     "hpt_get_nvars": [_VP, _VP, _VP, _VP],
     "hpt_euler_newton": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
     "hpt_binomial_start_device": [_I32, _VP, _VP, _VP, _VP, _I64, _I64, _VP, _VP, _VP],
+    "hpt_mixed_cells": [_I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int
@@ -199,6 +200,17 @@ def binomial_start(n, m, exponents, coeffs, pairs, first=0, count=None):
     _check(_lib.hpt_binomial_start(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(co), _np_ptr(pr), int(first),
                                    int(count), _np_ptr(y0), ctypes.byref(tot)), "hpt_binomial_start")
     return y0, int(tot.value)
+
+
+def mixed_cells(n, m, exponents, lifting, cap=1 << 16):
+    """Host-only fine mixed cells (hpt_mixed_cells): (pairs (count, n, 2)
+    int32 numpy, mixed volume)."""
+    msz, ex, _, li, M = _arrays(n, m, exponents, np.zeros(sum(np.atleast_1d(m)), np.complex128), lifting)
+    out = np.zeros((cap, n, 2), np.int32)
+    cnt, vol = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.hpt_mixed_cells(n, _np_ptr(msz), _np_ptr(ex), _np_ptr(li), cap, _np_ptr(out), ctypes.byref(cnt),
+                                ctypes.byref(vol)), "hpt_mixed_cells")
+    return out[:min(cnt.value, cap)].copy(), int(vol.value)
 
 
 def binomial_start_device(n, m, exponents, coeffs, pairs, first=0, count=None, device="cuda", stream=None):
