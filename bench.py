@@ -327,7 +327,8 @@ def run_batch(args, dev):
     # tolerance the predictor is used with), and the Euler predictor at 1e-3
     # for a like-for-like step count
     pred = {}
-    for name, kw in (("euler_tol1e-3", dict(predictor=0)), ("hermite_tol1e-3", dict(predictor=1))):
+    for name, kw in (() if args.skip_predictors else
+                     (("euler_tol1e-3", dict(predictor=0)), ("hermite_tol1e-3", dict(predictor=1)))):
         prm_p = hpt.Params(tol_accept=1e-3, **kw)
         b.track(y0, paths, prm_p)
         torch.cuda.synchronize()
@@ -662,6 +663,8 @@ def main():
     ap.add_argument("--batch-paths", type=int, default=512)
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep the default tuning")
+    ap.add_argument("--skip-predictors", action="store_true",
+                    help="batch: skip the Euler/Hermite comparison at tol 1e-3 (shorter profiling runs)")
     ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective", "paper_shapes",
                                                              "start_points"],
                     help="step: the n=16 hpt_step line only; batch: the many-systems batch only; "

@@ -301,7 +301,7 @@ __device__ __forceinline__ bool qr_null(int nv, cx<T> (&a)[R][CM], cx<T> (&wE)[R
 // Step control of one projective path (all lanes of its group), given the
 // directions in y coordinates: the affine rule (and predictor choice) with
 // the point scaled back to unit norm after every correction and divergence
-// judged on y_j / y_n.
+// tested on y_j / y_n.
 template <typename T, int G, int R>
 __device__ __forceinline__ void update_proj(int n, int nv, int64_t path, size_t vbase, int32_t status, bool ok,
                                             const cx<T> (&xE)[R], const cx<T> (&xN)[R], const hpt_paths& S,
@@ -621,7 +621,7 @@ cudaError_t launch_qr_shape(hpt_system s, int64_t p, const void* ext, const void
 // Shapes by N = nv (CM >= N + 2 columns in registers): (G, R, CM) =
 // (8, 1, 10) for N <= 8, (8, 2, 18) for N <= 16; FP32: (8, 3, 20) for N <= 18,
 // (8, 3, 26) for N <= 24, (32, 1, 34) above; FP64 (whose rows take twice the
-// registers): (32, 1, 20), (32, 1, 26), (32, 1, 34).
+// registers): (16, 2, 20), (32, 1, 26), (32, 1, 34).
 template <bool STEP>
 cudaError_t launch_qr_any(hpt_system s, int64_t p, const void* ext, const void* y, void* dE, void* dN, int32_t* ok,
                           const hpt_paths& S, const hpt_params& prm, cudaStream_t st) {
@@ -630,7 +630,7 @@ cudaError_t launch_qr_any(hpt_system s, int64_t p, const void* ext, const void* 
   if (s->prec == HPT_FP64) {
     if (N <= 8) return launch_qr_shape<double, 8, 1, 10, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
     if (N <= 16) return launch_qr_shape<double, 8, 2, 18, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
-    if (N <= 18) return launch_qr_shape<double, 32, 1, 20, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
+    if (N <= 18) return launch_qr_shape<double, 16, 2, 20, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
     if (N <= 24) return launch_qr_shape<double, 32, 1, 26, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
     return launch_qr_shape<double, 32, 1, 34, STEP>(s, p, ext, y, dE, dN, ok, S, prm, st);
   }
