@@ -473,7 +473,9 @@ hpt_status track_impl(hpt_batch_s* b, const int64_t* paths, const void* y0, cons
       pm.pos_begin = ctl + 1 + bk;
       pm.npos = ctl + 1 + kBuckets + bk;
       const int sh = bk < 2 ? bk : 2;   // FP64: n <= 8, <= 16, <= 32 lane groups
-      e = launch_eval_fp64_map(sh, b->d_f64, q.cap_bucket[bk], x_out, nullptr, pm, d + q.o_ext, st);
+      // evaluation sized for the bucket's variables (n <= 8, 16, 24, 32)
+      const int esh = bk < 2 ? bk : (bk == 2 ? kEval24 : 2);
+      e = launch_eval_fp64_map(esh, b->d_f64, q.cap_bucket[bk], x_out, nullptr, pm, d + q.o_ext, st);
       if (e == cudaSuccess)
         e = launch_newton_map(sh, q.cap_bucket[bk], d + q.o_ext, x_out, done, last, prm.polish_tol, pm, st);
     }

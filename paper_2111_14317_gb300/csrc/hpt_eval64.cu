@@ -198,6 +198,8 @@ cudaError_t launch_eval_fp64_map(int shape, const Fp64Sys* tab, int64_t cap, con
     eval_fp64_kernel<8, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
   else if (shape == 1)
     eval_fp64_kernel<16, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
+  else if (shape == kEval24)
+    eval_fp64_kernel<24, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
   else
     eval_fp64_kernel<32, true><<<(unsigned)blocks, 128, 0, st>>>(f, cap, yy, tau, 0, e, nullptr, nullptr, nullptr, pm, tab);
   return cudaGetLastError();

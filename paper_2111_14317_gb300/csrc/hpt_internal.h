@@ -194,8 +194,10 @@ cudaError_t launch_eval_fp64(hpt_system s, int64_t p, const void* y, const doubl
 
 Fp64Sys fp64_sys_of(const hpt_system s);
 // The same over the position range [*pm.pos_begin, *pm.npos) of a map whose
-// systems all have shape_of(n) == shape (tab: per-system constants); cap
-// bounds the range's length.  Writes the extended Jacobian (FP64) only.
+// systems all have shape_of(n) == shape (tab: per-system constants), or with
+// shape kEval24 all n <= 24; cap bounds the range's length.  Writes the
+// extended Jacobian (FP64) only.
+constexpr int kEval24 = 4;
 cudaError_t launch_eval_fp64_map(int shape, const Fp64Sys* tab, int64_t cap, const void* y, const double* tau,
                                  const PathMap& pm, void* ext, cudaStream_t st);
 
