@@ -49,6 +49,7 @@ struct MixedArgs {
   int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_cpart, s_bar;
   int64_t p;
   int ntiles;
+  int esplit;   // equation groups per tile (single-system launches with few tiles), >= 1
 };
 
 __device__ __forceinline__ uint32_t su32(const void* ptr) {
@@ -200,13 +201,24 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   const int row = tid & 127;          // point of the tile = TMEM lane
   const int half = tid >> 7;          // warpgroup: splits the column chunks
   const int ntiles = pm.npos ? (*pm.npos + 127) / 128 : P.ntiles;
-  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  // a CTA's work items are (tile, group of equations) pairs: with esplit > 1
+  // (few tiles) the equations of a tile are shared out among esplit CTAs in
+  // contiguous groups of ceil(ne / esplit); the evaluation of one (tile,
+  // equation) is the same either way
+  const int esplit = MAP ? 1 : P.esplit;
+  const int my_tiles = (ntiles * esplit - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   if (my_tiles <= 0) return;
   const bool lookahead = P.nbuf == 2 && P.wbuf == 2;
   const int nmax = pm.nmax ? pm.nmax : P.sys.n;
-  // work items are (tile, equation) pairs; a tile's system fixes the shapes
-  auto tile_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
+  auto item_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
+  auto tile_of = [&](int it) { return item_of(it) / esplit; };
   auto sys_of = [&](int tile) { return pm.tile_sys ? pm.tile_sys[tile] : 0; };
+  // equations [kb, ke) of work item it (ln: the tile's equation count)
+  auto krange = [&](int it, int ln, int& kb, int& ke) {
+    const int per = (ln + esplit - 1) / esplit, grp = item_of(it) % esplit;
+    kb = min(ln, grp * per);
+    ke = min(ln, kb + per);
+  };
 
   if (tid == 0) {
     for (int i = 0; i < (SPLIT ? 6 : 5); ++i) mbar_init(su32(&bars[i]), 1);
@@ -250,6 +262,11 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   // (cit, ck, cissued) loads the coefficient parts, one item ahead.
   int lit = 0, lk = 0, issued = 0;
   int cit = 0, ck = 0, cissued = 0;
+  {
+    int kb0, ke0;
+    krange(0, pm.sys_tab ? pm.sys_tab[sys_of(tile_of(0))].ne : P.sys.ne, kb0, ke0);
+    lk = ck = kb0;
+  }
   auto load_item = [&](int& xit, int& xk, bool cpart) {
     const int ls = sys_of(tile_of(xit));
     const int ln = pm.sys_tab ? pm.sys_tab[ls].ne : P.sys.ne;   // one image per equation
@@ -262,7 +279,16 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     } else {
       bulk_load(su32(cbuf(issued)), src, SPLIT ? lsplit : lbytes, su32(&bars[P.nbuf == 2 ? (issued & 1) : 0]));
     }
-    if (++xk >= ln) { xk = 0; ++xit; }
+    int kb, ke;
+    krange(xit, ln, kb, ke);
+    if (++xk >= ke) {
+      ++xit;
+      if (xit < my_tiles) {
+        const int nl = pm.sys_tab ? pm.sys_tab[sys_of(tile_of(xit))].ne : P.sys.ne;
+        krange(xit, nl, kb, ke);
+        xk = kb;
+      }
+    }
   };
   auto load_next = [&]() {
     if (lit >= my_tiles) return;
@@ -284,6 +310,8 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     const int tile = tile_of(it);
     const MixedSys S = pm.sys_tab ? pm.sys_tab[sys_of(tile)] : P.sys;
     const int n = S.n, ne = S.ne;   // variables, equations
+    int kb, ke;
+    krange(it, ne, kb, ke);
     const uint32_t t_j = tbase + (uint32_t)(P.wbuf * 2 * S.MP);
     const int64_t pos = (int64_t)tile * 128 + row;   // position of this row
     const int64_t path = pm.list ? pm.list[pos] : pos;
@@ -355,11 +383,11 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       }
     };
 
-    for (int k = 0; k < ne; ++k, ++g) {
+    for (int k = kb; k < ke; ++k, ++g) {
       // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
       // GEMM of equation k+1 is issued now and runs under this epilogue
       if (tid == 0) {
-        const bool ok1 = lookahead ? (k + 1 < ne ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
+        const bool ok1 = lookahead ? (k + 1 < ke ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
         if (!ok1) atomicExch(sAbort, 1);
       }
       bool ok = mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g));   // e of equation k visible
@@ -556,6 +584,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.s_bar = take(128);
     a.p = p;
     a.ntiles = (int)ntiles;
+    a.esplit = 1;
     const int smem = off + 1024;   // slack for aligning the dynamic base
     if (smem > max_smem) continue;
     cudaFuncAttributes fa;
@@ -576,8 +605,17 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, best_smem);
   if (e != cudaSuccess) return e;
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, best_per_sm) : best_per_sm;
-  int64_t grid = (int64_t)num_sms() * per_sm;
-  if (grid > ntiles) grid = ntiles;
+  const int64_t slots = (int64_t)num_sms() * per_sm;
+  // few tiles (small batches of one system): share each tile's equations out
+  // among several CTAs so that the launch's latency is not one CTA walking
+  // all n equations in turn
+  if (!map && ntiles * 2 <= slots && sys.ne > 1) {
+    const int want = (int)std::min<int64_t>(sys.ne, (slots + ntiles - 1) / ntiles);
+    const int per = (sys.ne + want - 1) / want;
+    best.esplit = (sys.ne + per - 1) / per;   // every group non-empty
+  }
+  int64_t grid = slots;
+  if (grid > ntiles * best.esplit) grid = ntiles * best.esplit;
   if (grid < 1) return cudaSuccess;
   int pi = prof_begin(prof, "eval_mixed_tc", st);
   kern<<<(unsigned)grid, kEvalThreads, best_smem, st>>>(best, (const float2*)y, tin, tau_is_t, chunks,
