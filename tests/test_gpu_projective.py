@@ -276,3 +276,30 @@ def test_parallel_lines_diverge_to_infinity(hpt, prec):
     y = y / np.linalg.norm(y)
     assert abs(y[2]) <= abs(y[0]) / prm.div_bound * 1.01
     assert abs(y[0] + y[1]) < (1e-6 if prec == 0 else 1e-4) * abs(y[0])
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("n,M", [(12, 150), (20, 260), (24, 300)], ids=["nv13", "nv21", "nv25"])
+def test_euler_newton_every_qr_shape(hpt, oracle_mod, n, M, prec):
+    """nv = 13, 21, 25: the (8,2,18), (8,3,26) / (32,1,26) and (32,1,34)
+    lane shapes of the FP32 and FP64 factorisations, on projective handles of
+    paper-shape systems, against the oracle's Algorithm 3."""
+    s, pairs = W.paper_shape(n, M)
+    cell = {"kind": "pairs", "pairs": pairs}
+    te = cells.t_exponents(s, cell)
+    ps = PJ.ProjectiveSystem(s, te["e"], te["D"])
+    h = hpt.System.from_laurent(s, cell, prec).homogenize()
+    assert h.nv == n + 1
+    p = 200
+    y = _hom_points(13, p, h.nv)
+    tau = -np.random.default_rng(14).uniform(0.0, 2.0, p)
+    dE, dN, ok = (a.cpu().numpy() for a in h.euler_newton(torch.from_numpy(y).to("cuda", h.cdtype),
+                                                          torch.from_numpy(tau).cuda()))
+    dEo, dNo, oko = ps.directions(y, tau)
+    assert oko.all() and (ok == 1).all()
+    if prec == 0:
+        assert _rel(dE, dEo).max() < 1e-10 and _rel(dN, dNo).max() < 1e-10
+    else:
+        kappa = _cond(ps.consolidated(y, tau))
+        assert (_rel(dE, dEo) <= 5e-4 * kappa).all(), np.max(_rel(dE, dEo) / kappa)
+        assert (_rel(dN, dNo) <= 5e-4 * kappa).all(), np.max(_rel(dN, dNo) / kappa)
