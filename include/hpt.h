@@ -385,6 +385,13 @@ hpt_status hpt_adjoint(hpt_system sys, int64_t p, const void* x_dev, const void*
  * HPT_OK or HPT_ETIMEOUT. */
 hpt_status hpt_device_error(hpt_system sys);
 
+/* Diagnostic: enqueues on `stream` one CTA that waits, with the library's
+ * bounded device-side wait, on an mbarrier that nothing completes; after about
+ * 2 s the wait gives up and sets the handle's error flag, so that the next
+ * hpt_device_error returns HPT_ETIMEOUT and the context stays usable.  For
+ * testing the failure path without any device fault. */
+hpt_status hpt_check_bounded_wait(hpt_system sys, void* stream);
+
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every kernel the handle launches while enabled.  hpt_profile_read returns,
  * for up to cap kernels, the name, the number of launches and the summed

@@ -328,6 +328,14 @@ hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, v
   return HPT_OK;
 }
 
+hpt_status hpt_check_bounded_wait(hpt_system s, void* stream) {
+  hpt_status rc = check_sys(s);
+  if (rc) return rc;
+  cudaError_t e = launch_bounded_wait_probe(s->d_err, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bounded-wait probe launch");
+  return HPT_OK;
+}
+
 hpt_status hpt_euler_newton(hpt_system s, int64_t p, const void* y, const double* tau, void* dE, void* dN,
                             int32_t* ok, void* stream) {
   hpt_status rc = check_sys(s);

@@ -212,6 +212,9 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
 cudaError_t launch_eval_mixed_map(hpt_system prof, const MixedSys& maxs, int tmem_cols, const uint8_t* chunks,
                                   int64_t p, const void* y, const double* tau, const PathMap& pm, void* ext,
                                   int32_t* err, int ctas_per_sm, cudaStream_t st);
+// A one-CTA kernel whose bounded mbarrier wait runs out (nothing arrives):
+// sets *err after ~2 s.
+cudaError_t launch_bounded_wait_probe(int32_t* err, cudaStream_t st);
 // Whether the mixed evaluation kernel can run these operand shapes at all
 // (its leanest configuration within max_smem bytes of shared memory and the
 // 512 tensor-memory columns of an SM).

@@ -510,6 +510,20 @@ teardown:
   }
 }
 
+// One CTA waits on an mbarrier that nothing completes, with the bounded wait
+// of the evaluation kernel: it gives up after ~2 s and raises the error flag
+// (the failure path, exercised without a device fault).
+__global__ void bounded_wait_probe_kernel(int32_t* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(su32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(su32(&bar), 0);   // no arrival: times out
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 int g_num_sms = 0;
 
 int num_sms() {
@@ -626,6 +640,11 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
 }
 
 }  // namespace
+
+cudaError_t launch_bounded_wait_probe(int32_t* err, cudaStream_t st) {
+  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(err);
+  return cudaGetLastError();
+}
 
 bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, int max_smem) {
   auto r = [](int v) { return (v + 1023) / 1024 * 1024; };

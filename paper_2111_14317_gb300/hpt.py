@@ -33,7 +33,7 @@ EXPORTS = ["hpt_default_params", "hpt_status_string", "hpt_last_error", "hpt_lif
            "hpt_device_error", "hpt_profile_enable", "hpt_profile_read", "hpt_binomial_points",
            "hpt_batch_create", "hpt_batch_destroy", "hpt_batch_get_tuning", "hpt_batch_set_tuning",
            "hpt_batch_track", "hpt_batch_autotune", "hpt_batch_stats", "hpt_homogenize", "hpt_get_nvars",
-           "hpt_euler_newton", "hpt_binomial_start_device", "hpt_mixed_cells"]
+           "hpt_euler_newton", "hpt_binomial_start_device", "hpt_mixed_cells", "hpt_check_bounded_wait"]
 
 
 class HptError(RuntimeError):
@@ -115,6 +115,7 @@ for _name, _args in {
     "hpt_euler_newton": [_VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP],
     "hpt_binomial_start_device": [_I32, _VP, _VP, _VP, _VP, _I64, _I64, _VP, _VP, _VP],
     "hpt_mixed_cells": [_I32, _VP, _VP, _VP, _I64, _VP, _VP, _VP],
+    "hpt_check_bounded_wait": [_VP, _VP],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int
@@ -356,6 +357,10 @@ class System:
                "hpt_get_texp")
         return dict(e=e.tolist(), D=int(D.value), alpha_num=al.tolist(), beta_num=be.tolist())
 
+    def check_bounded_wait(self, stream=None):
+        """Enqueue the bounded-wait probe (times out after ~2 s, sets the error flag)."""
+        _check(_lib.hpt_check_bounded_wait(self._h, _stream(stream)), "hpt_check_bounded_wait")
+
     def device_error(self):
         rc = _lib.hpt_device_error(self._h)
         return rc
@@ -494,13 +499,23 @@ class Batch:
         assert len(p) == len(self.systems)
         return p
 
+    def _check_y0(self, y0, paths):
+        """The library cannot see buffer sizes: the start points must hold
+        exactly sum_s paths[s] n_s values for the batch's systems."""
+        p = np.ascontiguousarray(np.asarray(paths, dtype=np.int64).reshape(-1))
+        if len(p) != len(self.systems) or (p < 0).any():
+            raise ValueError(f"paths must list {len(self.systems)} non-negative counts")
+        need = int(sum(int(c) * h.n for c, h in zip(p, self.systems)))
+        if y0.dtype != torch.complex128 or not y0.is_contiguous() or y0.numel() != need:
+            raise ValueError(f"y0 must be a contiguous complex128 tensor of {need} values")
+        return p
+
     def track(self, y0, paths, params=None, stream=None):
         """y0: (sum p_s n_s,) complex128 device tensor (systems concatenated,
         path-major); paths: per-system path counts.  Returns (x like y0,
         status (P,) int32, steps (P,) int32)."""
         params = params or Params()
-        p = np.ascontiguousarray(np.asarray(paths, dtype=np.int64))
-        assert y0.dtype == torch.complex128 and y0.is_contiguous()
+        p = self._check_y0(y0, paths)
         x = torch.empty_like(y0)
         P = int(p.sum())
         st = torch.empty(P, dtype=torch.int32, device=y0.device)
@@ -513,7 +528,7 @@ class Batch:
         """Coordinate-descent autotuner (hpt_batch_autotune).  Returns
         (best (K, ctas, lanes), {(K, ctas, lanes): ms})."""
         params = params or Params()
-        p = np.ascontiguousarray(np.asarray(paths, dtype=np.int64))
+        p = self._check_y0(y0, paths)
         x = torch.empty_like(y0)
         cap = 16
         cand = (Tuning * cap)()
