@@ -49,7 +49,6 @@ struct MixedArgs {
   int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_cpart, s_bar;
   int64_t p;
   int ntiles;
-  int esplit;   // equation groups per tile (single-system launches with few tiles), >= 1
 };
 
 __device__ __forceinline__ uint32_t su32(const void* ptr) {
@@ -201,23 +200,34 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   const int row = tid & 127;          // point of the tile = TMEM lane
   const int half = tid >> 7;          // warpgroup: splits the column chunks
   const int ntiles = pm.npos ? (*pm.npos + 127) / 128 : P.ntiles;
-  // a CTA's work items are (tile, group of equations) pairs: with esplit > 1
-  // (few tiles) the equations of a tile are shared out among esplit CTAs in
-  // contiguous groups of ceil(ne / esplit); the evaluation of one (tile,
-  // equation) is the same either way
-  const int esplit = MAP ? 1 : P.esplit;
-  const int my_tiles = (ntiles * esplit - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  // A CTA's work items are (tile, range of equations) pairs; the evaluation
+  // of one (tile, equation) is the same whichever CTA does it.  Many
+  // systems: whole tiles, strided over the grid.  One system: the sequence
+  // of (tile, equation) units, tile-major, is cut into gridDim.x contiguous
+  // ranges of equal length (to within one unit), so every CTA does the same
+  // work whether the tiles outnumber the CTAs or not; a range that crosses
+  // tile boundaries is one item per tile it touches.
+  const int64_t units = MAP ? 0 : (int64_t)ntiles * P.sys.ne;
+  const int64_t u0 = (int64_t)blockIdx.x * units / (int64_t)gridDim.x;
+  const int64_t u1 = ((int64_t)blockIdx.x + 1) * units / (int64_t)gridDim.x;
+  const int t0 = MAP ? 0 : (int)(u0 / P.sys.ne);
+  const int my_tiles = MAP ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                           : (u1 > u0 ? (int)((u1 - 1) / P.sys.ne) - t0 + 1 : 0);
   if (my_tiles <= 0) return;
   const bool lookahead = P.nbuf == 2 && P.wbuf == 2;
   const int nmax = pm.nmax ? pm.nmax : P.sys.n;
-  auto item_of = [&](int it) { return (int)blockIdx.x + it * (int)gridDim.x; };
-  auto tile_of = [&](int it) { return item_of(it) / esplit; };
+  auto tile_of = [&](int it) { return MAP ? (int)blockIdx.x + it * (int)gridDim.x : t0 + it; };
   auto sys_of = [&](int tile) { return pm.tile_sys ? pm.tile_sys[tile] : 0; };
   // equations [kb, ke) of work item it (ln: the tile's equation count)
   auto krange = [&](int it, int ln, int& kb, int& ke) {
-    const int per = (ln + esplit - 1) / esplit, grp = item_of(it) % esplit;
-    kb = min(ln, grp * per);
-    ke = min(ln, kb + per);
+    if (MAP) {
+      kb = 0;
+      ke = ln;
+      return;
+    }
+    const int64_t base = (int64_t)tile_of(it) * ln;
+    kb = (int)(u0 > base ? u0 - base : 0);
+    ke = (int)(u1 - base < (int64_t)ln ? u1 - base : (int64_t)ln);
   };
 
   if (tid == 0) {
@@ -598,7 +608,6 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.s_bar = take(128);
     a.p = p;
     a.ntiles = (int)ntiles;
-    a.esplit = 1;
     const int smem = off + 1024;   // slack for aligning the dynamic base
     if (smem > max_smem) continue;
     cudaFuncAttributes fa;
@@ -620,16 +629,20 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
   if (e != cudaSuccess) return e;
   const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, best_per_sm) : best_per_sm;
   const int64_t slots = (int64_t)num_sms() * per_sm;
-  // few tiles (small batches of one system): share each tile's equations out
-  // among several CTAs so that the launch's latency is not one CTA walking
-  // all n equations in turn
-  if (!map && ntiles * 2 <= slots && sys.ne > 1) {
-    const int want = (int)std::min<int64_t>(sys.ne, (slots + ntiles - 1) / ntiles);
-    const int per = (sys.ne + want - 1) / want;
-    best.esplit = (sys.ne + per - 1) / per;   // every group non-empty
-  }
+  // One system: the (tile, equation) units are shared out in equal
+  // contiguous ranges (see the kernel), so with few tiles a tile's equations
+  // go to several CTAs and with many the last wave is not left to part of
+  // the SMs (512 tiles on 304 slots: 27 units per CTA instead of 2 tiles
+  // on some CTAs and 1 on others).  The grid is the fewest CTAs that still
+  // give the smallest range length.
   int64_t grid = slots;
-  if (grid > ntiles * best.esplit) grid = ntiles * best.esplit;
+  if (!map) {
+    const int64_t units = ntiles * sys.ne;
+    const int64_t per = (units + slots - 1) / slots;
+    grid = per > 0 ? (units + per - 1) / per : 0;
+  } else if (grid > ntiles) {
+    grid = ntiles;
+  }
   if (grid < 1) return cudaSuccess;
   int pi = prof_begin(prof, "eval_mixed_tc", st);
   kern<<<(unsigned)grid, kEvalThreads, best_smem, st>>>(best, (const float2*)y, tin, tau_is_t, chunks,
