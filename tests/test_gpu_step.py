@@ -180,3 +180,100 @@ def test_step_over_several_chunks(hpt, prec):
     for k in hw:
         assert torch.equal(hw[k], torch.cat([ha[k], hb[k]])), k
     h.close()
+
+
+def _bench_like_state(hpt, y, t, prec, accepts):
+    st = hpt.PathState(y.shape[0], y.shape[1], prec)
+    yd = torch.from_numpy(y).cuda().to(st.y.dtype)
+    st.y.copy_(yd)
+    st.y_acc.copy_(yd)
+    st.tau.copy_(torch.from_numpy(np.log(t)))
+    st.tau_acc.copy_(st.tau)
+    st.dtau.fill_(0.01)
+    st.accepts.fill_(accepts)
+    return st
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_step_full_size_sampled(hpt, oracle_mod, prec):
+    """The throughput step at its full size and launch shape: n = 16, 32
+    monomials per equation, 65,536 random points (seed 1), one hpt_step, the
+    tolerance of the form (1e-3 FP64, 3e-3 mixed).  400 sampled paths (and
+    both ends of the first and last tiles) are stepped by the oracle from the
+    same state, cast to the form's precision.
+
+    (A) One accepted point and dE_acc = 0: the same accept decisions and, where
+        they agree, the same new state.
+    (B) No accepted point: every path's new y_acc is y + d_N (accepted or not),
+        so the Newton direction of every sampled path is compared.  FP64:
+        relative 1e-10 on 99% of the paths.  Mixed: the evaluation is good to
+        about 2e-4 of the term magnitudes and the solve factors the row- and
+        column-equilibrated D_z H = H_y diag(y), which turns that into a
+        relative error of at most about kappa_eq times as much, so
+        |d_N - d_N(oracle)| <= 1e-3 kappa_eq |d_N(oracle)| on 97% of the paths
+        (kappa_eq of the oracle's D_z H, equilibrated; at these random points
+        its median is about 50), and the median error is below 1e-2."""
+    sysm, alpha = W.config3(16, 32)
+    cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
+    te = cells.t_exponents(sysm, cell)
+    osys = oracle_mod.System(sysm, te["e"], te["D"])
+    P = oracle_mod.Params(tol_accept=3e-3 if prec else 1e-3)
+    prm = hpt.Params(tol_accept=P.tol_accept)
+    p = 65536
+    y, t = W.random_points(1, p, 16)
+    if prec:
+        y = y.astype(np.complex64).astype(np.complex128)
+    idx = np.concatenate([[0, 127, 128, p - 128, p - 1],
+                          np.random.default_rng(3).choice(p, 400, replace=False)])
+    idx = np.unique(idx)
+    h = hpt.System.from_laurent(sysm, cell, prec)
+    got = {}
+    for acc in (1, 0):
+        st = _bench_like_state(hpt, y, t, prec, acc)
+        h.step(st, 1, prm)
+        torch.cuda.synchronize()
+        got[acc] = {k: v.numpy()[idx] for k, v in st.to_host().items()}
+    ost = {}
+    for acc in (1, 0):
+        o = oracle_mod.PathState.start(y[idx], 0.0, 0.01)
+        o.tau[:] = np.log(t[idx])
+        o.tauacc[:] = o.tau
+        o.accepts[:] = acc
+        osys.step(P, o, 1)
+        ost[acc] = o
+
+    def rel(a, b):
+        return np.abs(a - b).max(-1) / np.maximum(1.0, np.abs(b).max(-1))
+
+    # (A) the bench's state
+    g, o = got[1], ost[1]
+    same = (g["accepts"] == o.accepts) & (g["status"] == o.status)
+    assert same.mean() >= 0.97, same.mean()
+    assert np.allclose(g["tau"][same], o.tau[same], rtol=0, atol=1e-12)
+    assert np.allclose(g["dtau"][same], o.dtau[same], rtol=0, atol=1e-15)
+    rej = same & (o.accepts == 1)    # rejected: the predicted point is y_acc again
+    assert np.array_equal(g["y"][rej], y[idx][rej].astype(g["y"].dtype))
+    if prec == 0:
+        for a, b in (("y", "y"), ("yacc", "y_acc"), ("dEacc", "dE_acc")):
+            assert rel(g[b][same], getattr(o, a)[same]).max() < 1e-10, a
+    # (B) every path's Newton direction
+    g, o = got[0], ost[0]
+    same = g["status"] == o.status
+    assert same.mean() >= 0.97, same.mean()
+    act = same & (o.status == oracle_mod.ACTIVE)
+    assert act.mean() > 0.9
+    dg = g["y_acc"][act] - y[idx][act]
+    do = o.yacc[act] - y[idx][act]
+    if prec == 0:
+        e = rel(g["y_acc"][act], o.yacc[act])
+        assert np.quantile(e, 0.99) < 1e-10 and e.max() < 1e-6, np.sort(e)[-5:]
+    else:
+        _, Hy, _ = osys.eval(y[idx][act], np.log(t[idx][act]))
+        A = Hy * y[idx][act][:, None, :]
+        A = A / np.max(np.abs(A), axis=2, keepdims=True)
+        A = A / np.max(np.abs(A), axis=1, keepdims=True)
+        kappa = np.linalg.cond(A)
+        e = np.abs(dg - do).max(-1) / np.abs(do).max(-1)
+        ok = e <= 1e-3 * kappa
+        q = np.quantile(e, [0.5, 0.9, 0.99])
+        assert ok.mean() >= 0.97 and q[0] < 1e-2, (ok.mean(), q, np.quantile(e / kappa, [0.5, 0.9, 0.99]))
