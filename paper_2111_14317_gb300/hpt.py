@@ -134,6 +134,16 @@ def _t_ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _need(t, name, dtype, shape):
+    """The library sees a pointer only: refuse (ValueError) a tensor it would
+    read or write with another layout, size or device."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} must be a tensor on the current CUDA device")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -165,7 +175,9 @@ def _arrays(n, m, exponents, coeffs, lifting):
     msz = np.ascontiguousarray(np.asarray(m, dtype=np.int32).reshape(-1))
     ex = np.ascontiguousarray(np.asarray(exponents, dtype=np.int32))
     M = int(msz.sum())
-    assert msz.shape == (n,) and ex.shape == (M, n)
+    if msz.shape != (n,) or ex.shape != (M, n) or (msz < 0).any():
+        raise ValueError(f"support sizes must be n = {n} non-negative counts and exponents an (M, n) = "
+                         f"({M}, {n}) integer array, got {msz.shape} and {ex.shape}")
     co = np.asarray(coeffs, dtype=np.complex128).reshape(M)
     co = np.ascontiguousarray(np.stack([co.real, co.imag], -1).reshape(-1))
     li = np.ascontiguousarray(np.asarray(lifting, dtype=np.int64).reshape(M))
@@ -366,15 +378,24 @@ class System:
         return rc
 
     # ----------------------------------------------------------- device work
+    def _need_state(self, state):
+        if state.n != self.nv or state.precision != self.precision or not state.y.is_cuda:
+            raise ValueError(f"state must be a device PathState with {self.nv} variables per path in "
+                             f"precision {self.precision}")
+
     def eval(self, y, t, stream=None, out=None):
         """H (p,n), H_y (p,n,nv), H_t (p,n) at y (p,nv) complex, t (p,) float64."""
         p = y.shape[0]
-        assert y.dtype == self.cdtype and y.is_contiguous() and t.dtype == torch.float64
+        _need(y, "y", self.cdtype, (p, self.nv))
+        _need(t, "t", torch.float64, (p,))
         if out is None:
             out = (torch.empty(p, self.n, dtype=self.cdtype, device=y.device),
                    torch.empty(p, self.n, self.nv, dtype=self.cdtype, device=y.device),
                    torch.empty(p, self.n, dtype=self.cdtype, device=y.device))
         H, Hy, Ht = out
+        for a, nm, shp in ((H, "H", (p, self.n)), (Hy, "Hy", (p, self.n, self.nv)), (Ht, "Ht", (p, self.n))):
+            if a is not None:
+                _need(a, nm, self.cdtype, shp)
         _check(_lib.hpt_eval(self._h, p, _t_ptr(y), _t_ptr(t), _t_ptr(H), _t_ptr(Hy), _t_ptr(Ht),
                              _stream(stream)), "hpt_eval")
         return H, Hy, Ht
@@ -383,17 +404,20 @@ class System:
         """Algorithm 3 at y (p,nv) complex, tau (p,) float64: the Euler and
         Newton directions (p,nv) each and ok (p,) int32."""
         p = y.shape[0]
-        assert y.dtype == self.cdtype and y.is_contiguous() and tau.dtype == torch.float64
+        tau = tau.contiguous()
+        _need(y, "y", self.cdtype, (p, self.nv))
+        _need(tau, "tau", torch.float64, (p,))
         dE = torch.empty(p, self.nv, dtype=self.cdtype, device=y.device)
         dN = torch.empty(p, self.nv, dtype=self.cdtype, device=y.device)
         ok = torch.empty(p, dtype=torch.int32, device=y.device)
-        _check(_lib.hpt_euler_newton(self._h, p, _t_ptr(y), _t_ptr(tau.contiguous()), _t_ptr(dE), _t_ptr(dN),
+        _check(_lib.hpt_euler_newton(self._h, p, _t_ptr(y), _t_ptr(tau), _t_ptr(dE), _t_ptr(dN),
                                      _t_ptr(ok), _stream(stream)), "hpt_euler_newton")
         return dE, dN, ok
 
     def paths_init(self, state, y0, params=None, stream=None):
         params = params or Params()
-        assert y0.dtype == torch.complex128 and y0.is_contiguous()
+        self._need_state(state)
+        _need(y0, "y0", torch.complex128, (state.p, self.n))
         c = state._c()
         _check(_lib.hpt_paths_init(self._h, state.p, _t_ptr(y0), ctypes.byref(params), ctypes.byref(c),
                                    _stream(stream)), "hpt_paths_init")
@@ -401,6 +425,7 @@ class System:
 
     def step(self, state, nsteps=1, params=None, stream=None):
         params = params or Params()
+        self._need_state(state)
         c = state._c()
         _check(_lib.hpt_step(self._h, state.p, ctypes.byref(c), int(nsteps), ctypes.byref(params),
                              _stream(stream)), "hpt_step")
@@ -411,6 +436,7 @@ class System:
         fixed 32 MiB array (see hpt_step_static in include/hpt.h for the path
         limit and the sharing rules)."""
         params = params or Params()
+        self._need_state(state)
         c = state._c()
         _check(_lib.hpt_step_static(self._h, state.p, ctypes.byref(c), int(nsteps), ctypes.byref(params),
                                     _stream(stream)), "hpt_step_static")
@@ -420,7 +446,7 @@ class System:
         """Returns (x (p,n) complex128, status (p,) int32, steps (p,) int32)."""
         params = params or Params()
         p = y0.shape[0]
-        assert y0.dtype == torch.complex128 and y0.is_contiguous()
+        _need(y0, "y0", torch.complex128, (p, self.n))
         x = torch.empty(p, self.n, dtype=torch.complex128, device=y0.device)
         st = torch.empty(p, dtype=torch.int32, device=y0.device)
         sp = torch.empty(p, dtype=torch.int32, device=y0.device)
@@ -430,16 +456,20 @@ class System:
 
     def polish(self, x, status=None, params=None, stream=None):
         params = params or Params()
-        assert x.dtype == torch.complex128 and x.is_contiguous()
+        _need(x, "x", torch.complex128, (x.shape[0], self.n))
+        if status is not None:
+            _need(status, "status", torch.int32, (x.shape[0],))
         _check(_lib.hpt_polish(self._h, x.shape[0], _t_ptr(x), _t_ptr(status), ctypes.byref(params),
                                _stream(stream)), "hpt_polish")
         return x
 
     def adjoint(self, x, gx, stream=None):
         """Coefficient gradient (M,) complex128 of a real loss with gx = dL/dx."""
-        assert x.dtype == torch.complex128 and gx.dtype == torch.complex128
+        x, gx = x.contiguous(), gx.contiguous()
+        _need(x, "x", torch.complex128, (x.shape[0], self.n))
+        _need(gx, "gx", torch.complex128, (x.shape[0], self.n))
         gc = torch.empty(self.M, dtype=torch.complex128, device=x.device)
-        _check(_lib.hpt_adjoint(self._h, x.shape[0], _t_ptr(x.contiguous()), _t_ptr(gx.contiguous()),
+        _check(_lib.hpt_adjoint(self._h, x.shape[0], _t_ptr(x), _t_ptr(gx),
                                 _t_ptr(gc), _stream(stream)), "hpt_adjoint")
         return gc
 
@@ -493,11 +523,6 @@ class Batch:
         kv = tuple(kv) + cur[len(kv):]
         t = Tuning(int(kv[0]), int(kv[1]), int(kv[2]))
         _check(_lib.hpt_batch_set_tuning(self._h, ctypes.byref(t)), "hpt_batch_set_tuning")
-
-    def _paths(self, y0s):
-        p = np.ascontiguousarray(np.array([int(y.shape[0]) for y in y0s], dtype=np.int64))
-        assert len(p) == len(self.systems)
-        return p
 
     def _check_y0(self, y0, paths):
         """The library cannot see buffer sizes: the start points must hold

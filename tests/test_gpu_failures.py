@@ -5,9 +5,11 @@ context is still usable (an evaluation that matches the oracle):
 
 * a bounded device-side wait that nothing completes gives up after about
   2 s and is reported as HPT_ETIMEOUT (then cleared);
-* non-finite coefficients, out-of-range step parameters, a projective
-  handle where an affine one is needed, and mismatched batch inputs are
-  refused with status codes;
+* non-finite coefficients and out-of-range step parameters are refused
+  with status codes; tensors whose shape, dtype or device the library
+  would misread (a state of the other precision or width, points with the
+  affine width on a projective handle, host memory) and mismatched batch
+  inputs are refused by the binding before any device work;
 * on a system whose two equations coincide (singular Jacobian everywhere)
   every path stops within its step budget; non-finite start points end as
   HPT_PATH_SINGULAR; both forms, affine and projective.
@@ -73,6 +75,23 @@ def test_refusals(hpt, oracle_mod):
         b.track(x0[:3].reshape(-1).contiguous(), [4], hpt.Params(tol_accept=3e-3))   # 3 paths of data, 4 announced
     with pytest.raises(ValueError):
         b.track(x0.reshape(-1).contiguous(), [x0.shape[0], 1], hpt.Params(tol_accept=3e-3))   # two counts, one system
+    # tensors the library would read with another layout or size
+    hp = h.homogenize()
+    t = torch.rand(x0.shape[0], dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        hp.eval(x0, t)                                    # n columns where the projective form reads n + 1
+    with pytest.raises(ValueError):
+        h.eval(x0, t[:-1])                                # one t short
+    with pytest.raises(ValueError):
+        h.step(hm.new_state(x0.shape[0]), 1)              # a mixed-form state on an FP64 handle
+    with pytest.raises(ValueError):
+        h.step(hp.new_state(x0.shape[0]), 1)              # n + 1 variables per path on an affine handle
+    with pytest.raises(ValueError):
+        h.track(x0.to(torch.complex64))                   # start points are complex128
+    with pytest.raises(ValueError):
+        h.track(x0.cpu())                                 # host memory
+    with pytest.raises(ValueError):
+        h.polish(x0[:, :-1].contiguous())
     _usable(hpt, oracle_mod)
 
 
