@@ -277,3 +277,38 @@ def test_step_full_size_sampled(hpt, oracle_mod, prec):
         ok = e <= 1e-3 * kappa
         q = np.quantile(e, [0.5, 0.9, 0.99])
         assert ok.mean() >= 0.97 and q[0] < 1e-2, (ok.mean(), q, np.quantile(e / kappa, [0.5, 0.9, 0.99]))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_step_control_schedule(hpt, prec):
+    """The GPU step control on the path y(tau) = (c0 + c2 e^tau) / c1 of
+    h = c1 y - c0 - c2 t, accepting every step (tol_accept = 1e30) from
+    tau = -3 with dtau 0.05: the Newton points are at the hand-worked tau
+    values (the step doubles after every third accept up to 0.5 and the last
+    one lands on tau = 0 exactly), y_acc is on the path (FP64 1e-14, mixed
+    1e-5) and the 14th step ends the path as converged -- the same schedule
+    the oracle's pins check."""
+    c1, c0, c2 = 2 - 1j, 0.5 + 0.25j, -1.5 + 2j
+    yx = lambda tau: (c0 + c2 * np.exp(tau)) / c1
+    h = hpt.System(1, [3], np.array([[1], [0], [0]]), np.array([c1, -c0, -c2]), np.array([0, 0, 1]),
+                   {"kind": "explicit", "alpha_num": [0], "beta_num": [0], "denom": 1}, prec)
+    st = h.new_state(1)
+    y0 = torch.tensor([[yx(-3.0)]], dtype=st.y.dtype, device="cuda")
+    st.y.copy_(y0)
+    st.y_acc.copy_(y0)
+    st.tau.fill_(-3.0)
+    st.tau_acc.fill_(-3.0)
+    st.dtau.fill_(0.05)
+    taus = [-3, -2.95, -2.90, -2.80, -2.70, -2.60, -2.40, -2.20, -2.00, -1.60, -1.20, -0.80, -0.30, 0.0]
+    dts = [0.05, 0.05, 0.1, 0.1, 0.1, 0.2, 0.2, 0.2, 0.4, 0.4, 0.4, 0.5, 0.5]
+    tol = 1e-14 if prec == 0 else 1e-5
+    for k in range(14):
+        h.step(st, 1, hpt.Params(tol_accept=1e30))
+        r = {f: v.numpy() for f, v in st.to_host().items()}
+        assert r["accepts"][0] == k + 1 and r["rejects"][0] == 0
+        assert abs(r["tau_acc"][0] - taus[k]) < 1e-12
+        assert abs(r["y_acc"][0, 0] - yx(taus[k])) < tol * max(1.0, abs(yx(taus[k])))
+        if k < 13:
+            assert r["status"][0] == hpt.ACTIVE and abs(r["dtau"][0] - dts[k]) < 1e-15 and r["tau"][0] <= 0.0
+    assert r["status"][0] == hpt.CONVERGED and r["tau_acc"][0] == 0.0
+    assert h.device_error() == 0
