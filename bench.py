@@ -271,6 +271,7 @@ def run_gpu(args):
         out["projective"] = run_projective(args, dev)
         out["paper_shapes"] = run_paper_shapes(args, dev)
         out["start_points"] = run_start_points(args, dev)
+        out["step100"] = run_step100(args, dev)
     if ws > 1:
         dist.destroy_process_group()
     return out, ws, rank
@@ -598,6 +599,57 @@ def run_paper_shapes(args, dev):
     return out
 
 
+def run_step100(args, dev):
+    """The paper's protocol (100 consecutive Euler-Newton steps in one call)
+    at the throughput size: 65,536 paths of a system of the same shape
+    (n = 16, 32 monomials per equation, exponent vectors with 4 nonzeros, here
+    in [-2, 2]) whose planted cell gives real homotopy paths, started at
+    exp(V^-1 (log b + 2 pi i j e_1)), j < 65,536 (j taken modulo |det V| by
+    the lattice: a repeated start point costs the same).  One hpt_step call
+    with nsteps = 100 per run, CUDA events around it, median of 3 after a
+    warm-up; path-steps are the steps the paths actually took (accepts and
+    rejects alike; a path that finishes stops)."""
+    import torch
+    from paper_2111_14317_gb300 import hpt
+    import workloads as W
+    n = N_VARS
+    s, pairs = W.paper_shape(n, N_VARS * M_PER_EQ)
+    _, det = hpt.binomial_start(s.n, s.m, s.exponents, s.coeffs, pairs, 0, 0)
+    ks = np.zeros((PATHS, n), np.int64)
+    ks[:, 0] = np.arange(PATHS)
+    x0 = torch.from_numpy(np.ascontiguousarray(hpt.binomial_points(n, s.m, s.exponents, s.coeffs, pairs, ks)))
+    x0 = x0.to(dev)
+    out = {"workload": f"planted-cell system n={n}, {M_PER_EQ} monomials/equation, |det V| = {det}; "
+                       f"{PATHS} paths from the start points; hpt_step(nsteps=100) per call",
+           "det_V": int(det)}
+    for form, prec in (("mixed", hpt.HPT_MIXED), ("fp64", hpt.HPT_FP64)):
+        h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": pairs}, prec)
+        prm = hpt.Params(tol_accept=3e-3 if prec == hpt.HPT_MIXED else 1e-3)
+        st = hpt.PathState(PATHS, n, prec, device=dev)
+        ms = []
+        for rep in range(4):
+            h.paths_init(st, x0, prm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.step(st, 100, prm)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep:   # the first run warms up
+                ms.append(e0.elapsed_time(e1))
+        med = statistics.median(ms)
+        steps = int(st.steps.sum().item())
+        out[form] = {"ms_per_call": med, "path_steps": steps, "value": steps / (med * 1e-3), "unit": UNIT,
+                     "active_after": int((st.status == hpt.ACTIVE).sum().item()),
+                     "converged_after": int((st.status == hpt.CONVERGED).sum().item())}
+        assert h.device_error() == 0, "device-side wait timed out"
+        h.close()
+        del st
+        torch.cuda.empty_cache()
+    out["mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def run_start_points(args, dev):
     """Start points of a large cell (the n = 24, 324-monomial stand-in):
     hpt_binomial_start_device for 2^20 solutions (CUDA events) against the
@@ -666,7 +718,7 @@ def main():
     ap.add_argument("--skip-predictors", action="store_true",
                     help="batch: skip the Euler/Hermite comparison at tol 1e-3 (shorter profiling runs)")
     ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective", "paper_shapes",
-                                                             "start_points"],
+                                                             "start_points", "step100"],
                     help="step: the n=16 hpt_step line only; batch: the many-systems batch only; "
                          "projective: the projective-form step only (the last two print their own JSON "
                          "object, for profiling)")
@@ -702,12 +754,13 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"batch": run_batch(args, torch.device("cuda", 0))}))
         return
-    if args.workload in ("paper_shapes", "start_points"):
+    if args.workload in ("paper_shapes", "start_points", "step100"):
         import torch
         from paper_2111_14317_gb300 import build as hbuild
         hbuild.build()
         torch.cuda.set_device(0)
-        fn = run_paper_shapes if args.workload == "paper_shapes" else run_start_points
+        fn = {"paper_shapes": run_paper_shapes, "start_points": run_start_points,
+              "step100": run_step100}[args.workload]
         print(json.dumps({args.workload: fn(args, torch.device("cuda", 0))}))
         return
     if args.workload == "projective":
@@ -786,6 +839,8 @@ def main():
         line["paper_shapes"] = out["paper_shapes"]
     if "start_points" in out:
         line["start_points"] = out["start_points"]
+    if "step100" in out:
+        line["step100"] = out["step100"]
     print(json.dumps(line))
 
 
