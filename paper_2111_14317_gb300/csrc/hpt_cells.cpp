@@ -5,8 +5,9 @@
 //   <a_p0, alpha> + w(p0) = <a_p1, alpha> + w(p1) <= <a, alpha> + w(a), a in S_k.
 // The search fixes the pairs equation by equation and keeps a partial choice
 // only while these conditions, for the equations fixed so far, have a
-// solution alpha (a linear feasibility problem, dense Phase-I simplex in
-// FP64); candidate pairs of each support are its lower edges alone (the same
+// solution alpha (a linear feasibility problem in FP64: the pair equations
+// are eliminated, then a point test, an interval, a Fourier-Motzkin
+// elimination for two free variables, or a dense Phase-I simplex); candidate pairs of each support are its lower edges alone (the same
 // test with one equation), and a table of which edges of two supports can be
 // lowest together (the test with two equations) discards most branches
 // before any larger problem is solved.  Every complete choice is then confirmed exactly
@@ -27,13 +28,19 @@ namespace {
 // Feasibility of {x : E x = f, G x >= h} (x free), Phase I of the simplex
 // method on x = u - v, G x - s = h, u, v, s >= 0 with one artificial per row,
 // Bland's rule.  Returns true when the artificial sum reaches (about) zero.
+struct LpScratch {
+  std::vector<double> T;
+  std::vector<int> basis;
+};
+
 bool lp_feasible(int n, const std::vector<double>& E, const std::vector<double>& f, const std::vector<double>& G,
-                 const std::vector<double>& h) {
+                 const std::vector<double>& h, LpScratch& W) {
   const int me = (int)f.size(), mg = (int)h.size(), m = me + mg;
   if (m == 0) return true;
   const int nv = 2 * n + mg;          // u, v, s
   const int cols = nv + m + 1;        // + artificials + rhs
-  std::vector<double> T((size_t)(m + 1) * cols, 0.0);
+  std::vector<double>& T = W.T;
+  T.assign((size_t)(m + 1) * cols, 0.0);
   auto at = [&](int r, int c) -> double& { return T[(size_t)r * cols + c]; };
   double scale = 1.0;
   for (int r = 0; r < m; ++r) {
@@ -58,7 +65,8 @@ bool lp_feasible(int n, const std::vector<double>& E, const std::vector<double>&
     for (int r = 0; r < m; ++r) s += at(r, c);
     at(m, c) = (c >= nv && c < nv + m) ? 0.0 : -s;
   }
-  std::vector<int> basis(m);
+  std::vector<int>& basis = W.basis;
+  basis.resize(m);
   for (int r = 0; r < m; ++r) basis[r] = nv + r;
   const double eps = 1e-10;
   for (int it = 0; it < 50 * (m + nv); ++it) {
@@ -108,6 +116,11 @@ struct Search {
   i128 volume = 0;
   int32_t* out;
   hpt_status err = HPT_OK;
+  // scratch of feasible(), reused from node to node
+  mutable std::vector<double> E, f, G, h, A, b, a0, N, G2, h2;
+  mutable std::vector<int> pivc, freec;
+  mutable std::vector<char> isp;
+  mutable LpScratch lp;
 
   // the conditions of equation k with pair (p0, p1), appended to E/f, G/h
   void add(int k, int p0, int p1, std::vector<double>& E, std::vector<double>& f, std::vector<double>& G,
@@ -129,15 +142,19 @@ struct Search {
   // in t are then a point test (d = n), an interval (d = n - 1) or a
   // Phase-I problem in n - d variables.
   bool feasible(int depth) const {
-    std::vector<double> E, f, G, h;
+    E.clear();
+    f.clear();
+    G.clear();
+    h.clear();
     for (int d = 0; d < depth; ++d) {
       const int k = order[d];
       add(k, chosen[k].first, chosen[k].second, E, f, G, h);
     }
     const int me = (int)f.size(), mg = (int)h.size();
     // row echelon form of [E | f] with partial pivoting
-    std::vector<double> A(E), b(f);
-    std::vector<int> pivc;
+    A = E;
+    b = f;
+    pivc.clear();
     int r = 0;
     for (int c = 0; c < n && r < me; ++c) {
       int p = -1;
@@ -162,20 +179,22 @@ struct Search {
     for (int i = r; i < me; ++i)
       if (fabs(b[i]) > 1e-7 * (1.0 + fabs(b[i]))) return false;   // inconsistent equations
     // alpha = alpha0 + N t over the free columns
-    std::vector<int> freec;
-    std::vector<char> isp(n, 0);
+    freec.clear();
+    isp.assign(n, 0);
     for (int c : pivc) isp[c] = 1;
     for (int c = 0; c < n; ++c)
       if (!isp[c]) freec.push_back(c);
     const int nf = (int)freec.size();
-    std::vector<double> a0(n, 0.0), N((size_t)n * nf, 0.0);
+    a0.assign(n, 0.0);
+    N.assign((size_t)n * nf, 0.0);
     for (int i = 0; i < r; ++i) a0[pivc[i]] = b[i];
     for (int q = 0; q < nf; ++q) {
       N[(size_t)freec[q] * nf + q] = 1.0;
       for (int i = 0; i < r; ++i) N[(size_t)pivc[i] * nf + q] = -A[i * n + freec[q]];
     }
     // inequalities in t: (G N) t >= h - G alpha0
-    std::vector<double> G2((size_t)mg * nf), h2(mg);
+    G2.assign((size_t)mg * nf, 0.0);
+    h2.assign(mg, 0.0);
     for (int i = 0; i < mg; ++i) {
       double ga = 0.0;
       for (int x = 0; x < n; ++x) ga += G[(size_t)i * n + x] * a0[x];
@@ -192,22 +211,44 @@ struct Search {
         if (h2[i] > tol * (1.0 + fabs(h2[i]))) return false;
       return true;
     }
+    // one free variable: conditions g t >= c bound t from below or above
+    double lo = -INFINITY, hi = INFINITY;
+    auto bound = [&](double g, double c) -> bool {
+      if (fabs(g) < 1e-12) return !(c > tol * (1.0 + fabs(c)));
+      if (g > 0) lo = std::max(lo, c / g);
+      else hi = std::min(hi, c / g);
+      return true;
+    };
     if (nf == 1) {
-      double lo = -INFINITY, hi = INFINITY;
+      for (int i = 0; i < mg; ++i)
+        if (!bound(G2[i], h2[i])) return false;
+      return lo <= hi + tol * (1.0 + fabs(lo) + fabs(hi));
+    }
+    if (nf == 2) {
+      // Fourier-Motzkin: a condition with a positive t2 coefficient bounds
+      // t2 from below by c_i - d_i t1, one with a negative coefficient from
+      // above by c_j - d_j t1 (both rows divided by |g_2|); t2 exists
+      // exactly when every lower bound is at most every upper bound, i.e.
+      // (d_i - d_j) t1 >= c_i - c_j for each such pair, together with the
+      // conditions that do not involve t2
       for (int i = 0; i < mg; ++i) {
-        const double g = G2[i];
-        if (fabs(g) < 1e-12) {
-          if (h2[i] > tol * (1.0 + fabs(h2[i]))) return false;
-        } else if (g > 0) {
-          lo = std::max(lo, h2[i] / g);
-        } else {
-          hi = std::min(hi, h2[i] / g);
+        const double gi = G2[2 * i + 1];
+        if (fabs(gi) < 1e-12) {
+          if (!bound(G2[2 * i], h2[i])) return false;
+        } else if (gi > 0) {
+          const double di = G2[2 * i] / gi, ci = h2[i] / gi;
+          for (int j = 0; j < mg; ++j) {
+            const double gj = G2[2 * j + 1];
+            if (!(gj < -1e-12)) continue;
+            const double dj = G2[2 * j] / gj, cj = h2[j] / gj;
+            if (!bound(di - dj, ci - cj)) return false;
+          }
         }
       }
       return lo <= hi + tol * (1.0 + fabs(lo) + fabs(hi));
     }
     const std::vector<double> none;
-    return lp_feasible(nf, none, none, G2, h2);
+    return lp_feasible(nf, none, none, G2, h2, lp);
   }
 
   void leaf() {
@@ -294,7 +335,7 @@ extern "C" hpt_status hpt_mixed_cells(int32_t n, const int32_t* msz, const int32
       for (int j = i + 1; j < msz[k]; ++j) {
         std::vector<double> E, f, G, h;
         S.add(k, i, j, E, f, G, h);
-        if (lp_feasible(n, E, f, G, h)) S.edges[k].push_back({i, j});
+        if (lp_feasible(n, E, f, G, h, S.lp)) S.edges[k].push_back({i, j});
       }
   // relation table of every two supports' lower edges
   S.rel.assign((size_t)n * n, {});
@@ -314,7 +355,7 @@ extern "C" hpt_status hpt_mixed_cells(int32_t n, const int32_t* msz, const int32
           std::vector<double> E, f, G, h;
           S.add(k, S.edges[k][i].first, S.edges[k][i].second, E, f, G, h);
           S.add(l, S.edges[l][j].first, S.edges[l][j].second, E, f, G, h);
-          R[i * S.edges[l].size() + j] = lp_feasible(n, E, f, G, h) ? 1 : 0;
+          R[i * S.edges[l].size() + j] = lp_feasible(n, E, f, G, h, S.lp) ? 1 : 0;
         }
     }
   S.pick.assign(n, 0);
