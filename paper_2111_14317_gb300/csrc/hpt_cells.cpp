@@ -7,10 +7,12 @@
 // only while these conditions, for the equations fixed so far, have a
 // solution alpha (a linear feasibility problem in FP64: the pair equations
 // are eliminated, then a point test, an interval, a Fourier-Motzkin
-// elimination for two free variables, or a dense Phase-I simplex); candidate pairs of each support are its lower edges alone (the same
-// test with one equation), and a table of which edges of two supports can be
+// elimination for two free variables, or a dense Phase-I simplex).
+// Candidate pairs of each support are its lower edges alone (the same test
+// with one equation), and a table of which edges of two supports can be
 // lowest together (the test with two equations) discards most branches
-// before any larger problem is solved.  Every complete choice is then confirmed exactly
+// before any larger problem is solved.  Every complete choice is then
+// confirmed exactly
 // (integer arithmetic: alpha solves the pair equations and every other point
 // of every support lies strictly above), and |det V| of the confirmed cells
 // sums to the mixed volume.
