@@ -7,7 +7,8 @@
 // only while these conditions, for the equations fixed so far, have a
 // solution alpha (a linear feasibility problem in FP64: the pair equations
 // are eliminated, then a point test, an interval, a Fourier-Motzkin
-// elimination for two free variables, or a dense Phase-I simplex).
+// elimination for two free variables, or the Farkas alternative by a small
+// two-phase simplex).
 // Candidate pairs of each support are its lower edges alone (the same test
 // with one equation), and a table of which edges of two supports can be
 // lowest together (the test with two equations) discards most branches
@@ -100,6 +101,88 @@ bool lp_feasible(int n, const std::vector<double>& E, const std::vector<double>&
     basis[leave] = enter;
   }
   return -at(m, cols - 1) <= 1e-7 * scale;
+}
+
+// Feasibility of {t in R^d : G t >= h} (mg rows of G) through the Farkas
+// alternative: the system is infeasible exactly when some y >= 0 with
+// G^T y = 0 and sum y = 1 has h^T y > 0.  Two-phase simplex on those d + 1
+// equality rows (Bland's rule): if Phase I finds no such y the system is
+// feasible (strictly, by Gordan's theorem); otherwise Phase II maximises
+// h^T y.  The tableau has d + 1 rows where the primal Phase I of lp_feasible
+// has mg, which is what makes it the cheaper test for many conditions in few
+// variables.
+bool farkas_feasible(int d, int mg, const std::vector<double>& G, const std::vector<double>& h, LpScratch& W) {
+  if (mg == 0) return true;
+  const int R = d + 1, C = mg + R + 1;   // y, artificials, rhs
+  std::vector<double>& T = W.T;
+  T.assign((size_t)(R + 2) * C, 0.0);    // + Phase I and Phase II objective rows
+  auto at = [&](int r, int c) -> double& { return T[(size_t)r * C + c]; };
+  double hmax = 0.0;
+  for (int i = 0; i < mg; ++i) {
+    for (int q = 0; q < d; ++q) at(q, i) = G[(size_t)i * d + q];
+    at(d, i) = 1.0;
+    hmax = std::max(hmax, fabs(h[i]));
+  }
+  at(d, C - 1) = 1.0;
+  for (int r = 0; r < R; ++r) at(r, mg + r) = 1.0;
+  // reduced costs with the artificials basic: Phase I (minimise their sum)
+  // in row R, Phase II (minimise -h^T y) in row R + 1
+  for (int i = 0; i < mg; ++i) {
+    double s = 0.0;
+    for (int r = 0; r < R; ++r) s += at(r, i);
+    at(R, i) = -s;
+    at(R + 1, i) = -h[i];
+  }
+  at(R, C - 1) = -1.0;
+  std::vector<int>& basis = W.basis;
+  basis.resize(R);
+  for (int r = 0; r < R; ++r) basis[r] = mg + r;
+  const double eps = 1e-10;
+  auto pivot = [&](int pr, int pc) {
+    const double pv = at(pr, pc);
+    for (int c = 0; c < C; ++c) at(pr, c) /= pv;
+    for (int r = 0; r < R + 2; ++r) {
+      if (r == pr) continue;
+      const double fct = at(r, pc);
+      if (fct == 0.0) continue;
+      for (int c = 0; c < C; ++c) at(r, c) -= fct * at(pr, c);
+    }
+    basis[pr] = pc;
+  };
+  // one simplex phase on objective row `obj`; only y columns enter
+  auto run = [&](int obj) {
+    for (int it = 0; it < 50 * (R + mg); ++it) {
+      int enter = -1;
+      for (int c = 0; c < mg; ++c)
+        if (at(obj, c) < -eps) { enter = c; break; }   // Bland: lowest index
+      if (enter < 0) return;
+      int leave = -1;
+      double best = 0.0;
+      for (int r = 0; r < R; ++r) {
+        const double a = at(r, enter);
+        if (a > eps) {
+          const double ratio = at(r, C - 1) / a;
+          if (leave < 0 || ratio < best - 1e-12 || (ratio <= best + 1e-12 && basis[r] < basis[leave])) {
+            leave = r;
+            best = ratio;
+          }
+        }
+      }
+      if (leave < 0) return;   // unbounded: cannot happen with sum y = 1
+      pivot(leave, enter);
+    }
+  };
+  run(R);
+  if (-at(R, C - 1) > 1e-9) return true;   // no y: the conditions hold strictly somewhere
+  // artificials left in the basis (at zero) leave it on any y column; a row
+  // with no y entry is redundant and stays out of the ratio tests
+  for (int r = 0; r < R; ++r) {
+    if (basis[r] < mg) continue;
+    for (int c = 0; c < mg; ++c)
+      if (fabs(at(r, c)) > eps) { pivot(r, c); break; }
+  }
+  run(R + 1);
+  return !(at(R + 1, C - 1) > 1e-7 * std::max(1.0, hmax));   // max h^T y
 }
 
 struct Search {
@@ -249,8 +332,7 @@ struct Search {
       }
       return lo <= hi + tol * (1.0 + fabs(lo) + fabs(hi));
     }
-    const std::vector<double> none;
-    return lp_feasible(nf, none, none, G2, h2, lp);
+    return farkas_feasible(nf, mg, G2, h2, lp);
   }
 
   void leaf() {
