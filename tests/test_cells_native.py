@@ -1,8 +1,8 @@
 """The library's mixed-cell search (hpt_mixed_cells, host code; CPU tests).
 
-* On configs 1 and 2 and small random systems it finds exactly the oracle's
-  brute-force cells (same pairs, same mixed volume, and the BKK root counts
-  of those configs).
+* On configs 1 and 2 and on dozens of small random systems it finds exactly
+  the oracle's brute-force cells (same pairs, same mixed volume, and the BKK
+  root counts of those configs).
 * Beyond brute force (n = 6 and 8) the mixed volume it reports does not
   depend on the lifting (two independent generic liftings agree), every cell
   passes the exact cell test, and no two cells coincide.
@@ -49,6 +49,23 @@ def test_cells_equal_brute_force_random(hpt_host, n, m, seed):
         assert vol == mv and _canon(pc) == _canon([c["pairs"] for c in cl])
         return
     pytest.skip("no generic sample")
+
+
+@pytest.mark.parametrize("n,m", [(2, 4), (3, 4), (3, 5), (4, 4)])
+def test_cells_equal_brute_force_sweep(hpt_host, n, m):
+    """Many generic random systems per shape (lifting up to 2^12): the same
+    cells and mixed volume as brute force every time."""
+    checked = 0
+    for seed in range(10):
+        s = W.laurent_system(900 + seed, n, m, -2, 2, 1 << 12, attempt=seed)
+        try:
+            cl, mv = cells.mixed_cells(s)
+        except cells.NonGeneric:
+            continue
+        pc, vol = hpt_host.mixed_cells(s.n, s.m, s.exponents, s.lifting)
+        assert vol == mv and _canon(pc) == _canon([c["pairs"] for c in cl]), seed
+        checked += 1
+    assert checked >= 5
 
 
 @pytest.mark.parametrize("n,m", [(6, 5), (8, 5)])
