@@ -191,7 +191,9 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* support_sizes, const int
  * w(p1) < <a, alpha> + w(a) for every other a in S_k.  A depth-first search
  * fixes the pairs equation by equation among each support's lower edges and
  * prunes a partial choice as soon as its conditions have no solution alpha
- * (FP64 linear feasibility, Phase-I simplex); every complete choice is
+ * (FP64 linear feasibility: the pair equations eliminated, then an interval,
+ * a Fourier-Motzkin step, or a small simplex on the Farkas alternative);
+ * every complete choice is
  * confirmed exactly as hpt_lift_exponents does for a PAIRS cell.  For a
  * generic lifting these are the cells of the fine mixed subdivision and the
  * sum of their |det V| is the mixed volume (the root count of Section 2).
