@@ -201,10 +201,15 @@ struct Search {
   i128 volume = 0;
   int32_t* out;
   hpt_status err = HPT_OK;
-  // scratch of feasible(), reused from node to node
-  mutable std::vector<double> E, f, G, h, A, b, a0, N, G2, h2;
-  mutable std::vector<int> pivc, freec;
-  mutable std::vector<char> isp;
+  // level d of the search (the first d equations of `order` fixed): the
+  // inner normals alpha = a0 + N t, t in R^nf, that satisfy their pair
+  // equations, and their other conditions G2 t >= h2 (nf values per row)
+  struct Level {
+    int nf = 0;
+    std::vector<double> a0, N, G2, h2;
+  };
+  std::vector<Level> lv;
+  std::vector<double> u;
   mutable LpScratch lp;
 
   // the conditions of equation k with pair (p0, p1), appended to E/f, G/h
@@ -222,74 +227,11 @@ struct Search {
     }
   }
 
-  // The conditions of the equations fixed so far.  The d pair equations are
-  // eliminated first (alpha = alpha0 + N t, t in R^{n-d}); the inequalities
-  // in t are then a point test (d = n), an interval (d = n - 1) or a
-  // Phase-I problem in n - d variables.
-  bool feasible(int depth) const {
-    E.clear();
-    f.clear();
-    G.clear();
-    h.clear();
-    for (int d = 0; d < depth; ++d) {
-      const int k = order[d];
-      add(k, chosen[k].first, chosen[k].second, E, f, G, h);
-    }
-    const int me = (int)f.size(), mg = (int)h.size();
-    // row echelon form of [E | f] with partial pivoting
-    A = E;
-    b = f;
-    pivc.clear();
-    int r = 0;
-    for (int c = 0; c < n && r < me; ++c) {
-      int p = -1;
-      double best = 1e-9;
-      for (int i = r; i < me; ++i)
-        if (fabs(A[i * n + c]) > best) { best = fabs(A[i * n + c]); p = i; }
-      if (p < 0) continue;
-      for (int x = 0; x < n; ++x) std::swap(A[p * n + x], A[r * n + x]);
-      std::swap(b[p], b[r]);
-      const double pv = A[r * n + c];
-      for (int x = 0; x < n; ++x) A[r * n + x] /= pv;
-      b[r] /= pv;
-      for (int i = 0; i < me; ++i) {
-        if (i == r || A[i * n + c] == 0.0) continue;
-        const double fct = A[i * n + c];
-        for (int x = 0; x < n; ++x) A[i * n + x] -= fct * A[r * n + x];
-        b[i] -= fct * b[r];
-      }
-      pivc.push_back(c);
-      ++r;
-    }
-    for (int i = r; i < me; ++i)
-      if (fabs(b[i]) > 1e-7 * (1.0 + fabs(b[i]))) return false;   // inconsistent equations
-    // alpha = alpha0 + N t over the free columns
-    freec.clear();
-    isp.assign(n, 0);
-    for (int c : pivc) isp[c] = 1;
-    for (int c = 0; c < n; ++c)
-      if (!isp[c]) freec.push_back(c);
-    const int nf = (int)freec.size();
-    a0.assign(n, 0.0);
-    N.assign((size_t)n * nf, 0.0);
-    for (int i = 0; i < r; ++i) a0[pivc[i]] = b[i];
-    for (int q = 0; q < nf; ++q) {
-      N[(size_t)freec[q] * nf + q] = 1.0;
-      for (int i = 0; i < r; ++i) N[(size_t)pivc[i] * nf + q] = -A[i * n + freec[q]];
-    }
-    // inequalities in t: (G N) t >= h - G alpha0
-    G2.assign((size_t)mg * nf, 0.0);
-    h2.assign(mg, 0.0);
-    for (int i = 0; i < mg; ++i) {
-      double ga = 0.0;
-      for (int x = 0; x < n; ++x) ga += G[(size_t)i * n + x] * a0[x];
-      h2[i] = h[i] - ga;
-      for (int q = 0; q < nf; ++q) {
-        double s = 0.0;
-        for (int x = 0; x < n; ++x) s += G[(size_t)i * n + x] * N[(size_t)x * nf + q];
-        G2[(size_t)i * nf + q] = s;
-      }
-    }
+  // Whether {t in R^nf : G2 t >= h2} has a solution (rows of G2 hold nf
+  // values): a point test (nf = 0), an interval (nf = 1), Fourier-Motzkin
+  // (nf = 2), else the Farkas alternative.
+  bool solve_t(int nf, const std::vector<double>& G2, const std::vector<double>& h2) const {
+    const int mg = (int)h2.size();
     const double tol = 1e-7;
     if (nf == 0) {
       for (int i = 0; i < mg; ++i)
@@ -335,6 +277,83 @@ struct Search {
     return farkas_feasible(nf, mg, G2, h2, lp);
   }
 
+
+  // Level d + 1 of the search from level d: the pair equation of equation
+  // order[d] in the current parameters t (u.t = c) removes one parameter,
+  // pivoting on its largest coefficient so that N's entries never grow (a
+  // dependent equation removes none, an inconsistent one ends the branch);
+  // the inherited conditions are rewritten in the remaining parameters and
+  // the conditions of the new support appended.  Returns false when the
+  // equation contradicts the ones fixed before.
+  bool descend(int depth) {
+    const Level& P = lv[depth];
+    Level& Q = lv[depth + 1];
+    const int k = order[depth];
+    const int p0 = chosen[k].first, p1 = chosen[k].second;
+    const int32_t* ap0 = exps + (size_t)(off[k] + p0) * n;
+    const int32_t* ap1 = exps + (size_t)(off[k] + p1) * n;
+    const int nf = P.nf;
+    u.assign(nf, 0.0);
+    double c = (double)(lift[off[k] + p0] - lift[off[k] + p1]);
+    for (int x = 0; x < n; ++x) {
+      const double e = (double)ap1[x] - ap0[x];
+      if (e == 0.0) continue;
+      c -= e * P.a0[x];
+      for (int q = 0; q < nf; ++q) u[q] += e * P.N[(size_t)x * nf + q];
+    }
+    int piv = -1;
+    double best = 1e-9;
+    for (int q = 0; q < nf; ++q)
+      if (fabs(u[q]) > best) { best = fabs(u[q]); piv = q; }
+    const int mg = (int)P.h2.size();
+    if (piv < 0) {
+      if (fabs(c) > 1e-7 * (1.0 + fabs(c))) return false;
+      Q.nf = nf;
+      Q.a0 = P.a0;
+      Q.N = P.N;
+      Q.G2 = P.G2;
+      Q.h2 = P.h2;
+    } else {
+      // t_piv = (c - sum_{q != piv} u_q t_q) / u_piv
+      const int nq = nf - 1;
+      const double up = u[piv], tp = c / up;
+      Q.nf = nq;
+      Q.a0.resize(n);
+      Q.N.resize((size_t)n * nq);
+      for (int x = 0; x < n; ++x) {
+        const double np = P.N[(size_t)x * nf + piv];
+        Q.a0[x] = P.a0[x] + np * tp;
+        for (int q = 0, j = 0; q < nf; ++q)
+          if (q != piv) Q.N[(size_t)x * nq + j++] = P.N[(size_t)x * nf + q] - np * (u[q] / up);
+      }
+      Q.G2.resize((size_t)mg * nq);
+      Q.h2.resize(mg);
+      for (int i = 0; i < mg; ++i) {
+        const double gp = P.G2[(size_t)i * nf + piv];
+        Q.h2[i] = P.h2[i] - gp * tp;
+        for (int q = 0, j = 0; q < nf; ++q)
+          if (q != piv) Q.G2[(size_t)i * nq + j++] = P.G2[(size_t)i * nf + q] - gp * (u[q] / up);
+      }
+    }
+    // the new support's conditions (a_l - a_p0).alpha >= w(p0) - w(l)
+    const int nq = Q.nf;
+    for (int l = 0; l < msz[k]; ++l) {
+      if (l == p0 || l == p1) continue;
+      const int32_t* al = exps + (size_t)(off[k] + l) * n;
+      double hh = (double)(lift[off[k] + p0] - lift[off[k] + l]);
+      const size_t base = Q.G2.size();
+      Q.G2.resize(base + nq, 0.0);
+      for (int x = 0; x < n; ++x) {
+        const double g = (double)al[x] - ap0[x];
+        if (g == 0.0) continue;
+        hh -= g * Q.a0[x];
+        for (int q = 0; q < nq; ++q) Q.G2[base + q] += g * Q.N[(size_t)x * nq + q];
+      }
+      Q.h2.push_back(hh);
+    }
+    return true;
+  }
+
   void leaf() {
     std::vector<int32_t> pairs(2 * n);
     for (int k = 0; k < n; ++k) {
@@ -378,7 +397,9 @@ struct Search {
       if (!compatible(k, i, depth)) continue;   // a pair of edges that cannot be lowest together
       chosen[k] = edges[k][i];
       pick[k] = i;
-      if (depth < 1 || feasible(depth + 1)) dfs(depth + 1);
+      if (!descend(depth)) continue;
+      // one equation with a lower edge is always feasible
+      if (depth < 1 || solve_t(lv[depth + 1].nf, lv[depth + 1].G2, lv[depth + 1].h2)) dfs(depth + 1);
       if (err) return;
     }
   }
@@ -443,6 +464,11 @@ extern "C" hpt_status hpt_mixed_cells(int32_t n, const int32_t* msz, const int32
         }
     }
   S.pick.assign(n, 0);
+  S.lv.resize(n + 1);
+  S.lv[0].nf = n;
+  S.lv[0].a0.assign(n, 0.0);
+  S.lv[0].N.assign((size_t)n * n, 0.0);
+  for (int x = 0; x < n; ++x) S.lv[0].N[(size_t)x * n + x] = 1.0;
   // fewest candidate edges first
   S.order.resize(n);
   for (int k = 0; k < n; ++k) S.order[k] = k;
