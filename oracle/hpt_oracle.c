@@ -33,7 +33,9 @@
  * Parity status: every function here is pinned by the CPU tests (finite
  * differences, the log-coordinate identity of Section 5, H(y,1) = F(y),
  * numpy.polyval for one variable, numpy.linalg.solve, closed-form paths,
- * the BKK root count, finite differences of the adjoint).
+ * the BKK root count, finite differences of the adjoint; the tolerance
+ * scales of ora_scale against the term magnitudes summed with numpy powers,
+ * with planted mistakes that the pin must reject).
  */
 #include <complex.h>
 #include <math.h>

@@ -132,3 +132,91 @@ def test_t_to_zero_leaves_the_cell(oracle_mod):
         b = (s.coeffs[o + pairs[k][0]] * np.prod(y ** a0, axis=1)
              + s.coeffs[o + pairs[k][1]] * np.prod(y ** a1, axis=1))
         assert np.allclose(H[:, k], b, rtol=1e-13, atol=1e-13)
+
+
+def _scale_numpy(s, texp, D, y, tau):
+    """The componentwise tolerance scales written out term by term with numpy
+    powers (no repeated multiplication, no logarithms): for every term
+    c y^a t^s of h_k, |c| |y^a| t^s for H, |c a_j| |y^(a - e_j)| t^s for
+    dH/dy_j and |c s| |y^a| t^s for dH/dtau (t = e^tau is real and positive)."""
+    p, n = y.shape
+    SH = np.zeros((p, n))
+    SHy = np.zeros((p, n, n))
+    SHt = np.zeros((p, n))
+    for k in range(n):
+        o = s.offsets[k]
+        for i in range(s.m[k]):
+            a = s.exponents[o + i].astype(float)
+            sx = texp[o + i] / D
+            c = abs(s.coeffs[o + i])
+            mono = np.abs(np.prod(y ** a[None, :], axis=1))
+            ts = np.exp(sx * tau)
+            SH[:, k] += c * mono * ts
+            SHt[:, k] += c * abs(sx) * mono * ts
+            for j in range(n):
+                if a[j] != 0:
+                    SHy[:, k, j] += c * abs(a[j]) * mono / np.abs(y[:, j]) * ts
+    return SH, SHy, SHt
+
+
+def _signed_system(seed, n, m):
+    """A system whose t-exponents take both signs, so that every |.| of the
+    scales matters."""
+    s = W.laurent_system(seed, n, m, -3, 3, 16)
+    rng = np.random.default_rng(seed + 1)
+    texp = rng.integers(-8, 9, size=s.M)
+    # coefficient magnitudes other than 1, so that |c| matters too
+    s = W.LaurentSystem(s.n, s.m, s.exponents, s.coeffs * rng.uniform(0.25, 4.0, s.M), s.lifting)
+    return s, texp
+
+
+def _check_scale(osys, s, texp, D, n, seed):
+    y, t = W.random_points(seed, 48, n)
+    tau = np.log(t)
+    SH, SHy, SHt = osys.scale(y, tau)
+    RH, RHy, RHt = _scale_numpy(s, texp, D, y, tau)
+    for got, ref in ((SH, RH), (SHy, RHy), (SHt, RHt)):
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref) / np.maximum(ref, 1e-300)) < 1e-12
+
+
+@pytest.mark.parametrize("n,m,D", [(2, 3, 1), (4, 5, 3), (7, 9, 2), (16, 32, 1)])
+def test_scale_is_the_sum_of_term_magnitudes(oracle_mod, n, m, D):
+    """ora_scale (the denominator of every parity tolerance: the sums of term
+    magnitudes of Section 5's extended Jacobian entries) against numpy."""
+    s, texp = _signed_system(30 + n, n, m)
+    _check_scale(oracle_mod.System(s, texp, D), s, texp, D, n, 5 + n)
+
+
+# Mistakes planted in a copy of the oracle's C core, each in the scale sums:
+# the pin above must reject every one of them.
+_SCALE_MUTANTS = [
+    ("dropped |s|", "ht += c * fabs(sexp) * mono * ts;", "ht += c * sexp * mono * ts;"),
+    ("dropped t^s", "h += c * mono * ts;\n            ht += c * fabs", "h += c * mono;\n            ht += c * fabs"),
+    ("dropped |a_j|", "SHy[k * n + j] += c * fabs((double)a[j])", "SHy[k * n + j] += c * ((double)a[j])"),
+    ("y^a for y^(a - e_j)", "cabs(powprod(n, y, yinv, a, j)) * ts;", "cabs(powprod(n, y, yinv, a, -1)) * ts;"),
+    ("|c| dropped", "const double c = cabs(coef_at(s, idx));", "const double c = 1.0;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", _SCALE_MUTANTS, ids=[m[0] for m in _SCALE_MUTANTS])
+def test_scale_pin_rejects_planted_mistakes(oracle_mod, tmp_path, name, old, new):
+    import ctypes
+    import subprocess
+    src = open(oracle_mod._SRC).read()
+    assert src.count(old) == 1, name
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(lib),
+                    str(mut), "-lm"], check=True)
+    mlib = ctypes.CDLL(str(lib))
+    mlib.ora_scale.restype = ctypes.c_int
+    saved = oracle_mod._lib
+    oracle_mod._lib = mlib
+    try:
+        s, texp = _signed_system(34, 4, 5)
+        with pytest.raises(AssertionError):
+            _check_scale(oracle_mod.System(s, texp, 3), s, texp, 3, 4, 9)
+    finally:
+        oracle_mod._lib = saved
