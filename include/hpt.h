@@ -362,7 +362,11 @@ hpt_status hpt_step_static(hpt_system sys, int64_t p, const hpt_paths* state, in
                            const hpt_params* params, void* stream);
 
 /* Whole tracks: start points y0_dev[p*n] complex128 at tau0 -> tau = 0, then an
- * FP64 Newton polish at t = 1 of the converged paths.  Writes x_out_dev[p*n]
+ * FP64 Newton polish at t = 1 of the converged paths.  Section 2.1, eq. (2):
+ * with t = e^tau the paths run over tau in (-inf, 0], starting from a tau0 < 0
+ * of large magnitude (tau0 = ln(eps0) / s_min, s_min the smallest positive
+ * t-exponent) and ending at tau = 0, where H(x, 1) = F(x) (Section 2, below
+ * eq. (1)); each step is the Euler-Newton step of Section 8.  Writes x_out_dev[p*n]
  * complex128, status_dev[p], steps_dev[p].  Synchronises the stream.  The
  * HPT_MIXED form runs as a one-system hpt_batch_track (created on first use
  * and kept with the handle), which compacts finished paths out of the
@@ -371,11 +375,17 @@ hpt_status hpt_track(hpt_system sys, int64_t p, const void* y0_dev, const hpt_pa
                      void* x_out_dev, int32_t* status_dev, int32_t* steps_dev, void* stream);
 
 /* FP64 Newton polish at t = 1 of x_dev[p*n] complex128 in place, for paths
- * whose status_dev entry is HPT_PATH_CONVERGED (status_dev NULL: all paths). */
+ * whose status_dev entry is HPT_PATH_CONVERGED (status_dev NULL: all paths).
+ * Section 2.3: repeated affine Newton directions, dH/dx dN = -H, at tau = 0,
+ * where H(x, 1) = F(x) is the target system (Section 2, below eq. (1));
+ * stops when |dN|_inf / max(1, |x|_inf) <= polish_tol or after polish_iters
+ * iterations. */
 hpt_status hpt_polish(hpt_system sys, int64_t p, void* x_dev, const int32_t* status_dev,
                       const hpt_params* params, void* stream);
 
-/* Implicit-function adjoint at solutions x_dev[p*n] complex128 of F = H(., 1):
+/* Implicit-function adjoint.  The paper has no counterpart of this entry
+ * point; it reuses the Jacobian dH/dx of Section 2.3 at tau = 0 (J = F_x,
+ * since H(x, 1) = F(x)).  At solutions x_dev[p*n] complex128 of F = H(., 1):
  * with J = F_x and gx_dev[p*n] = dL/dRe x + i dL/dIm x of a real loss L, solves
  * J^H lambda = gx per solution and writes gc_dev[M] complex128 =
  * -sum over solutions of lambda_k conj(x^{a_{k,i}}), the gradient of L with
