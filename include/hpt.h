@@ -200,7 +200,11 @@ hpt_status hpt_lift_exponents(int32_t n, const int32_t* support_sizes, const int
  * Inputs as hpt_lift_exponents (m_k >= 2).  Writes up to cap cells to
  * pairs_out[cap * 2n] (local indices, the hpt_cell PAIRS layout), the number
  * found to *ncells and sum |det V| to *mixed_volume (either may be NULL).
- * HPT_ERANGE when a determinant or the volume leaves the exact range. */
+ * HPT_ERANGE when a lifting value lies outside [-2^40, 2^40], or when a
+ * determinant, an exact cell test or the volume leaves the exact range.
+ * HPT_ENOTCELL when the lifting is not generic: some complete choice passed
+ * the FP64 search but failed the exact test (a tie with another point); the
+ * cells and volume written are then incomplete, so draw a new lifting. */
 hpt_status hpt_mixed_cells(int32_t n, const int32_t* support_sizes, const int32_t* exponents, const int64_t* lifting,
                            int64_t cap, int32_t* pairs_out, int64_t* ncells, int64_t* mixed_volume);
 

@@ -201,6 +201,7 @@ struct Search {
   i128 volume = 0;
   int32_t* out;
   hpt_status err = HPT_OK;
+  int64_t ties = 0;   // complete choices the FP64 search kept that fail the exact test
   // level d of the search (the first d equations of `order` fixed): the
   // inner normals alpha = a0 + N t, t in R^nf, that satisfy their pair
   // equations, and their other conditions G2 t >= h2 (nf values per row)
@@ -365,7 +366,15 @@ struct Search {
     cell.kind = HPT_CELL_PAIRS;
     cell.pairs = pairs.data();
     int64_t D = 0;
-    if (hpt_lift_exponents(n, msz.data(), exps, lift, &cell, nullptr, &D, nullptr, nullptr) != HPT_OK) return;
+    const hpt_status lrc = hpt_lift_exponents(n, msz.data(), exps, lift, &cell, nullptr, &D, nullptr, nullptr);
+    if (lrc == HPT_ENOTCELL) {   // a tie with another point (or det V = 0): the lifting is not generic
+      ++ties;
+      return;
+    }
+    if (lrc != HPT_OK) {
+      err = lrc;
+      return;
+    }
     // |det V| exactly (the pair matrix of a confirmed cell is nonsingular)
     std::vector<int64_t> V((size_t)n * n);
     for (int k = 0; k < n; ++k)
@@ -428,6 +437,10 @@ extern "C" hpt_status hpt_mixed_cells(int32_t n, const int32_t* msz, const int32
   }
   for (int64_t i = 0; i < M * n; ++i)
     if (exps[i] < -(1 << 20) || exps[i] > (1 << 20)) { set_error("exponent too large"); return HPT_ERANGE; }
+  // the exact confirmation's range (hpt_lift_exponents), checked before the
+  // search so that no lifting difference below can overflow
+  for (int64_t i = 0; i < M; ++i)
+    if (lifting[i] < -(1LL << 40) || lifting[i] > (1LL << 40)) { set_error("lifting too large"); return HPT_ERANGE; }
   S.exps = exps;
   S.lift = lifting;
   S.cap = cap;
@@ -478,5 +491,10 @@ extern "C" hpt_status hpt_mixed_cells(int32_t n, const int32_t* msz, const int32
   if (S.err) return S.err;
   if (ncells) *ncells = S.found;
   if (mixed_volume) *mixed_volume = (int64_t)S.volume;
+  if (S.ties) {
+    set_error("the lifting is not generic: %lld choices tie with another point; draw a new lifting",
+              (long long)S.ties);
+    return HPT_ENOTCELL;
+  }
   return HPT_OK;
 }

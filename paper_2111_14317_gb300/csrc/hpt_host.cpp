@@ -581,6 +581,9 @@ hpt_status binomial_setup(int32_t n, const int32_t* msz, const int32_t* exps, co
   std::vector<uint64_t> inv[2];
   uint64_t detp[2];
   uint64_t cand = ((uint64_t)1 << 62) - 1;
+  // every prime tried exceeds 2^61, so k of them dividing det V means
+  // |det V| >= 2^(61 k) or det V = 0; past Hadamard's bound it is 0
+  int nsing = 0;
   for (int t = 0; t < 2; ++t) {
     for (;; cand -= 2) {
       if (!is_prime64(cand)) continue;
@@ -615,7 +618,13 @@ hpt_status binomial_setup(int32_t n, const int32_t* msz, const int32_t* exps, co
           }
         }
       }
-      if (sing) continue;   // p divides det V: next prime
+      if (sing) {   // p divides det V: next prime, unless det V must be 0
+        if (61.0 * ++nsing > log2_h + 1.0) {
+          set_error("the cell's pair matrix is singular");
+          return HPT_ENOTCELL;
+        }
+        continue;
+      }
       pr[t] = p;
       detp[t] = det;
       inv[t].resize((size_t)n * n);

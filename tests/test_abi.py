@@ -166,3 +166,17 @@ def test_lift_singular_planted_cell(hpt):
     with pytest.raises(hpt.HptError) as ei:
         hpt.lift_exponents(s.n, s.m, ex, s.lifting, {"kind": "pairs", "pairs": pairs})
     assert ei.value.code == 5
+
+
+@pytest.mark.timeout(60)
+def test_binomial_start_singular_pairs_cell(hpt):
+    """A pairs cell whose pair matrix is singular although no row is zero
+    (rows (1, 0) and (2, 0)) is refused with HPT_ENOTCELL; every prime the
+    exact determinant tries divides 0, so the search for a usable prime has to
+    stop once det V = 0 is certain."""
+    exps = np.array([[0, 0], [1, 0], [0, 1],
+                     [0, 0], [2, 0], [1, 1]], dtype=np.int32)
+    coeffs = np.ones(6, complex)
+    with pytest.raises(hpt.HptError) as ei:
+        hpt.binomial_start(2, [3, 3], exps, coeffs, [[0, 1], [0, 1]])
+    assert ei.value.code == 5

@@ -88,3 +88,37 @@ def test_cap_and_count(hpt_host):
     assert pc.shape[0] == 3 and vol == mv
     full, _ = hpt_host.mixed_cells(s.n, s.m, s.exponents, s.lifting)
     assert _canon(pc) == sorted(_canon(full[:3]))
+
+
+def test_cells_refuse_a_lifting_beyond_the_exact_range(hpt_host):
+    """A lifting value outside [-2^40, 2^40] is refused up front (HPT_ERANGE),
+    not dropped cell by cell."""
+    s, _, _ = _util.first_generic(W.config2)
+    lift = s.lifting.copy()
+    lift[3] = (1 << 40) + 1
+    with pytest.raises(hpt_host.HptError) as ei:
+        hpt_host.mixed_cells(s.n, s.m, s.exponents, lift)
+    assert ei.value.code == 4
+
+
+def test_cells_report_a_non_generic_lifting(hpt_host):
+    """A lifting with an exact tie (a non-cell point lifted onto a cell's lower
+    facet) is reported (HPT_ENOTCELL, 'not generic') instead of returning a
+    short mixed volume; the oracle's brute force calls the same lifting
+    non-generic."""
+    s, cl, _ = _util.first_generic(W.config2)
+    pairs = cl[0]["pairs"]
+    D = cells.t_exponents(s, {"kind": "pairs", "pairs": pairs})["D"]
+    lift = s.lifting * D          # the cell's inner normal becomes integral
+    s2 = W.LaurentSystem(s.n, s.m, s.exponents, s.coeffs, lift)
+    te = cells.t_exponents(s2, {"kind": "pairs", "pairs": pairs})
+    assert te["D"] == 1
+    o = s.offsets[0]
+    i = [q for q in range(s.m[0]) if q not in pairs[0]][0]
+    lift[o + i] = te["beta_num"][0] - int(np.asarray(s.exponents[o + i], np.int64) @ np.asarray(te["alpha_num"]))
+    s3 = W.LaurentSystem(s.n, s.m, s.exponents, s.coeffs, lift)
+    with pytest.raises(cells.NonGeneric):
+        cells.mixed_cells(s3)
+    with pytest.raises(hpt_host.HptError) as ei:
+        hpt_host.mixed_cells(s3.n, s3.m, s3.exponents, s3.lifting)
+    assert ei.value.code == 5 and "not generic" in str(ei.value)
