@@ -44,8 +44,14 @@ FLOP_EXP_GEMM = 2 * (2 * N_VARS + 1) * N_VARS * M_PER_EQ          # 33,792
 FLOP_COEF_GEMM = 8 * (N_VARS + 2) * N_VARS * M_PER_EQ             # 73,728
 CEXP = N_VARS * M_PER_EQ                                           # 512
 n = N_VARS
-FLOP_LU = 8 * (n - 1) * n * (2 * n - 1) // 6 + 6 * n * (n - 1) // 2
-FLOP_SOLVE = 16 * n * n + 16 * n
+FLOP_LU = 8 * (n - 1) * n * (2 * n - 1) // 6 + 6 * n * (n - 1) // 2   # 10,640
+FLOP_SOLVE = 16 * n * n + 16 * n                                     # 4,352
+# path state read and written by a step (mixed form, complex64): y, y_acc,
+# dE_acc (n complex each), tau, dtau, tau_acc (FP64), five int32 counters
+STATE_BYTES = 2 * (3 * N_VARS * 8 + 3 * 8 + 5 * 4)                  # 856
+# MUFU issue slots per SM and clock (derived): ex2 32 (the doubled
+# special-function rate of this part), sin and cos 16 each
+MUFU_EX2_PER_CLK, MUFU_SINCOS_PER_CLK, FP32_LANES = 32, 16, 128
 
 
 def _dist():
@@ -266,6 +272,7 @@ def run_gpu(args):
         torch.cuda.empty_cache()
     if args.batch_systems > 0:
         out["batch"] = run_batch(args, dev)
+    out["sms"] = torch.cuda.get_device_properties(dev).multi_processor_count
     if args.workload == "all":
         out["track_adjoint"] = run_track_adjoint(args, dev)
         out["projective"] = run_projective(args, dev)
@@ -676,6 +683,85 @@ def run_start_points(args, dev):
             "host_one_core": {"points": int(nh), "ms": hms, "points_per_s": nh / (hms * 1e-3)}}
 
 
+def alu_peaks(sms, clk_mhz):
+    """Derived ALU rates at the maximum SM clock: FP32 FMA (TFLOP/s) and the
+    MUFU time of one path's complex exponentials (seconds per path, ex2 at
+    MUFU_EX2_PER_CLK and sin, cos at MUFU_SINCOS_PER_CLK per SM and clock)."""
+    hz = clk_mhz * 1e6
+    fp32 = sms * FP32_LANES * 2 * hz / 1e12
+    mufu_s_per_path = (CEXP / MUFU_EX2_PER_CLK + 2 * CEXP / MUFU_SINCOS_PER_CLK) / (sms * hz)
+    return fp32, mufu_s_per_path
+
+
+def step_roofline(mx, peaks, peak_kind, sms):
+    """Per-kernel and whole-step rooflines of the mixed step from the
+    algorithmic work of one path-step (dense within each equation's block):
+    GEMM flops on the tensor pipe, 3 MUFU operations per complex exponential,
+    LU + two solves + update on the FP32 pipe, the path state in HBM.  The
+    bound of a kernel is the pipe whose time is the largest; frac = that
+    time / the measured kernel time (achieved / peak of that pipe).  The
+    extended-Jacobian scratch between the kernels is not algorithmic work:
+    the DRAM bytes ncu measured are reported beside it as traffic_ratio."""
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak, mufu_path = alu_peaks(sms, clk)
+    bf16 = peaks["bf16_tflops"]
+    hbm = peaks["hbm_gbs"]
+    src = f"{peak_kind} (MEASURED_PEAKS.json, burst)"
+    derived = f"derived: {sms} SMs x {clk:.0f} MHz"
+    kinfo = {}
+    for name, (launches, msum) in mx["kernels"].items():
+        avg = msum / max(launches, 1) * 1e-3
+        ppl = PATHS * mx["steps"] / max(launches, 1)
+        rec = {"ms_avg": avg * 1e3, "launches": launches, "share": msum}
+        if name.startswith("eval_mixed"):
+            gemm = (FLOP_EXP_GEMM + FLOP_COEF_GEMM) * ppl
+            ops = 3 * CEXP * ppl                       # ex2, sin, cos per exponential
+            mufu_peak = 3 * CEXP / mufu_path / 1e12    # the mix's rate at the derived unit counts
+            rec.update({"bound": "alu", "pipe": "MUFU", "achieved": ops / avg / 1e12, "peak": mufu_peak,
+                        "unit": "Tops/s", "frac": ops / avg / 1e12 / mufu_peak,
+                        "peak_source": derived + f", ex2 {MUFU_EX2_PER_CLK}/clk/SM, sin/cos "
+                                                 f"{MUFU_SINCOS_PER_CLK}/clk/SM",
+                        "tensor": {"achieved": gemm / avg / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                                   "frac": gemm / avg / 1e12 / bf16, "peak_source": src}})
+        elif name.startswith("redo"):
+            # re-solves a device-side list of a few paths: no per-path figure
+            rec.update({"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None})
+        else:
+            fl = (FLOP_LU + FLOP_SOLVE) * ppl
+            ach = fl / avg / 1e12
+            rec.update({"bound": "alu", "pipe": "FP32 FMA", "achieved": ach, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": ach / fp32_peak, "peak_source": derived + ", 128 FP32 lanes"})
+        tr = _traffic(name)
+        rec["traffic"] = tr
+        if tr is not None:
+            rec["traffic_ratio"] = tr / (STATE_BYTES * ppl)
+        kinfo[name] = rec
+    total_k = sum(v["share"] for v in kinfo.values()) or 1.0
+    for v in kinfo.values():
+        v["share"] = v["share"] / total_k
+    dom = max(kinfo, key=lambda k: kinfo[k]["share"])
+    roof = {k: kinfo[dom].get(k) for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roof["kernel"] = dom
+    roof["pipe"] = kinfo[dom].get("pipe")
+    roof["peak_source"] = kinfo[dom].get("peak_source")
+    # whole step: T_roof = max over pipes of the step's algorithmic work / peak
+    t_pipe = {"tensor": (FLOP_EXP_GEMM + FLOP_COEF_GEMM) * PATHS / (bf16 * 1e12),
+              "MUFU": mufu_path * PATHS,
+              "FP32 FMA": (FLOP_LU + FLOP_SOLVE) * PATHS / (fp32_peak * 1e12),
+              "HBM": STATE_BYTES * PATHS / (hbm * 1e9)}
+    bind = max(t_pipe, key=t_pipe.get)
+    t_step = mx["ms_per_step"] * 1e-3
+    traffic = [v["traffic"] for v in kinfo.values() if v.get("traffic") is not None]
+    step_roof = {"t_roof_us": t_pipe[bind] * 1e6, "binding_pipe": bind,
+                 "t_pipe_us": {k: v * 1e6 for k, v in t_pipe.items()},
+                 "t_measured_us": t_step * 1e6, "frac": t_pipe[bind] / t_step,
+                 "algorithmic_bytes": STATE_BYTES * PATHS,
+                 "traffic_ratio": (sum(traffic) / (STATE_BYTES * PATHS)
+                                   if len(traffic) == len([v for v in kinfo.values() if v["bound"] != "latency"])
+                                   else None)}
+    return kinfo, roof, step_roof
+
+
 def cpu_baseline(seconds=12.0, max_paths=PATHS):
     """Times the oracle's step (as it stands) on growing slices of the same
     workload until about `seconds` of work is done."""
@@ -779,35 +865,7 @@ def main():
     mx, fp = out["mixed"], out["fp64"]
     value = whole_job_rate(ws, PATHS, mx["ms_per_step"] * 1e-3)
     fp_value = whole_job_rate(ws, PATHS, fp["ms_per_step"] * 1e-3)
-    # per-kernel roofline of the mixed step
-    kinfo = {}
-    for name, (launches, msum) in mx["kernels"].items():
-        avg = msum / max(launches, 1) * 1e-3
-        paths_per_launch = PATHS * mx["steps"] / max(launches, 1)
-        if name.startswith("eval_mixed"):
-            flops = (FLOP_EXP_GEMM + FLOP_COEF_GEMM) * paths_per_launch
-            ach = flops / avg / 1e12
-            kinfo[name] = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
-                           "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "ms_avg": avg * 1e3,
-                           "launches": launches, "share": msum}
-        elif name.startswith("redo"):
-            # re-solves a device-side list of a few paths: no per-path figure
-            kinfo[name] = {"bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
-                           "ms_avg": avg * 1e3, "launches": launches, "share": msum}
-        else:
-            byts = paths_per_launch * (N_VARS * (N_VARS + 2) * 8 + 3 * N_VARS * 8 * 2 + 3 * 8 * 2 + 5 * 4 * 2)
-            ach = byts / avg / 1e9
-            kinfo[name] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                           "frac": ach / peaks["hbm_gbs"], "ms_avg": avg * 1e3, "launches": launches,
-                           "share": msum}
-    total_k = sum(v["share"] for v in kinfo.values()) or 1.0
-    for v in kinfo.values():
-        v["share"] = v["share"] / total_k
-    dom = max(kinfo, key=lambda k: kinfo[k]["share"])
-    roof = {k: kinfo[dom][k] for k in ("bound", "achieved", "peak", "unit", "frac")}
-    roof["kernel"] = dom
-    roof["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json, burst)"
-    roof["traffic"] = _traffic(dom)
+    kinfo, roof, step_roof = step_roofline(mx, peaks, peak_kind, out["sms"])
     cpu_v, cores, sample = cpu_baseline(args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": mx["steps"],
@@ -822,6 +880,7 @@ def main():
                                                         for k, v in fp["kernels"].items()}},
         "mixed_vs_fp64": value / fp_value,
         "roofline": roof,
+        "step_roofline": step_roof,
         "kernels": kinfo,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": ws * PATHS / mx["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": mx["h2d"],

@@ -361,6 +361,7 @@ hpt_status hpt_step(hpt_system sys, int64_t p, const hpt_paths* state, int32_t n
  * device current) and caches it; make that first call before any stream
  * capture.  All calls on a device share the one array: calls whose GPU work
  * overlaps (other streams, other host threads) race and corrupt each other.
+ * Like hpt_step it runs in rounds of at most 65,536 paths.
  * Same arguments, results and error behaviour as hpt_step otherwise. */
 hpt_status hpt_step_static(hpt_system sys, int64_t p, const hpt_paths* state, int32_t nsteps,
                            const hpt_params* params, void* stream);

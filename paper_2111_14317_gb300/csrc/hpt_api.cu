@@ -7,14 +7,6 @@
 #include "hpt_internal.h"
 
 namespace hpt {
-namespace {
-
-// Paths per evaluate/solve round of hpt_step: the extended Jacobian of a
-// chunk (n (n+2) complex per path) stays resident in L2 between the two
-// kernels.  A multiple of the tensor-core tile.
-constexpr int64_t kChunk = 65536;
-
-inline size_t csize(const hpt_system s) { return s->prec == HPT_FP64 ? 16 : 8; }
 
 hpt_paths offset_paths(const hpt_paths& S, int64_t q0, int n, size_t cs) {
   hpt_paths o = S;
@@ -35,6 +27,10 @@ hpt_paths offset_paths(const hpt_paths& S, int64_t q0, int n, size_t cs) {
   if (S.hermite) o.hermite = S.hermite + q0;
   return o;
 }
+
+namespace {
+
+inline size_t csize(const hpt_system s) { return s->prec == HPT_FP64 ? 16 : 8; }
 
 cudaError_t eval_form(hpt_system s, int64_t p, const void* y, const double* tau, int tau_is_t,
                       const EvalOut& out, cudaStream_t st) {

@@ -77,6 +77,11 @@ __host__ __device__ inline size_t ext_index(int64_t path, int k, int u, int n) {
 }
 inline size_t ext_entries(int64_t p, int n) { return (size_t)((p + 127) / 128) * 128 * n * (n + 2); }
 
+// Paths per evaluate/solve round of hpt_step: the extended Jacobian of a
+// chunk (n (n+2) complex per path) stays resident in L2 between the two
+// kernels.  A multiple of the tensor-core tile.
+constexpr int64_t kChunk = 65536;
+
 // Positions of a launch and the paths behind them.  With every pointer null a
 // launch covers one system: position q is path q, every path has n
 // variables.  A many-systems launch walks a list of positions padded per
@@ -238,6 +243,8 @@ struct StepArgs {
 // Consolidated solve + update + step control.  T = double for HPT_FP64,
 // float for HPT_MIXED.
 cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st);
+// The state arrays of paths q0.. of S (nv complex entries per path of cs bytes).
+hpt_paths offset_paths(const hpt_paths& S, int64_t q0, int nv, size_t cs);
 // Many-systems pieces of the mixed step: the FP32 solve of one lane-group
 // shape (shape_of(n)) over the map's position range, appending FP64
 // re-solves to a.redo_list (the caller zeroes a.redo_count once per step),

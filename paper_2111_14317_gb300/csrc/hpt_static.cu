@@ -13,6 +13,7 @@
 // current) and cached.  All calls on a device share the array and it keeps
 // the last call's contents; the only value that must start at zero (the FP64
 // re-solve counter) is cleared by every solve launch.
+#include <algorithm>
 #include <mutex>
 
 #include "hpt_internal.h"
@@ -84,32 +85,39 @@ extern "C" hpt_status hpt_step_static(hpt_system s, int64_t p, const hpt_paths* 
   void* base = nullptr;
   hpt_status rc = static_scratch(dev, &base);
   if (rc) return rc;
+  // rounds of at most kChunk paths, as hpt_step runs them, so that no launch
+  // is larger than the ones hpt_step makes; the scratch holds one round
+  const int64_t chunk = std::min<int64_t>(p, kChunk);
   int32_t* redo_count = (int32_t*)base;
   int64_t* redo_list = (int64_t*)((char*)base + 256);
-  void* ext = (char*)base + 256 + ((size_t)p * sizeof(int64_t) + 255) / 256 * 256;
+  void* ext = (char*)base + 256 + ((size_t)chunk * sizeof(int64_t) + 255) / 256 * 256;
   cudaStream_t st = (cudaStream_t)stream;
   for (int r = 0; r < nsteps; ++r) {
-    EvalOut out;
-    out.ext = ext;
-    cudaError_t e = s->prec == HPT_FP64 ? launch_eval_fp64(s, p, S->y, S->tau, 0, out, st)
-                                        : launch_eval_mixed(s, p, S->y, S->tau, 0, out, st);
-    if (e != cudaSuccess) {
-      set_error("evaluation launch: %s", cudaGetErrorString(e));
-      return HPT_ECUDA;
-    }
-    StepArgs a;
-    a.n = n;
-    a.p = p;
-    a.ext = ext;
-    a.st = *S;
-    a.prm = *prm;
-    a.err = s->d_err;
-    a.redo_count = redo_count;
-    a.redo_list = redo_list;
-    e = launch_solve_update(s, a, st);
-    if (e != cudaSuccess) {
-      set_error("solve launch: %s", cudaGetErrorString(e));
-      return HPT_ECUDA;
+    for (int64_t q0 = 0; q0 < p; q0 += chunk) {
+      const int64_t cnt = std::min(chunk, p - q0);
+      const hpt_paths sub = offset_paths(*S, q0, n, cs);
+      EvalOut out;
+      out.ext = ext;
+      cudaError_t e = s->prec == HPT_FP64 ? launch_eval_fp64(s, cnt, sub.y, sub.tau, 0, out, st)
+                                          : launch_eval_mixed(s, cnt, sub.y, sub.tau, 0, out, st);
+      if (e != cudaSuccess) {
+        set_error("evaluation launch: %s", cudaGetErrorString(e));
+        return HPT_ECUDA;
+      }
+      StepArgs a;
+      a.n = n;
+      a.p = cnt;
+      a.ext = ext;
+      a.st = sub;
+      a.prm = *prm;
+      a.err = s->d_err;
+      a.redo_count = redo_count;
+      a.redo_list = redo_list;
+      e = launch_solve_update(s, a, st);
+      if (e != cudaSuccess) {
+        set_error("solve launch: %s", cudaGetErrorString(e));
+        return HPT_ECUDA;
+      }
     }
   }
   return HPT_OK;

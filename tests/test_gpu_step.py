@@ -210,9 +210,10 @@ def test_step_full_size_sampled(hpt, oracle_mod, prec):
         about 2e-4 of the term magnitudes and the solve factors the row- and
         column-equilibrated D_z H = H_y diag(y), which turns that into a
         relative error of at most about kappa_eq times as much, so
-        |d_N - d_N(oracle)| <= 1e-3 kappa_eq |d_N(oracle)| on 97% of the paths
-        (kappa_eq of the oracle's D_z H, equilibrated; at these random points
-        its median is about 50), and the median error is below 1e-2."""
+        |d_N - d_N(oracle)| <= 1e-3 kappa_eq |d_N(oracle)| on every sampled
+        path, the worst e / kappa_eq below 1e-4 (kappa_eq of the oracle's
+        D_z H, equilibrated; at these random points its median is about 50),
+        the median error below 1e-3, and at most two decisions differing."""
     sysm, alpha = W.config3(16, 32)
     cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
     te = cells.t_exponents(sysm, cell)
@@ -276,7 +277,15 @@ def test_step_full_size_sampled(hpt, oracle_mod, prec):
         e = np.abs(dg - do).max(-1) / np.abs(do).max(-1)
         ok = e <= 1e-3 * kappa
         q = np.quantile(e, [0.5, 0.9, 0.99])
-        assert ok.mean() >= 0.97 and q[0] < 1e-2, (ok.mean(), q, np.quantile(e / kappa, [0.5, 0.9, 0.99]))
+        worst = float(np.max(e / kappa))
+        print(f"mixed Newton directions: {int((~ok).sum())} of {ok.size} sampled paths beyond 1e-3 kappa_eq; "
+              f"worst e/kappa_eq {worst:.3e}; decisions differ on {int((~same).sum())}; "
+              f"e quantiles {q}")
+        # counted, not a fraction: no sampled path may miss the bound (the
+        # worst measured e/kappa_eq is about 4e-6), and at most two
+        # decisions may differ from the oracle's
+        assert int((~ok).sum()) == 0 and worst < 1e-4 and q[0] < 1e-3, (int((~ok).sum()), worst, q)
+        assert int((~same).sum()) <= 2, int((~same).sum())
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])

@@ -8,7 +8,8 @@ the library.  This file is collected last so that a stop at the first failure
 has already run every other test; it passes alone in a fresh process and after
 the others.  Checked through the C ABI: two calls in a row give the same
 states as hpt_step (bit for bit: same kernels on the same inputs), in both
-forms, and a batch over the array's limit is refused with HPT_ERANGE.
+forms, at n = 16 within one round and at n = 2 over two rounds of 65,536
+paths, and a batch over the array's limit is refused with HPT_ERANGE.
 """
 import numpy as np
 import pytest
@@ -50,6 +51,27 @@ def test_static_step_matches_step(hpt, prec):
         for f in FIELDS:
             a, b = getattr(ref, f), getattr(got, f)
             assert torch.equal(a, b), f
+    assert h.device_error() == 0
+    h.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_static_step_matches_step_beyond_one_round(hpt, prec):
+    """At n = 2 the array holds far more than the 65,536 paths of one round
+    of hpt_step; 70,001 paths run as two rounds, exactly as in hpt_step."""
+    s = W.config1(0)
+    cl, _ = cells.mixed_cells(s)
+    h = hpt.System.from_laurent(s, {"kind": "pairs", "pairs": cl[0]["pairs"]}, prec)
+    y, t = W.random_points(6, 70001, 2)
+    prm = hpt.Params(tol_accept=1e-3 if prec == 0 else 3e-3)
+    ref = _state(hpt, h, y, t, prec)
+    got = _state(hpt, h, y, t, prec)
+    for _ in range(2):
+        h.step(ref, 1, prm)
+        h.step_static(got, 1, prm)
+        torch.cuda.synchronize()
+        for f in FIELDS:
+            assert torch.equal(getattr(ref, f), getattr(got, f)), f
     assert h.device_error() == 0
     h.close()
 
