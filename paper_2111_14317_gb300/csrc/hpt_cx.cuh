@@ -118,6 +118,30 @@ __device__ __forceinline__ void st(void* base, size_t idx, cx<T> v) {
   ((typename cplx_t<T>::type*)base)[idx] = w;
 }
 
+// Complex FP32 values as packed pairs (re in the low, im in the high half)
+// for the paired FP32 instructions of this architecture: one instruction
+// rounds each half exactly as the scalar operation would.
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t fma_x2(uint64_t a, uint64_t b, uint64_t c) {   // a * b + c
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul_x2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // Lanes of the calling thread's G-lane group within its warp.
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {

@@ -325,10 +325,42 @@ __device__ __forceinline__ bool group_solve(int n, PathRows<T, G, R>& P, cx<T> (
 // and two accepted points the cubic Hermite interpolant through them; the
 // point being replaced by an accept is kept in the state's *_prev arrays).
 // TS is the state precision; lane l handles the variables l + G s.
+// The state a step reads, loaded ahead of the solve so that its loads are in
+// flight together with the Jacobian's (the Hermite predictor's extra fields
+// are read only when used).
+template <typename TS, int R>
+struct StepState {
+  cx<TS> y[R], yacc[R], dEacc[R];
+  double tau, dtau, tauacc;
+  int32_t steps, accepts, rejects, streak;
+};
+
+template <typename TS, int G, int R>
+__device__ __forceinline__ void load_step_state(int n, int64_t path, size_t vbase, const hpt_paths& S,
+                                                StepState<TS, R>& Q) {
+  const int lane = threadIdx.x & (G - 1);
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int j = lane + G * s;
+    const bool mine = j < n;
+    const size_t vi = vbase + j;
+    Q.y[s] = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
+    Q.yacc[s] = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
+    Q.dEacc[s] = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
+  }
+  Q.tau = S.tau[path];
+  Q.dtau = S.dtau[path];
+  Q.tauacc = S.tau_acc[path];
+  Q.steps = S.steps[path];
+  Q.accepts = S.accepts[path];
+  Q.rejects = S.rejects[path];
+  Q.streak = S.streak[path];
+}
+
 template <typename TS, int G, int R>
 __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, int32_t status, bool ok,
                                             const cx<TS> (&wE)[R], const cx<TS> (&wN)[R], const hpt_paths& S,
-                                            const hpt_params& prm) {
+                                            const hpt_params& prm, const StepState<TS, R>& Q) {
   const int lane = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
   cx<TS> y[R], yacc[R], dEacc[R], xE[R], xN[R];
@@ -338,10 +370,9 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
   for (int s = 0; s < R; ++s) {
     const int j = lane + G * s;
     const bool mine = j < n;
-    const size_t vi = vbase + j;
-    y[s] = mine ? ld<TS>(S.y, vi) : mk<TS>(0, 0);
-    yacc[s] = mine ? ld<TS>(S.y_acc, vi) : mk<TS>(0, 0);
-    dEacc[s] = mine ? ld<TS>(S.dE_acc, vi) : mk<TS>(0, 0);
+    y[s] = Q.y[s];
+    yacc[s] = Q.yacc[s];
+    dEacc[s] = Q.dEacc[s];
     // the scratch holds D_z H = H_y diag(y): the solve gave diag(1/y) times
     // the directions
     xE[s] = cmul(y[s], wE[s]);
@@ -359,9 +390,8 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
     nd = t_max(nd, __shfl_xor_sync(gmask, nd, o, G));
   }
   const bool bad = !(ok && solfin);
-  double tau = S.tau[path], dtau = S.dtau[path], tauacc = S.tau_acc[path];
-  int32_t steps = S.steps[path] + 1, accepts = S.accepts[path], rejects = S.rejects[path],
-          streak = S.streak[path];
+  double tau = Q.tau, dtau = Q.dtau, tauacc = Q.tauacc;
+  int32_t steps = Q.steps + 1, accepts = Q.accepts, rejects = Q.rejects, streak = Q.streak;
   const TS err = nd / t_max(TS(1), ny);
   const bool accept = !bad && err <= (TS)prm.tol_accept;
   const bool herm = prm.predictor == 1;
@@ -489,6 +519,15 @@ __device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, i
   }
 }
 
+template <typename TS, int G, int R>
+__device__ __forceinline__ void update_path(int n, int64_t path, size_t vbase, int32_t status, bool ok,
+                                            const cx<TS> (&wE)[R], const cx<TS> (&wN)[R], const hpt_paths& S,
+                                            const hpt_params& prm) {
+  StepState<TS, R> Q;
+  load_step_state<TS, G, R>(n, path, vbase, S, Q);
+  update_path<TS, G, R>(n, path, vbase, status, ok, wE, wN, S, prm, Q);
+}
+
 __device__ __forceinline__ int64_t pm_path(const PathMap& m, int64_t q) { return m.list ? m.list[q] : q; }
 __device__ __forceinline__ int pm_n(const PathMap& m, int64_t q, int n) {
   return m.sys_n ? m.sys_n[m.tile_sys[q >> 7]] : n;
@@ -538,6 +577,310 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
     return;
   }
   update_path<T, G, R>(n, path, vbase, status, ok, xE, xN, S, prm);
+}
+
+// FP32 step of one system with n <= G R by Gauss-Jordan elimination.  A
+// G-lane group owns one path as in group_solve: lane l holds rows l + G s,
+// s < R, of [D_z H | -H_tau | -H] in registers, here as packed FP32 pairs
+// (rows >= n are zero).  After the exact power-of-two row and column
+// equilibration of group_solve (the column magnitudes go through shared
+// memory, one reduction per column instead of a butterfly per column), each
+// column is eliminated from every other row, the rows already used as pivots
+// included: group_solve updates those rows too, with zero multipliers, so
+// the elimination costs the same and no back substitution follows.  At the
+// end row i holds only its pivot u_i and its two right-hand sides, and the
+// unknowns of the column it pivoted are b_i / u_i.  The pivot of a column is
+// the one of group_solve (largest |.|^2 among the unused rows, ties to the
+// lowest row), so the pivots, the condition proxy and the FP64 re-solve
+// list are those of the LU form.  The owner writes the live part of the
+// pivot row once to shared memory, each entry as (re, im, im, re): a row's
+// update a - l u is then two paired FMAs on one 16-byte load shared by the
+// R rows of a lane.  Rows are shifted as in group_solve (column j is always
+// register 0).
+template <int NC>
+struct GjSmem {
+  union {
+    float cm[NC][NC + 4];       // the rows' entry magnitudes, read back by column
+    struct {
+      float4 piv[2][NC + 3];    // pivot rows of alternate steps: [0] the pivot, [1..NC) entries, [NC], [NC+1] bE, bN
+      float4 x[NC];             // the solutions by column: (xE.re, xE.im, xN.re, xN.im)
+    } e;
+  } u;
+  float dcol[NC];               // the column scales
+};
+// Per-group stride in words, = G (mod 32): the column reads of cm and the
+// broadcast pivot-row reads of the groups of a warp fall on distinct banks.
+template <int G, int NC>
+struct GjLayout {
+  static constexpr int raw = (int)(sizeof(GjSmem<NC>) / 4);
+  static constexpr int words = (raw - G + 31) / 32 * 32 + G;
+  static constexpr int bytes = words * 4;
+};
+
+__device__ __forceinline__ float cmag2(uint64_t v) {
+  const float2 f = upk2(v);
+  return fmaxf(fabsf(f.x), fabsf(f.y));
+}
+
+// One path (position q of the scratch, laid out for nmax variables) for
+// every lane of its group; call with the whole warp converged.  Returns with
+// the state updated, or the position queued for the FP64 re-solve.
+template <int G, int R>
+__device__ __forceinline__ void gj_path(int n, int nmax, int64_t q, int64_t path, size_t vbase, int32_t status,
+                                        const float2* __restrict__ ext, const hpt_paths& S, const hpt_params& prm,
+                                        int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list,
+                                        unsigned char* smem) {
+  constexpr int NC = G * R;
+  const int lane = threadIdx.x & (G - 1);
+  const bool valid = status == HPT_PATH_ACTIVE;
+  GjSmem<NC>& sh = *(GjSmem<NC>*)(smem + (threadIdx.x / G) * GjLayout<G, NC>::bytes);
+  const unsigned gmask = group_mask<G>();
+
+  // rows lane + G s and their right-hand sides
+  uint64_t a[R][NC], bE[R], bN[R];
+  float chk = 0.f;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int r = lane + G * s;
+    const bool have = valid && r < n;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float2 v = make_float2(0.f, 0.f);
+      if (have && c < n) v = ext[ext_index(q, r, c, nmax)];
+      a[s][c] = pk2(v.x, v.y);
+      chk += fabsf(v.x) + fabsf(v.y);
+    }
+    float2 ht = make_float2(0.f, 0.f), h = make_float2(0.f, 0.f);
+    if (have) {
+      ht = ext[ext_index(q, r, n, nmax)];
+      h = ext[ext_index(q, r, n + 1, nmax)];
+    }
+    bE[s] = pk2(-ht.x, -ht.y);
+    bN[s] = pk2(-h.x, -h.y);
+    chk += fabsf(ht.x) + fabsf(ht.y) + fabsf(h.x) + fabsf(h.y);
+  }
+  // a sum of magnitudes is finite iff every entry is
+  const bool fin = (__ballot_sync(0xffffffffu, isfinite(chk)) & gmask) == gmask;
+
+  // equilibration: each row, then the columns, by exact powers of two
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) m = fmaxf(m, cmag2(a[s][c]));
+    const float dr = pow2_inv(m);
+    const uint64_t DR = pk2(dr, dr);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a[s][c] = mul_x2(a[s][c], DR);
+    bE[s] = mul_x2(bE[s], DR);
+    bN[s] = mul_x2(bN[s], DR);
+#pragma unroll
+    for (int c = 0; c < NC; c += 4)
+      *(float4*)&sh.u.cm[lane + G * s][c] =
+          make_float4(cmag2(a[s][c]), cmag2(a[s][c + 1]), cmag2(a[s][c + 2]), cmag2(a[s][c + 3]));
+  }
+  __syncwarp();
+  float dc[R];   // the scales of columns lane + G s
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    float mc = 0.f;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) mc = fmaxf(mc, sh.u.cm[r][lane + G * s]);
+    dc[s] = pow2_inv(mc);   // 1 for a zero column
+    sh.dcol[lane + G * s] = dc[s];
+  }
+  __syncwarp();   // every column magnitude read before the pivot rows reuse the space
+#pragma unroll
+  for (int c = 0; c < NC; c += 4) {
+    const float4 d = *(const float4*)&sh.dcol[c];
+    const uint64_t D0 = pk2(d.x, d.x), D1 = pk2(d.y, d.y), D2 = pk2(d.z, d.z), D3 = pk2(d.w, d.w);
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      a[s][c] = mul_x2(a[s][c], D0);
+      a[s][c + 1] = mul_x2(a[s][c + 1], D1);
+      a[s][c + 2] = mul_x2(a[s][c + 2], D2);
+      a[s][c + 3] = mul_x2(a[s][c + 3], D3);
+    }
+  }
+
+  // elimination
+  bool used[R];
+  int step[R];
+  uint64_t piv[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    used[s] = lane + G * s >= n;
+    step[s] = 0;
+    piv[s] = pk2(1.f, 0.f);
+  }
+  bool ok = true;
+  float pmax = 0.f, pmin = 0.f;   // extreme |u_jj|^2
+#pragma unroll 1
+  for (int j = 0; j < n; ++j) {
+    float4* buf = sh.u.e.piv[j & 1];
+    unsigned key = 0u;
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const float2 v = upk2(a[s][0]);
+      key = max(key, pivot_key<float>(v.x * v.x + v.y * v.y, used[s], lane + G * s));
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o, G));
+    const int br = 31 - (int)(key & 31u);
+    const int bs = br / G;
+    const bool owner = lane == (br & (G - 1));
+    const int lim = n - 1 - j;   // live registers 1..lim
+    if (owner) {
+      // the owner's slot chosen entry by entry (a per-slot conditional store
+      // would be turned into a dynamically indexed, local-memory row)
+      uint64_t v0 = a[0][0];
+#pragma unroll
+      for (int s = 1; s < R; ++s) v0 = bs == s ? a[s][0] : v0;
+      const float2 w0 = upk2(v0);
+      buf[0] = make_float4(w0.x, w0.y, 0.f, 0.f);
+#pragma unroll
+      for (int c0 = 1; c0 < NC; c0 += 4) {
+        if (c0 <= lim) {
+#pragma unroll
+          for (int c = c0; c < c0 + 4 && c < NC; ++c) {
+            uint64_t v = a[0][c];
+#pragma unroll
+            for (int s = 1; s < R; ++s) v = bs == s ? a[s][c] : v;
+            const float2 w = upk2(v);
+            buf[c] = make_float4(w.x, w.y, w.y, w.x);
+          }
+        }
+      }
+      uint64_t e = bE[0], f = bN[0];
+#pragma unroll
+      for (int s = 1; s < R; ++s) {
+        e = bs == s ? bE[s] : e;
+        f = bs == s ? bN[s] : f;
+      }
+      const float2 we = upk2(e), wf = upk2(f);
+      buf[NC] = make_float4(we.x, we.y, we.y, we.x);
+      buf[NC + 1] = make_float4(wf.x, wf.y, wf.y, wf.x);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        if (bs == s) {
+          used[s] = true;
+          step[s] = j;
+          piv[s] = a[s][0];
+        }
+      }
+    }
+    __syncwarp();
+    const float4 pv = buf[0];
+    const float p2 = pv.x * pv.x + pv.y * pv.y;
+    if (!(p2 > 0.f) || !isfinite(p2)) ok = false;
+    pmax = j == 0 ? p2 : fmaxf(pmax, p2);
+    pmin = j == 0 ? p2 : fminf(pmin, p2);
+    const float rp = t_rcp(p2);   // one reciprocal per pivot, shared by all rows
+    // multipliers a_s0 / pivot; the pivot row itself keeps its values
+    uint64_t NL[R], LS[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      const float2 v = upk2(a[s][0]);
+      float lr = (v.x * pv.x + v.y * pv.y) * rp, li = (v.y * pv.x - v.x * pv.y) * rp;
+      if (owner && bs == s) {
+        lr = 0.f;
+        li = 0.f;
+      }
+      NL[s] = pk2(-lr, -lr);
+      LS[s] = pk2(li, -li);
+    }
+    // shifted update a[c-1] = a[c] - l u over the live width, in chunks of
+    // four columns behind one warp-uniform branch each (the columns of the
+    // last chunk beyond the live width are never read again)
+#pragma unroll
+    for (int c0 = 1; c0 < NC; c0 += 4) {
+      if (c0 <= lim) {
+#pragma unroll
+        for (int c = c0; c < c0 + 4 && c < NC; ++c) {
+          const float4 u = buf[c];
+          const uint64_t U = pk2(u.x, u.y), US = pk2(u.z, u.w);
+#pragma unroll
+          for (int s = 0; s < R; ++s) a[s][c - 1] = fma_x2(LS[s], US, fma_x2(NL[s], U, a[s][c]));
+        }
+      }
+    }
+    {
+      const float4 u = buf[NC], v = buf[NC + 1];
+      const uint64_t U = pk2(u.x, u.y), US = pk2(u.z, u.w), V = pk2(v.x, v.y), VS = pk2(v.z, v.w);
+#pragma unroll
+      for (int s = 0; s < R; ++s) {
+        bE[s] = fma_x2(LS[s], US, fma_x2(NL[s], U, bE[s]));
+        bN[s] = fma_x2(LS[s], VS, fma_x2(NL[s], V, bN[s]));
+      }
+    }
+  }
+  // row i < n now holds its pivot and right-hand sides: the unknowns of the
+  // column it pivoted, put in column order through shared memory
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    if (lane + G * s < n) {
+      const float2 u = upk2(piv[s]), e = upk2(bE[s]), f = upk2(bN[s]);
+      const float ru = t_rcp(u.x * u.x + u.y * u.y);
+      sh.u.e.x[step[s]] = make_float4((e.x * u.x + e.y * u.y) * ru, (e.y * u.x - e.x * u.y) * ru,
+                                      (f.x * u.x + f.y * u.y) * ru, (f.y * u.x - f.x * u.y) * ru);
+    }
+  }
+  __syncwarp();
+  cx<float> wE[R], wN[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    wE[s] = mk<float>(0.f, 0.f);
+    wN[s] = mk<float>(0.f, 0.f);
+    if (lane + G * s < n) {
+      const float4 v = sh.u.e.x[lane + G * s];
+      wE[s] = mk<float>(v.x * dc[s], v.y * dc[s]);
+      wN[s] = mk<float>(v.z * dc[s], v.w * dc[s]);
+    }
+  }
+  const float cond = pmin > 0.f ? sqrtf(pmax / pmin) : INFINITY;
+  ok = ok && fin;
+  __syncwarp();   // the group's shared memory is reused by its next path
+  if (!valid) return;   // group-uniform; only group-masked shuffles below
+  if (redo_list && ok && !(cond <= (float)prm.cond_max)) {
+    if (lane == 0) redo_list[atomicAdd(redo_count, 1)] = q;
+    return;
+  }
+  update_path<float, G, R>(n, path, vbase, status, ok, wE, wN, S, prm);
+}
+
+template <int G, int R>
+__global__ void __launch_bounds__(kSolveThreads, R == 1 ? 6 : 4)
+gj_update_kernel(int n, int64_t p, const float2* __restrict__ ext, hpt_paths S, hpt_params prm,
+                 int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t path = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int32_t status = path < p ? S.status[path] : -1;
+  if (!__any_sync(0xffffffffu, status == HPT_PATH_ACTIVE)) return;   // warp-uniform exit
+  gj_path<G, R>(n, n, path, path, (size_t)path * n, status, ext, S, prm, redo_count, redo_list, smem);
+}
+
+// The same over a position map (many systems), persistent as
+// solve_update_map_kernel: a warp's 32/G consecutive positions lie in one
+// 128-position tile, so n is warp-uniform.
+template <int G, int R>
+__global__ void __launch_bounds__(kSolveThreads, R == 1 ? 6 : 4)
+gj_update_map_kernel(int n0, int64_t p, const float2* __restrict__ ext, hpt_paths S, hpt_params prm,
+                     int32_t* __restrict__ redo_count, int64_t* __restrict__ redo_list, PathMap pm) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int per_warp = 32 / G;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int g = (threadIdx.x & 31) / G;
+  const int64_t npos = pm_count(pm, p);
+  for (int64_t base = pm_begin(pm) + warp_id * per_warp; base < npos; base += nwarps * per_warp) {
+    const int64_t q = base + g;
+    const int n = pm_n(pm, base, n0);
+    const int64_t path = q < npos ? pm_path(pm, q) : -1;
+    const int32_t status = path >= 0 ? S.status[path] : -1;
+    if (!__any_sync(0xffffffffu, status == HPT_PATH_ACTIVE)) continue;   // warp-uniform skip
+    const size_t vbase = status == HPT_PATH_ACTIVE ? pm_vbase(pm, path, n) : 0;
+    gj_path<G, R>(n, pm.nmax, q, path, vbase, status, ext, S, prm, redo_count, redo_list, smem);
+  }
 }
 
 // The same over a position map (many systems).  Persistent: the warps loop
@@ -912,6 +1255,27 @@ cudaError_t launch_solve_shape(const StepArgs& a, int32_t* rc, int64_t* rl, cuda
   return cudaGetLastError();
 }
 
+// FP32 Gauss-Jordan solve + update (n <= 16: (G, R) = (8, 1) or (8, 2)), one
+// system or a position map.
+template <int G, int R>
+cudaError_t launch_gj(const StepArgs& a, cudaStream_t st) {
+  const int smem = (kSolveThreads / G) * GjLayout<G, G * R>::bytes;
+  if (!a.map.list) {
+    cudaError_t e = set_smem(gj_update_kernel<G, R>, smem);
+    if (e != cudaSuccess) return e;
+    gj_update_kernel<G, R><<<blocks_for(a.p * G, kSolveThreads), kSolveThreads, smem, st>>>(
+        a.n, a.p, (const float2*)a.ext, a.st, a.prm, a.redo_count, a.redo_list);
+    return cudaGetLastError();
+  }
+  cudaError_t e = set_smem(gj_update_map_kernel<G, R>, smem);
+  if (e != cudaSuccess) return e;
+  PathMap pm = a.map;
+  if (!pm.nmax) pm.nmax = a.n;
+  gj_update_map_kernel<G, R><<<solve_grid(a.p, G), kSolveThreads, smem, st>>>(
+      a.n, a.p, (const float2*)a.ext, a.st, a.prm, a.redo_count, a.redo_list, pm);
+  return cudaGetLastError();
+}
+
 template <int G, int R>
 cudaError_t launch_redo_shape(const StepArgs& a, cudaStream_t st) {
   const int smem = (kSolveThreads / G) * GroupSmem<double, G * R>::bytes;
@@ -970,10 +1334,16 @@ cudaError_t launch_solve_update(hpt_system s, const StepArgs& a, cudaStream_t st
   }
   e = cudaMemsetAsync(a.redo_count, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  int pi = prof_begin(s, "solve_update_fp32", st);
-  e = shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
-    : shape == 1 ? launch_solve_shape<float, 8, 2>(a, a.redo_count, a.redo_list, st)
-                 : launch_solve_shape<float, 32, 1>(a, a.redo_count, a.redo_list, st);
+  int pi;
+  if (!a.map.list && shape <= 1) {   // one system, n <= 16: Gauss-Jordan
+    pi = prof_begin(s, "solve_gj_fp32", st);
+    e = shape == 0 ? launch_gj<8, 1>(a, st) : launch_gj<8, 2>(a, st);
+  } else {
+    pi = prof_begin(s, "solve_update_fp32", st);
+    e = shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
+      : shape == 1 ? launch_solve_shape<float, 8, 2>(a, a.redo_count, a.redo_list, st)
+                   : launch_solve_shape<float, 32, 1>(a, a.redo_count, a.redo_list, st);
+  }
   prof_end(s, pi, st);
   if (e != cudaSuccess) return e;
   // FP64 re-solves: a fixed grid that loops over the device-side list
@@ -998,8 +1368,8 @@ cudaError_t launch_newton_map(int shape, int64_t cap, const void* ext, void* x, 
 
 cudaError_t launch_solve_fp32_shape(int shape, const StepArgs& a, cudaStream_t st) {
   if (a.p <= 0) return cudaSuccess;
-  return shape == 0 ? launch_solve_shape<float, 8, 1>(a, a.redo_count, a.redo_list, st)
-       : shape == 1 ? launch_solve_shape<float, 8, 2>(a, a.redo_count, a.redo_list, st)
+  return shape == 0 ? launch_gj<8, 1>(a, st)
+       : shape == 1 ? launch_gj<8, 2>(a, st)
        : shape == kShape8x3 ? launch_solve_shape<float, 8, 3>(a, a.redo_count, a.redo_list, st)
                     : launch_solve_shape<float, 32, 1>(a, a.redo_count, a.redo_list, st);
 }

@@ -321,3 +321,48 @@ def test_step_control_schedule(hpt, prec):
             assert r["status"][0] == hpt.ACTIVE and abs(r["dtau"][0] - dts[k]) < 1e-15 and r["tau"][0] <= 0.0
     assert r["status"][0] == hpt.CONVERGED and r["tau_acc"][0] == 0.0
     assert h.device_error() == 0
+
+
+@pytest.mark.parametrize("n,m", [(1, 3), (3, 6), (8, 12), (9, 14), (13, 20), (16, 32)])
+def test_mixed_step_newton_directions(hpt, oracle_mod, n, m):
+    """The FP32 step of one system for each lane-group shape of its solve
+    (n <= 8: 8 lanes, n <= 16: 16 lanes, one row per lane) on 3,000 random
+    points (23 full tiles and a ragged tail): from a state with no accepted
+    point every active path's new y_acc is y + d_N, so its Newton direction is
+    compared with the oracle's from the same (complex64) point, within
+    1e-3 kappa_eq (kappa_eq: condition number of the oracle's row- and
+    column-equilibrated D_z H), and the statuses agree."""
+    sysm = W.laurent_system(70 + n, n, m, -3, 3, 64, nnz=min(4, n))
+    alpha = W.random_alpha(70 + n, n)
+    cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
+    te = cells.t_exponents(sysm, cell)
+    osys = oracle_mod.System(sysm, te["e"], te["D"])
+    p = 3000
+    y, t = W.random_points(11, p, n)
+    y = y.astype(np.complex64).astype(np.complex128)
+    h = hpt.System.from_laurent(sysm, cell, hpt.HPT_MIXED)
+    st = _bench_like_state(hpt, y, t, 1, 0)
+    h.step(st, 1, hpt.Params(tol_accept=3e-3))
+    torch.cuda.synchronize()
+    g = {k: v.numpy() for k, v in st.to_host().items()}
+    o = oracle_mod.PathState.start(y, 0.0, 0.01)
+    o.tau[:] = np.log(t)
+    o.tauacc[:] = o.tau
+    osys.step(oracle_mod.Params(tol_accept=3e-3), o, 1)
+    same = g["status"] == o.status
+    assert int((~same).sum()) <= 3, int((~same).sum())
+    act = same & (o.status == oracle_mod.ACTIVE)
+    assert act.mean() > 0.9
+    dg = g["y_acc"][act] - y[act]
+    do = o.yacc[act] - y[act]
+    _, Hy, _ = osys.eval(y[act], np.log(t[act]))
+    A = Hy * y[act][:, None, :]
+    A = A / np.max(np.abs(A), axis=2, keepdims=True)
+    A = A / np.max(np.abs(A), axis=1, keepdims=True)
+    kappa = np.linalg.cond(A)
+    e = np.abs(dg - do).max(-1) / np.abs(do).max(-1)
+    miss = int((e > 1e-3 * kappa).sum())
+    print(f"n={n}: {miss} of {e.size} paths beyond 1e-3 kappa_eq, worst e/kappa_eq "
+          f"{float(np.max(e / kappa)):.3e}, median e {float(np.median(e)):.2e}")
+    assert miss == 0 and float(np.median(e)) < 1e-3
+    h.close()
