@@ -19,8 +19,9 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhpt.so")
 
 SOURCES = ["hpt_host.cpp", "hpt_cells.cpp", "hpt_eval64.cu", "hpt_mixed.cu", "hpt_solve.cu", "hpt_api.cu", "hpt_static.cu",
-           "hpt_batch.cu", "hpt_qr.cu", "hpt_start.cu"]
-HEADERS = [os.path.join(CSRC, "hpt_internal.h"), os.path.join(CSRC, "hpt_cx.cuh"), os.path.join(INCLUDE, "hpt.h")]
+           "hpt_batch.cu", "hpt_qr.cu", "hpt_start.cu", "hpt_evalpipe.cu"]
+HEADERS = [os.path.join(CSRC, "hpt_internal.h"), os.path.join(CSRC, "hpt_cx.cuh"), os.path.join(CSRC, "hpt_tc.cuh"),
+           os.path.join(INCLUDE, "hpt.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

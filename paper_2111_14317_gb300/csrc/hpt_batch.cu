@@ -555,6 +555,9 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
     mx.NJ = std::max(mx.NJ, h->ml.NJ);
     mx.KC = std::max(mx.KC, h->ml.KC);
     mx.chunk_bytes = std::max(mx.chunk_bytes, h->ml.chunk_bytes);
+    mx.off_bhi = std::max(mx.off_bhi, h->ml.off_bhi);     // the largest exponent part
+    mx.off_aint = std::max(mx.off_aint, h->ml.off_aint);   // nonzero: some system has large exponents
+    mx.off_bigm = std::max(mx.off_bigm, h->ml.off_bigm);
     b->tmem_cols = std::max(b->tmem_cols, h->ml.tmem_cols);
     b->nmax = std::max(b->nmax, h->n);
     // evaluation work of one tile: n equations x (exponent + coefficient GEMM + exp)

@@ -337,21 +337,27 @@ static void split2(double v, uint16_t& hi, uint16_t& lo) {
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-static MixedLayout mixed_layout(int n, int max_m) {
+static MixedLayout mixed_layout(int n, int max_m, bool big) {
   MixedLayout L;
   L.MP = round_up(max_m, 16);
   L.KX = round_up(3 * n, 16);
   L.NJ = round_up(2 * (n + 2), 16);
   L.KC = 2 * L.MP;
-  // exponent part (operand and t-exponents) first, coefficient part after,
-  // each starting on a 128-byte boundary, so that the evaluation can copy
-  // them separately
+  // exponent part (operand, t-exponents, and for large exponents the mask
+  // and int16 exponent vectors) first, coefficient part after, each starting
+  // on a 128-byte boundary, so that the evaluation can copy them separately
   L.off_bexp = 0;
   L.off_texp = L.MP * L.KX * 2;
-  L.off_bhi = round_up(L.off_texp + L.MP * 4, 128);
+  int end = L.off_texp + L.MP * 4;
+  if (big) {
+    L.off_bigm = round_up(end, 16);
+    L.off_aint = round_up(L.off_bigm + L.MP / 8, 16);   // MP / 32 words
+    end = L.off_aint + L.MP * n * 2;
+  }
+  L.off_bhi = round_up(end, 128);
   L.off_blo = L.off_bhi + L.NJ * L.KC * 2;
   L.chunk_bytes = round_up(L.off_blo + L.NJ * L.KC * 2, 128);
-  int cols = 4 * L.MP + L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
+  int cols = 4 * L.MP + 3 * L.NJ, t = 32;   // two exponent accumulators (Re, Im each), J in three passes
   while (t < cols) t *= 2;
   L.tmem_cols = t;
   return L;
@@ -400,10 +406,16 @@ static hpt_status upload_constants(hpt_system s, const int32_t* ex) {
   if (s->prec != HPT_MIXED) return HPT_OK;
 
   MixedLayout& ml = s->ml;
-  ml = mixed_layout(nv, s->max_m);
+  bool big = false;
+  for (int i = 0; i < M; ++i) {
+    int64_t s1 = 0;
+    for (int j = 0; j < nv; ++j) s1 += std::abs(ex[(size_t)i * nv + j]);
+    big = big || s1 > kBigPhase;
+  }
+  ml = mixed_layout(nv, s->max_m, big);
   int max_smem = 0;
   CUU(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
-  if (!eval_mixed_fits(nv, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, max_smem)) {
+  if (!eval_mixed_fits(nv, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, big, max_smem)) {
     set_error("%d variables with m_k up to %d exceed the mixed form's on-chip memory", nv, s->max_m);
     return HPT_ENOTSUP;
   }
@@ -414,8 +426,18 @@ static hpt_status upload_constants(hpt_system s, const int32_t* ex) {
     uint16_t* bhi = (uint16_t*)(ch + ml.off_bhi);
     uint16_t* blo = (uint16_t*)(ch + ml.off_blo);
     float* tf = (float*)(ch + ml.off_texp);
+    uint32_t* bigm = ml.off_bigm ? (uint32_t*)(ch + ml.off_bigm) : nullptr;
+    int16_t* aint = ml.off_aint ? (int16_t*)(ch + ml.off_aint) : nullptr;
     for (int i = 0; i < s->msz[k]; ++i) {
       const int idx = s->off[k] + i;
+      if (aint) {
+        int64_t s1 = 0;
+        for (int j = 0; j < nv; ++j) {
+          aint[(size_t)i * nv + j] = (int16_t)ex[(size_t)idx * nv + j];
+          s1 += std::abs(ex[(size_t)idx * nv + j]);
+        }
+        if (s1 > kBigPhase) bigm[i / 32] |= 1u << (i % 32);
+      }
       for (int sp = 0; sp < 3; ++sp)
         for (int j = 0; j < nv; ++j)
           bexp[canon_offset(i, sp * nv + j, ml.KX) / 2] = bf16_bits((float)ex[(size_t)idx * nv + j]);
@@ -466,7 +488,7 @@ void hpt_default_params(hpt_params* o) {
   o->polish_tol = 1e-13;
   o->polish_iters = 8;
   o->check_every = 32;
-  o->cond_max = 1e6;
+  o->cond_max = 3e4;
   o->eps0 = 1e-10;
   o->predictor = 0;
   o->pad_ = 0;
@@ -877,14 +899,13 @@ hpt_status hpt_create_system(int32_t n, const int32_t* msz, const int32_t* exps,
   for (int k = 0; k < n; ++k) max_m = std::max(max_m, (int)msz[k]);
   if (prec == HPT_MIXED) {
     if (max_m > kMixedMaxM) { set_error("mixed form supports m_k <= %d", kMixedMaxM); return HPT_ENOTSUP; }
+    // monomials with sum |a_j| > kBigPhase keep the tensor-core exponent GEMM
+    // for |y^a| and take their phase in fixed point (upload_constants)
     for (int i = 0; i < M; ++i) {
-      int64_t s1 = 0;
       for (int j = 0; j < n; ++j) {
         int a = exps[(size_t)i * n + j];
         if (a > 256 || a < -256) { set_error("|a| > 256 is not exact in bf16"); return HPT_ERANGE; }
-        s1 += a < 0 ? -a : a;
       }
-      if (s1 > 64) { set_error("mixed form needs sum |a_j| <= 64"); return HPT_ERANGE; }
       if (L.e[i] >= (1 << 24) || L.e[i] <= -(1 << 24)) { set_error("t-exponent not exact in fp32"); return HPT_ERANGE; }
     }
   }

@@ -13,6 +13,10 @@ namespace hpt {
 
 constexpr int kMaxN = 32;          // variables (equations = variables, or one fewer: projective form)
 constexpr int kMixedMaxM = 128;    // monomials per equation in the mixed form
+// Mixed form: monomials whose sum |a_j| exceeds this get their phase
+// sum_j a_j arg(y_j) accumulated exactly modulo one revolution in 32-bit
+// fixed point instead of by the FP32 exponent GEMM.
+constexpr int kBigPhase = 64;
 constexpr int kTile = 128;         // paths per tensor-core tile (MMA M)
 
 // Per-equation constant image of the mixed form, laid out exactly as the
@@ -30,8 +34,12 @@ struct MixedLayout {
   int NJ = 0;   // 2(n+2) padded to 16
   int KC = 0;   // 2 MP
   int off_bexp = 0, off_bhi = 0, off_blo = 0, off_texp = 0;
+  // monomials with sum |a_j| > kBigPhase (their phase is accumulated in
+  // fixed point): a bit mask per 32 columns and the exponent vectors as
+  // int16, both in the exponent part; 0 when the system has none
+  int off_bigm = 0, off_aint = 0;
   int chunk_bytes = 0;
-  int tmem_cols = 0;     // power of two >= 4 MP + NJ
+  int tmem_cols = 0;     // power of two >= 4 MP + 3 NJ
   int smem_bytes = 0;    // dynamic shared memory of the eval kernel
 };
 
@@ -44,6 +52,7 @@ struct MixedLayout {
 struct MixedSys {
   int n, MP, KX, NJ, KC;
   int chunk_bytes, off_bexp, off_bhi, off_blo, off_texp;
+  int off_bigm, off_aint;   // 0: no monomial with sum |a_j| > kBigPhase
   float inv_D;
   int ne;
   int64_t chunk_off;   // byte offset of the system's constant images
@@ -223,10 +232,16 @@ cudaError_t launch_bounded_wait_probe(int32_t* err, cudaStream_t st);
 // Whether the mixed evaluation kernel can run these operand shapes at all
 // (its leanest configuration within max_smem bytes of shared memory and the
 // 512 tensor-memory columns of an SM).
-bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, int max_smem);
+bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, bool big, int max_smem);
 // Resident eval CTAs per SM the tensor memory allows for tmem_cols (1 or 2).
 int eval_mixed_max_ctas(int tmem_cols);
 MixedSys mixed_sys_of(const hpt_system s);
+// The pipelined evaluation of one system for the step (scratch output only):
+// the dynamic shared memory it needs for shapes s (0: shapes it does not
+// serve), and its launch (one persistent CTA per SM).
+int eval_pipe_smem(const MixedSys& s);
+cudaError_t launch_eval_pipe(hpt_system prof, const MixedSys& s, int64_t p, const uint8_t* chunks, const void* y,
+                             const double* tau, void* ext, int32_t* err, int num_sms, cudaStream_t st);
 
 struct StepArgs {
   int n;

@@ -4,16 +4,20 @@
 // Algorithm 2 (Section 5) for tiles of 128 points: a persistent CTA of 256
 // threads walks its tiles; point r of a tile is tensor-memory lane r, served
 // by thread r of each of the two warpgroups, which split the columns:
-//   op. 1   z = log y in FP32 (principal branch), Re z and Im z each split into
-//           three BF16 parts (hi + mid + lo carries the full FP32 value);
+//   op. 1   z = log y in FP32 (principal branch) in the units of the
+//           exponential, Re z = log2 |y|, Im z = arg y / (2 pi); Re z and
+//           Im z each split into three BF16 parts (hi + mid + lo carries the
+//           full FP32 value);
 //   op. 2a  per equation k: W = Z A_k by tcgen05.mma kind::f16 with FP32
 //           accumulation, K = the three splits of the n coordinates; the
 //           integer exponents are exact in BF16.  Re W and Im W are two MMAs
 //           that share the B operand;
-//   exp     E = exp(Re W + (tau/D) e) (cos Im W, sin Im W): the t-exponent term
-//           is added in FP32 (e exact in FP32), Im W is reduced mod 2 pi with a
-//           two-constant Cody-Waite reduction before the MUFU sine/cosine; E is
-//           split into BF16 hi + lo and written as the A operand of op. 2b;
+//   exp     E = 2^(Re W + (tau/D) log2(e) e) (cos 2 pi r, sin 2 pi r),
+//           r = Im W - rint(Im W): the t-exponent term is added in FP32 (e
+//           exact in FP32), the phase in revolutions is reduced modulo 1 by one
+//           exact subtraction before the MUFU sine/cosine; E is split into
+//           BF16 hi + lo and written as the A operand of op. 2b (cexp_split8,
+//           shared with the pipelined step kernel);
 //   op. 2b  [D_z h_k | D_tau h_k | h_k] = E_k B_k^T as a real GEMM on
 //           [Re E, Im E] x [[Re B, Im B], [-Im B, Re B]]^T, three passes
 //           hi*hi + hi*lo + lo*hi, FP32 accumulation in tensor memory;
@@ -34,6 +38,7 @@
 #include <algorithm>
 
 #include "hpt_internal.h"
+#include "hpt_tc.cuh"
 
 namespace hpt {
 namespace {
@@ -47,129 +52,12 @@ struct MixedArgs {
   int wbuf;   // exponent accumulators W in tensor memory: 2 (next GEMM under the epilogue) or 1
   // shared-memory carve-up (bytes from the 1024-aligned base)
   int s_are, s_aim, s_invy, s_achi, s_aclo, s_const0, s_const1, s_cpart, s_bar;
+  int s_zq;   // fixed angles of the tile's points ([j][128] uint32) when a system has large exponents
   int64_t p;
   int ntiles;
 };
 
-__device__ __forceinline__ uint32_t su32(const void* ptr) {
-  return (uint32_t)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);           // start address
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;       // leading byte offset (K)
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;       // stride byte offset (M/N)
-  d |= (uint64_t)1 << 46;                            // descriptor version
-  return d;                                          // no swizzle, base offset 0
-}
-
-// kind::f16 instruction descriptor: FP32 D, BF16 A and B, both K-major.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
-}
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// Bounded wait: gives up after ~2 s of global time.
-__device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  if (mbar_try(mbar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  for (;;) {
-    if (mbar_try(mbar, parity)) return true;
-    if (gtimer() - t0 > 2000000000ull) return false;
-  }
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ int canon(int r, int k, int K) {
-  return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
-}
-
-__device__ __forceinline__ uint16_t bf16_rn(float v) {
-  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
-}
-__device__ __forceinline__ float bf16_f(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
-
-// 2 pi split for the Cody-Waite reduction: hi is the float nearest to 2 pi,
-// lo the float nearest to the remainder (2 pi - hi).
-constexpr float kTwoPiHi = 6.28318548202514648f;
-constexpr float kTwoPiLo = -1.74845553e-07f;
-constexpr float kInvTwoPi = 0.159154943091895336f;
-
 constexpr int kEvalThreads = 256;   // two warpgroups over the 128 TMEM lanes
-
-// Packed FP32 pairs (sm_100 family): one instruction rounds each half exactly
-// as the scalar operation would, so the results are those of the scalar code.
-__device__ __forceinline__ uint64_t f2pk(float a, float b) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2up(uint64_t v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {   // a * b + c
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 
 // Barriers in shared memory: [0], [1] constant buffers; [2], [3] exponent
 // accumulators W[0], W[1]; [4] coefficient accumulator J; [5] coefficient
@@ -331,11 +219,14 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     // ---- op. 1: z = log y, three-way BF16 split, 1/y (variables split by half)
     const double tv = (live && tin) ? tin[path] : (tau_is_t ? 1.0 : 0.0);
     const double tau = tau_is_t ? log(tv) : tv;
-    const float tau_d = (float)(tau * (double)inv_D);
+    const float tau2 = (float)(tau * (double)inv_D * 1.4426950408889634);   // (tau / D) log2(e)
     const float t_inv = (float)(tau_is_t ? 1.0 / tv : exp(-tau));
+    uint32_t* sZq = (uint32_t*)(sm + P.s_zq);
     for (int j = half; j < n; j += 2) {
       float2 v = live ? y[vbase + j] : make_float2(1.f, 0.f);
-      const float zr = logf(hypotf(v.x, v.y)), zi = atan2f(v.y, v.x);
+      float zr, zi;
+      log_coords(v, zr, zi);
+      if (S.off_aint) sZq[j * 128 + row] = fixed_angle(zi);
       if (oHy) {
         const float r2 = v.x * v.x + v.y * v.y;
         sInvY[j * 128 + row] = make_float2(v.x / r2, -v.y / r2);
@@ -367,14 +258,13 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       // with stride 128 (ext_index); the solve applies diag(1/y)
       float2* erow = ext ? ext + ext_index(pos, kk, 0, nmax) : nullptr;
       for (int c0 = 8 * half; c0 < S.NJ; c0 += 16) {
-        uint32_t jr[8];
-        tmem_ld8(tj + c0, jr);
-        tmem_wait_ld();
+        float jr[8];
+        tmem_ld8_coef(tj + c0, (uint32_t)S.NJ, jr);
         if (!live) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int u = c0 / 2 + q;
-          const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
+          const float2 v = make_float2(jr[2 * q], jr[2 * q + 1]);
           if (erow) {
             if (u < n + 2) erow[(size_t)u * 128] = v;
             continue;
@@ -415,48 +305,16 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
           tmem_ld8(tw + c0, wre);
           tmem_ld8(tw + S.MP + c0, wim);
           tmem_wait_ld();
-          uint32_t hr[4], hi_[4], lr[4], li[4];
-          // two monomials per pass, in packed FP32 pairs where the steps are
-          // plain arithmetic
-          const uint64_t TAU = f2pk(tau_d, tau_d), INV = f2pk(kInvTwoPi, kInvTwoPi);
-          const uint64_t NHI = f2pk(-kTwoPiHi, -kTwoPiHi), NLO = f2pk(-kTwoPiLo, -kTwoPiLo);
-#pragma unroll
-          for (int q = 0; q < 8; q += 2) {
-            const float2 te = *(const float2*)&texp[c0 + q];
-            const uint64_t wr = fma2(TAU, f2pk(te.x, te.y), f2pk(__uint_as_float(wre[q]), __uint_as_float(wre[q + 1])));
-            const uint64_t wi = f2pk(__uint_as_float(wim[q]), __uint_as_float(wim[q + 1]));
-            float t0, t1;
-            f2up(mul2(wi, INV), t0, t1);
-            const uint64_t kq = f2pk(rintf(t0), rintf(t1));
-            float r0, r1, w0, w1;
-            f2up(fma2(kq, NLO, fma2(kq, NHI, wi)), r0, r1);   // Cody-Waite: wi - kq hi - kq lo
-            f2up(wr, w0, w1);
-            float s0, c0_, s1, c1_;
-            __sincosf(r0, &s0, &c0_);
-            __sincosf(r1, &s1, &c1_);
-            const uint64_t m = f2pk(__expf(w0), __expf(w1));
-            float er0, er1, ei0, ei1;
-            const uint64_t er = mul2(m, f2pk(c0_, c1_)), ei = mul2(m, f2pk(s0, s1));
-            f2up(er, er0, er1);
-            f2up(ei, ei0, ei1);
-            const __nv_bfloat162 hre = __floats2bfloat162_rn(er0, er1);
-            const __nv_bfloat162 him = __floats2bfloat162_rn(ei0, ei1);
-            const float2 fre = __bfloat1622float2(hre), fim = __bfloat1622float2(him);
-            float lr0, lr1, li0, li1;
-            f2up(sub2(er, f2pk(fre.x, fre.y)), lr0, lr1);
-            f2up(sub2(ei, f2pk(fim.x, fim.y)), li0, li1);
-            const __nv_bfloat162 lre = __floats2bfloat162_rn(lr0, lr1);
-            const __nv_bfloat162 lim = __floats2bfloat162_rn(li0, li1);
-            hr[q / 2] = *(const uint32_t*)&hre;
-            hi_[q / 2] = *(const uint32_t*)&him;
-            lr[q / 2] = *(const uint32_t*)&lre;
-            li[q / 2] = *(const uint32_t*)&lim;
-          }
+          uint4 hre, lre, him, lim;
+          const uint32_t big8 =
+              S.off_bigm ? (((const uint32_t*)(cbuf(g) + S.off_bigm))[c0 >> 5] >> (c0 & 31)) & 0xffu : 0u;
+          cexp_split8(wre, wim, texp + c0, tau2, big8, (const int16_t*)(cbuf(g) + S.off_aint) + c0 * n,
+                      sZq + row, n, hre, lre, him, lim);
           // Re E at K = c0.., Im E at K = MP + c0..; 8 values = one core column
-          *(uint4*)(sAcHi + canon(row, c0, S.KC)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-          *(uint4*)(sAcLo + canon(row, c0, S.KC)) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-          *(uint4*)(sAcHi + canon(row, S.MP + c0, S.KC)) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-          *(uint4*)(sAcLo + canon(row, S.MP + c0, S.KC)) = make_uint4(li[0], li[1], li[2], li[3]);
+          *(uint4*)(sAcHi + canon(row, c0, S.KC)) = hre;
+          *(uint4*)(sAcLo + canon(row, c0, S.KC)) = lre;
+          *(uint4*)(sAcHi + canon(row, S.MP + c0, S.KC)) = him;
+          *(uint4*)(sAcLo + canon(row, S.MP + c0, S.KC)) = lim;
         }
       }
       proxy_fence();
@@ -471,16 +329,8 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
         // cb + off_bhi addresses the coefficient part in either layout
         const uint32_t cb = SPLIT ? su32(sm + P.s_cpart) - (uint32_t)S.off_bhi : su32(cbuf(g));
         const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
-        const uint32_t tj = t_j;
-        for (int s = 0; s < S.KC / 16; ++s) {
-          const uint64_t ah = smem_desc(su32(sAcHi) + s * 256, 128, sbo_c);
-          const uint64_t al = smem_desc(su32(sAcLo) + s * 256, 128, sbo_c);
-          const uint64_t bh = smem_desc(cb + S.off_bhi + s * 256, 128, sbo_c);
-          const uint64_t bl = smem_desc(cb + S.off_blo + s * 256, 128, sbo_c);
-          mma_bf16(tj, ah, bh, idx_c, s > 0);
-          mma_bf16(tj, ah, bl, idx_c, 1);
-          mma_bf16(tj, al, bh, idx_c, 1);
-        }
+        coef_gemm3(t_j, (uint32_t)S.NJ, smem_desc(su32(sAcHi), 128, sbo_c), smem_desc(su32(sAcLo), 128, sbo_c),
+                   smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
         mma_commit(su32(&bars[4]));
       }
       ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[4]), (uint32_t)g & 1u));
@@ -578,7 +428,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
   cudaError_t e = cudaSuccess;
   const int cfg[4][3] = {{2, 2, 0}, {2, 2, 1}, {1, 2, 0}, {1, 1, 0}};
   auto r128 = [](int v) { return (v + 127) / 128 * 128; };
-  const int xpart = r128(maxs.MP * maxs.KX * 2 + maxs.MP * 4);   // largest exponent part
+  const int xpart = r128(std::max(maxs.off_bhi, maxs.MP * maxs.KX * 2 + maxs.MP * 4));   // largest exponent part
   const int cpart = r128(2 * maxs.NJ * maxs.KC * 2);             // largest coefficient part
   for (const auto& c : cfg) {
     MixedArgs a;
@@ -586,7 +436,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.nbuf = c[0];
     a.wbuf = c[1];
     a.split = c[2];
-    int cols = a.wbuf * 2 * maxs.MP + maxs.NJ, t = 32;
+    int cols = a.wbuf * 2 * maxs.MP + 3 * maxs.NJ, t = 32;   // W buffers, three coefficient accumulators
     while (t < cols) t *= 2;
     if (t > 512) continue;
     a.tmem_cols = t;
@@ -599,6 +449,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.s_are = take(128 * maxs.KX * 2);
     a.s_aim = take(128 * maxs.KX * 2);
     a.s_invy = take(out.Hy ? 128 * maxs.n * 8 : 0);   // 1/y only for the caller's H_y
+    a.s_zq = take(maxs.off_aint ? 128 * maxs.n * 4 : 0);
     a.s_achi = take(128 * maxs.KC * 2);
     a.s_aclo = take(128 * maxs.KC * 2);
     const int cbytes = a.split ? xpart : maxs.chunk_bytes;
@@ -659,11 +510,13 @@ cudaError_t launch_bounded_wait_probe(int32_t* err, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, int max_smem) {
+bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, bool big, int max_smem) {
   auto r = [](int v) { return (v + 1023) / 1024 * 1024; };
-  // the leanest configuration (one constant buffer, one W accumulator), 1/y included
-  const int smem = r(128 * KX * 2) * 2 + r(128 * n * 8) + r(128 * KC * 2) * 2 + r(chunk_bytes) + r(128) + 1024;
-  return smem <= max_smem && 2 * MP + NJ <= 512;
+  // the leanest configuration (one constant buffer, one W accumulator), 1/y
+  // and the fixed angles of large exponents included
+  const int smem = r(128 * KX * 2) * 2 + r(128 * n * 8) + (big ? r(128 * n * 4) : 0) + r(128 * KC * 2) * 2 +
+                   r(chunk_bytes) + r(128) + 1024;
+  return smem <= max_smem && 2 * MP + 3 * NJ <= 512;
 }
 
 int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }
@@ -682,6 +535,8 @@ MixedSys mixed_sys_of(const hpt_system s) {
   m.off_bhi = L.off_bhi;
   m.off_blo = L.off_blo;
   m.off_texp = L.off_texp;
+  m.off_bigm = L.off_bigm;
+  m.off_aint = L.off_aint;
   m.inv_D = (float)(1.0 / (double)s->D);
   m.chunk_off = 0;
   return m;
@@ -691,6 +546,16 @@ cudaError_t launch_eval_mixed(hpt_system s, int64_t p, const void* y, const doub
                               const EvalOut& out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
   const MixedSys m = mixed_sys_of(s);
+  // the step's evaluation (the scratch only, tau given): the pipelined kernel
+  // where its shapes fit (same arithmetic, same bits)
+  if (out.ext && !out.H && !out.Hy && !out.Ht && !tau_is_t && tin) {
+    const int need = eval_pipe_smem(m);
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (need > 0 && need <= max_smem)
+      return launch_eval_pipe(s, m, p, s->d_chunks, y, tin, out.ext, s->d_err, num_sms(), st);
+  }
   return launch_core(s, m, m, p, (p + 127) / 128, s->d_chunks, y, tin, tau_is_t, out, s->d_err, PathMap(), 0,
                      st);
 }

@@ -101,3 +101,20 @@ def test_mixed_refuses_shapes_beyond_on_chip_memory(hpt):
     with pytest.raises(hpt.HptError) as ei:
         hpt.System.from_laurent(s, {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}, hpt.HPT_MIXED)
     assert ei.value.code == 7
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_eval_parity_large_exponents(hpt, oracle_mod, prec):
+    """Three monomials per equation with sum |a_j| between about 160 and 820
+    (four coordinates of magnitude 40..250) at points near the unit torus,
+    where such monomials stay in range: the mixed form takes their phase
+    sum_j a_j arg(y_j) in 32-bit fixed point, exact modulo one revolution,
+    instead of from the FP32 exponent GEMM, and meets the same 2e-4 (333
+    points, three tiles with a ragged tail)."""
+    s = W.large_exponent_system(31, 6, 8, 3, 40, 250)
+    assert (np.abs(s.exponents).sum(1) > 64).sum() == 18
+    cell = {"kind": "lower", "alpha_num": [0] * 6, "denom": 1}
+    y, t = W.torus_points(8, 333, 6, 0.005)
+    errs = _run(hpt, oracle_mod, s, cell, prec, y, t)
+    print("large exponents", ["fp64", "mixed"][prec], errs)
+    assert max(errs) <= TOL[prec], errs

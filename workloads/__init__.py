@@ -37,6 +37,8 @@ __all__ = [
     "LaurentSystem",
     "laurent_system",
     "random_points",
+    "torus_points",
+    "large_exponent_system",
     "random_alpha",
     "planted_lifting",
     "config1",
@@ -146,6 +148,48 @@ def random_points(seed, p, n):
     t = rng.uniform(0.0, 1.0, size=p)
     t = np.where(t <= 0.0, 0.5, t)
     return np.ascontiguousarray(y, dtype=np.complex128), np.ascontiguousarray(t)
+
+
+def torus_points(seed, p, n, sigma):
+    """Points near the unit torus: y_j = exp(g + i phi), g ~ N(0, sigma^2),
+    phi ~ U[0, 2 pi), t ~ U(0,1) -- for systems with large exponents, whose
+    monomials y^a stay in floating-point range only where |y_j| is near 1."""
+    rng = _rng(seed, p, n, 0x7085)
+    g = sigma * rng.standard_normal((p, n))
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=(p, n))
+    y = np.exp(g + 1j * phi)
+    t = rng.uniform(0.0, 1.0, size=p)
+    t = np.where(t <= 0.0, 0.5, t)
+    return np.ascontiguousarray(y, dtype=np.complex128), np.ascontiguousarray(t)
+
+
+def large_exponent_system(seed, n, m, n_big, big_lo, big_hi, lift_hi=64, attempt=0):
+    """A Laurent system whose equations each have n_big monomials with large
+    exponents (min(4, n) nonzero coordinates of magnitude in [big_lo,
+    big_hi], random signs) beside m - n_big monomials with exponents in
+    [-2, 2]; coefficients e^{i theta}, lifting U{0..lift_hi}."""
+    rng = _rng(seed, attempt, n, 0xB16E)
+    rows = []
+    for k in range(n):
+        seen = set()
+        while len(seen) < m:
+            big = len(seen) >= m - n_big
+            if big:
+                a = np.zeros(n, dtype=np.int64)
+                idx = rng.choice(n, size=min(4, n), replace=False)
+                a[idx] = rng.integers(big_lo, big_hi + 1, size=len(idx)) * rng.choice([-1, 1], size=len(idx))
+            else:
+                a = rng.integers(-2, 3, size=n)
+            key = tuple(int(v) for v in a)
+            if key in seen:
+                continue
+            seen.add(key)
+            rows.append(a)
+    M = n * m
+    exps = np.array(rows, dtype=np.int32).reshape(M, n)
+    coeffs = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=M))
+    lifting = rng.integers(0, lift_hi + 1, size=M).astype(np.int64)
+    return LaurentSystem(n, [m] * n, exps, coeffs, lifting)
 
 
 def random_alpha(seed, n, lo=-8, hi=8):
