@@ -277,16 +277,20 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       if (lane == 0) mbar_arrive(bar(B_JEMPTY + b));
     }
   } else if (warp == kMmaWarp) {
-    // ---------------- MMA issuer ----------------
-    if (lane == 0) {
+    // ---------------- MMA issuer: the whole warp runs the loop, one elected
+    // lane issues each MMA and commit ----------------
+    {
+      // a failed (timed-out) wait in any lane stops every lane: elect.sync
+      // needs the whole warp
+      auto waitw = [&](int bb, int uu) { return __all_sync(0xffffffffu, wait(bb, uu)); };
       const uint32_t idx_x = idesc_bf16(128, S.MP), sbo_x = S.KX * 16;
       const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
       int last_exp = -1, last_coef = -1;
       auto issue_exp = [&](const Unit& u) -> bool {
         const int i = u.i, w = ring(i, kWBuf), c = ring(i, kCBuf), lt = u.lt;
-        if (first_of_tile(u) && !wait(B_ZFULL + (lt & 1), lt >> 1)) return false;
-        if (!wait(B_CFULL + c, use(i, kCBuf))) return false;
-        if (i >= kWBuf && !wait(B_WEMPTY + w, use(i, kWBuf) - 1)) return false;
+        if (first_of_tile(u) && !waitw(B_ZFULL + (lt & 1), lt >> 1)) return false;
+        if (!waitw(B_CFULL + c, use(i, kCBuf))) return false;
+        if (i >= kWBuf && !waitw(B_WEMPTY + w, use(i, kWBuf) - 1)) return false;
         tc_fence_after();
         const uint32_t cb = su32(sm + coff(c));
         const uint32_t zre = su32(sm + zoff(lt & 1)), zim = zre + (uint32_t)P.z_im;
@@ -295,11 +299,11 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         const uint64_t bd = smem_desc(cb + S.off_bexp, 128, sbo_x);
         const uint64_t ar = smem_desc(zre, 128, sbo_x), ai = smem_desc(zim, 128, sbo_x);
         for (int s = 0; s < S.KX / 16; ++s) {
-          mma_bf16(tw, ar + 16 * s, bd + 16 * s, idx_x, s > 0);
-          mma_bf16(tw + S.MP, ai + 16 * s, bd + 16 * s, idx_x, s > 0);
+          mma_bf16_w(tw, ar + 16 * s, bd + 16 * s, idx_x, s > 0);
+          mma_bf16_w(tw + S.MP, ai + 16 * s, bd + 16 * s, idx_x, s > 0);
         }
-        mma_commit(bar(B_WFULL + w));
-        if (last_of_tile(u)) mma_commit(bar(B_ZEMPTY + (lt & 1)));
+        mma_commit_w(bar(B_WFULL + w));
+        if (last_of_tile(u)) mma_commit_w(bar(B_ZEMPTY + (lt & 1)));
         last_exp = i;
         return true;
       };
@@ -314,17 +318,17 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
           if (!(ok = issue_exp(ahead))) break;
           ahead = next_unit(ahead);
         }
-        if (!wait(B_EFULL + e, use(i, kEBuf))) break;
-        if (i >= kJBuf && !wait(B_JEMPTY + b, use(i, kJBuf) - 1)) break;
+        if (!waitw(B_EFULL + e, use(i, kEBuf))) break;
+        if (i >= kJBuf && !waitw(B_JEMPTY + b, use(i, kJBuf) - 1)) break;
         tc_fence_after();
         const uint32_t cb = su32(sm + coff(c));
         const uint32_t ah0 = su32(sm + eoff(e)), al0 = ah0 + (uint32_t)P.e_lo;
         const uint32_t tj = tj_col(b);
-        coef_gemm3(tj, (uint32_t)S.NJ, smem_desc(ah0, 128, sbo_c), smem_desc(al0, 128, sbo_c),
+        coef_gemm3<true>(tj, (uint32_t)S.NJ, smem_desc(ah0, 128, sbo_c), smem_desc(al0, 128, sbo_c),
                    smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
-        mma_commit(bar(B_JFULL + b));
-        mma_commit(bar(B_EEMPTY + e));
-        mma_commit(bar(B_CEMPTY + c));
+        mma_commit_w(bar(B_JFULL + b));
+        mma_commit_w(bar(B_EEMPTY + e));
+        mma_commit_w(bar(B_CEMPTY + c));
         last_coef = i;
       }
       if (*sAbort) {

@@ -138,19 +138,22 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   auto cpar = [&](int g) -> uint32_t { return (uint32_t)(P.nbuf == 2 ? (g >> 1) : g) & 1u; };
 
   // exponent GEMM of work item g (an equation of system S) into W[g & 1];
-  // thread 0 only
+  // the whole of warp 0 (one elected lane issues; the operands stay
+  // warp-uniform)
   auto issue_exp = [&](int g, const MixedSys& S) -> bool {
-    if (!mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g))) return false;
+    if (!__all_sync(0xffffffffu, mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g)))) return false;
     tc_fence_after();
     const uint32_t cb = su32(cbuf(g));
     const uint32_t tw = tbase + (uint32_t)((P.wbuf == 2 ? (g & 1) : 0) * 2 * S.MP);
     const uint32_t idx_x = idesc_bf16(128, S.MP), sbo_x = S.KX * 16;
+    // a K-slice of 256 bytes adds 16 to a descriptor's address field
+    const uint64_t bd = smem_desc(cb + S.off_bexp, 128, sbo_x);
+    const uint64_t ar = smem_desc(su32(sAre), 128, sbo_x), ai = smem_desc(su32(sAim), 128, sbo_x);
     for (int s = 0; s < S.KX / 16; ++s) {
-      const uint64_t bd = smem_desc(cb + S.off_bexp + s * 256, 128, sbo_x);
-      mma_bf16(tw, smem_desc(su32(sAre) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
-      mma_bf16(tw + S.MP, smem_desc(su32(sAim) + s * 256, 128, sbo_x), bd, idx_x, s > 0);
+      mma_bf16_w(tw, ar + 16 * s, bd + 16 * s, idx_x, s > 0);
+      mma_bf16_w(tw + S.MP, ai + 16 * s, bd + 16 * s, idx_x, s > 0);
     }
-    mma_commit(su32(&bars[2 + (g & 1)]));
+    mma_commit_w(su32(&bars[2 + (g & 1)]));
     return true;
   };
 
@@ -248,7 +251,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     proxy_fence();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0 && lookahead && !issue_exp(g, S)) atomicExch(sAbort, 1);
+    if (warp == 0 && lookahead && !issue_exp(g, S)) atomicExch(sAbort, 1);
 
     // row kk of the outputs from J: 8-column chunks (4 complex entries)
     // alternate between the warpgroups (NJ is a multiple of 16)
@@ -286,7 +289,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     for (int k = kb; k < ke; ++k, ++g) {
       // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
       // GEMM of equation k+1 is issued now and runs under this epilogue
-      if (tid == 0) {
+      if (warp == 0) {
         const bool ok1 = lookahead ? (k + 1 < ke ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
         if (!ok1) atomicExch(sAbort, 1);
       }
@@ -322,16 +325,16 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       __syncthreads();
       if (*sAbort) goto teardown;
       // ---- op. 2b: [D_z h | D_tau h | h] = E_k B_k^T, split passes
-      if (tid == 0) {
+      if (warp == 0) {   // one elected lane issues (operands warp-uniform)
         // split mode: the coefficient part of item g in its own buffer
-        if (SPLIT && !mbar_wait(su32(&bars[5]), (uint32_t)g & 1u)) atomicExch(sAbort, 1);
+        if (SPLIT && !__all_sync(0xffffffffu, mbar_wait(su32(&bars[5]), (uint32_t)g & 1u))) atomicExch(sAbort, 1);
         tc_fence_after();
         // cb + off_bhi addresses the coefficient part in either layout
         const uint32_t cb = SPLIT ? su32(sm + P.s_cpart) - (uint32_t)S.off_bhi : su32(cbuf(g));
         const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
-        coef_gemm3(t_j, (uint32_t)S.NJ, smem_desc(su32(sAcHi), 128, sbo_c), smem_desc(su32(sAcLo), 128, sbo_c),
+        coef_gemm3<true>(t_j, (uint32_t)S.NJ, smem_desc(su32(sAcHi), 128, sbo_c), smem_desc(su32(sAcLo), 128, sbo_c),
                    smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
-        mma_commit(su32(&bars[4]));
+        mma_commit_w(su32(&bars[4]));
       }
       ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[4]), (uint32_t)g & 1u));
       if (!ok) atomicExch(sAbort, 1);

@@ -47,12 +47,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
 // dependent MMAs per accumulator at K = 64 instead of one chain of twelve.
 // a_hi, a_lo, b_hi, b_lo are the descriptors of the first 256-byte K-slice;
 // a K-slice adds 16 to a descriptor's address field.
+// WARP: the whole warp calls it (elected issue), else one thread.
+template <bool WARP>
 __device__ __forceinline__ void coef_gemm3(uint32_t tj, uint32_t nj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
                                            uint64_t b_lo, uint32_t idesc, int kslices);
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
+}
+
+// The same two instructions for a whole warp that runs the issue loop
+// together: the operands stay warp-uniform (no per-thread copies into the
+// uniform datapath on every MMA) and one elected lane issues.
+__device__ __forceinline__ void mma_bf16_w(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit_w(uint32_t mbar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(mbar)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -62,12 +81,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+template <bool WARP>
 __device__ __forceinline__ void coef_gemm3(uint32_t tj, uint32_t nj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
                                            uint64_t b_lo, uint32_t idesc, int kslices) {
   for (int s = 0; s < kslices; ++s) {
-    mma_bf16(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
-    mma_bf16(tj + nj, a_hi + 16 * s, b_lo + 16 * s, idesc, s > 0);
-    mma_bf16(tj + 2 * nj, a_lo + 16 * s, b_hi + 16 * s, idesc, s > 0);
+    if (WARP) {
+      mma_bf16_w(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
+      mma_bf16_w(tj + nj, a_hi + 16 * s, b_lo + 16 * s, idesc, s > 0);
+      mma_bf16_w(tj + 2 * nj, a_lo + 16 * s, b_hi + 16 * s, idesc, s > 0);
+    } else {
+      mma_bf16(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
+      mma_bf16(tj + nj, a_hi + 16 * s, b_lo + 16 * s, idesc, s > 0);
+      mma_bf16(tj + 2 * nj, a_lo + 16 * s, b_hi + 16 * s, idesc, s > 0);
+    }
   }
 }
 
