@@ -60,10 +60,16 @@ struct PipeArgs {
   int s_bar;
 };
 
-// Barrier indices (one pair per buffer of each ring).
-enum { B_CFULL = 0, B_CEMPTY = B_CFULL + kCBuf, B_ZFULL = B_CEMPTY + kCBuf, B_ZEMPTY = B_ZFULL + 2,
-       B_WFULL = B_ZEMPTY + 2, B_WEMPTY = B_WFULL + kWBuf, B_EFULL = B_WEMPTY + kWBuf, B_EEMPTY = B_EFULL + kEBuf,
-       B_JFULL = B_EEMPTY + kEBuf, B_JEMPTY = B_JFULL + kJBuf, B_COUNT = B_JEMPTY + kJBuf };
+// Barriers.  One "coefficient GEMM of unit i done" ring (slot i % kDone)
+// stands for three events: J of unit i full (drain), E buffer of unit i free
+// (exp warps, kEBuf units later), constant buffer of unit i free (loader,
+// kCBuf units later); every waiter is at most one completion behind its slot.
+// The exp warps' "E full" also frees their W buffer: the MMA warp issues the
+// exponent GEMM into it only after it has waited for that arrival.
+constexpr int kDone = kCBuf;
+static_assert(kDone >= kEBuf && kDone >= kJBuf, "done ring");
+enum { B_CFULL = 0, B_DONE = B_CFULL + kCBuf, B_ZFULL = B_DONE + kDone, B_ZEMPTY = B_ZFULL + 2,
+       B_WFULL = B_ZEMPTY + 2, B_EFULL = B_WFULL + kWBuf, B_JEMPTY = B_EFULL + kEBuf, B_COUNT = B_JEMPTY + kJBuf };
 
 __global__ void __launch_bounds__(kPipeThreads, 1)
 eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restrict__ tau_in,
@@ -111,26 +117,15 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
   };
 
   if (tid == 0) {
-    for (int q = 0; q < kCBuf; ++q) {
-      mbar_init(bar(B_CFULL + q), 1);
-      mbar_init(bar(B_CEMPTY + q), 1);
-    }
+    for (int q = 0; q < kCBuf; ++q) mbar_init(bar(B_CFULL + q), 1);
+    for (int q = 0; q < kDone; ++q) mbar_init(bar(B_DONE + q), 1);
     for (int q = 0; q < 2; ++q) {
       mbar_init(bar(B_ZFULL + q), kExpWarps);
       mbar_init(bar(B_ZEMPTY + q), 1);
     }
-    for (int q = 0; q < kWBuf; ++q) {
-      mbar_init(bar(B_WFULL + q), 1);
-      mbar_init(bar(B_WEMPTY + q), kExpWarps);
-    }
-    for (int q = 0; q < kEBuf; ++q) {
-      mbar_init(bar(B_EFULL + q), kExpWarps);
-      mbar_init(bar(B_EEMPTY + q), 1);
-    }
-    for (int q = 0; q < kJBuf; ++q) {
-      mbar_init(bar(B_JFULL + q), 1);
-      mbar_init(bar(B_JEMPTY + q), kDrainWarps);
-    }
+    for (int q = 0; q < kWBuf; ++q) mbar_init(bar(B_WFULL + q), 1);
+    for (int q = 0; q < kEBuf; ++q) mbar_init(bar(B_EFULL + q), kExpWarps);
+    for (int q = 0; q < kJBuf; ++q) mbar_init(bar(B_JEMPTY + q), kDrainWarps);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -211,7 +206,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
     float tau2 = 0.f;
     const uint32_t* zq = nullptr;   // this point's fixed angles (large exponents)
     for (Unit u = first_unit; u.i < U; u = next_unit(u)) {
-      const int i = u.i, w = ring(i, kWBuf), e = ring(i, kEBuf), c = ring(i, kCBuf), lt = u.lt;
+      const int i = u.i, w = ring(i, kWBuf), e = ring(i, kEBuf), lt = u.lt;
       if (first_of_tile(u)) {
         if (i == 0 && !prep_z(0)) break;
         if (t_first + lt + 1 <= t_last && !prep_z(lt + 1)) break;   // the next tile, one tile ahead
@@ -219,11 +214,13 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         tau2 = ((const float*)(sm + zoff(lt & 1) + P.z_tau))[row];
         zq = (const uint32_t*)(sm + zoff(lt & 1) + P.z_q) + row;
       }
-      if (!wait(B_CFULL + c, use(i, kCBuf))) break;    // the t-exponents of unit i
       if (!wait(B_WFULL + w, use(i, kWBuf))) break;
-      if (i >= kEBuf && !wait(B_EEMPTY + e, use(i, kEBuf) - 1)) break;
+      if (i >= kEBuf && !wait(B_DONE + ring(i - kEBuf, kDone), use(i - kEBuf, kDone))) break;
       tc_fence_after();
-      const float* texp = (const float*)(sm + coff(c) + S.off_texp);
+      // the t-exponents (and large-exponent tables) of unit i's equation,
+      // read through L1 from its constant image in global memory
+      const uint8_t* cg = chunks + (size_t)u.k * S.chunk_bytes;
+      const float* texp = (const float*)(cg + S.off_texp);
       uint8_t* eh = sm + eoff(e);
       uint8_t* el = eh + P.e_lo;
       for (int c0 = 8 * wg; c0 < S.MP; c0 += 8 * 4) {
@@ -232,9 +229,8 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         tmem_ld8(tw_col(w) + lane_base + S.MP + c0, wim);
         tmem_wait_ld();
         uint4 hre, lre, him, lim;
-        const uint8_t* cb = sm + coff(c);
-        const uint32_t big8 = S.off_bigm ? (((const uint32_t*)(cb + S.off_bigm))[c0 >> 5] >> (c0 & 31)) & 0xffu : 0u;
-        cexp_split8(wre, wim, texp + c0, tau2, big8, (const int16_t*)(cb + S.off_aint) + c0 * n, zq, n, hre, lre,
+        const uint32_t big8 = S.off_bigm ? (((const uint32_t*)(cg + S.off_bigm))[c0 >> 5] >> (c0 & 31)) & 0xffu : 0u;
+        cexp_split8(wre, wim, texp + c0, tau2, big8, (const int16_t*)(cg + S.off_aint) + c0 * n, zq, n, hre, lre,
                     him, lim);
         // Re E at K = c0.., Im E at K = MP + c0..; 8 values = one core column
         *(uint4*)(eh + canon(row, c0, S.KC)) = hre;
@@ -245,10 +241,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       tc_fence_before();
       proxy_fence();
       __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(bar(B_WEMPTY + w));
-        mbar_arrive(bar(B_EFULL + e));
-      }
+      if (lane == 0) mbar_arrive(bar(B_EFULL + e));   // E full, W buffer free
     }
   } else if (warp < kMmaWarp) {
     // ---------------- drain warps ----------------
@@ -256,7 +249,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     for (Unit u = first_unit; u.i < U; u = next_unit(u)) {
       const int i = u.i, b = ring(i, kJBuf), lt = u.lt, k = u.k;
-      if (!wait(B_JFULL + b, use(i, kJBuf))) break;
+      if (!wait(B_DONE + ring(i, kDone), use(i, kDone))) break;
       tc_fence_after();
       const int64_t pos = (int64_t)(t_first + lt) * 128 + row;
       const bool live = pos < P.p;
@@ -290,7 +283,6 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         const int i = u.i, w = ring(i, kWBuf), c = ring(i, kCBuf), lt = u.lt;
         if (first_of_tile(u) && !waitw(B_ZFULL + (lt & 1), lt >> 1)) return false;
         if (!waitw(B_CFULL + c, use(i, kCBuf))) return false;
-        if (i >= kWBuf && !waitw(B_WEMPTY + w, use(i, kWBuf) - 1)) return false;
         tc_fence_after();
         const uint32_t cb = su32(sm + coff(c));
         const uint32_t zre = su32(sm + zoff(lt & 1)), zim = zre + (uint32_t)P.z_im;
@@ -326,15 +318,13 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         const uint32_t tj = tj_col(b);
         coef_gemm3<true>(tj, (uint32_t)S.NJ, smem_desc(ah0, 128, sbo_c), smem_desc(al0, 128, sbo_c),
                    smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
-        mma_commit_w(bar(B_JFULL + b));
-        mma_commit_w(bar(B_EEMPTY + e));
-        mma_commit_w(bar(B_CEMPTY + c));
+        mma_commit_w(bar(B_DONE + ring(i, kDone)));
         last_coef = i;
       }
       if (*sAbort) {
         // let the MMAs issued land before the CTA's memory goes away
         if (last_coef >= 0)
-          mbar_wait(bar(B_JFULL + ring(last_coef, kJBuf)), (uint32_t)use(last_coef, kJBuf) & 1u);
+          mbar_wait(bar(B_DONE + ring(last_coef, kDone)), (uint32_t)use(last_coef, kDone) & 1u);
         if (last_exp > last_coef)
           mbar_wait(bar(B_WFULL + ring(last_exp, kWBuf)), (uint32_t)use(last_exp, kWBuf) & 1u);
       }
@@ -345,7 +335,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       int issued = 0;
       for (Unit u = first_unit; u.i < U; u = next_unit(u)) {
         const int i = u.i, c = ring(i, kCBuf);
-        if (i >= kCBuf && !wait(B_CEMPTY + c, use(i, kCBuf) - 1)) break;
+        if (i >= kCBuf && !wait(B_DONE + ring(i - kCBuf, kDone), use(i - kCBuf, kDone))) break;
         bulk_load(su32(sm + coff(c)), chunks + (size_t)u.k * S.chunk_bytes, S.chunk_bytes, bar(B_CFULL + c));
         issued = i + 1;
       }

@@ -136,9 +136,20 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
+// Non-blocking test of phase `parity` (the cheap path when it has completed).
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait: gives up after ~2 s of global time.
 __device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  if (mbar_try(mbar, parity)) return true;
+  if (mbar_test(mbar, parity)) return true;
   const uint64_t t0 = gtimer();
   for (;;) {
     if (mbar_try(mbar, parity)) return true;
