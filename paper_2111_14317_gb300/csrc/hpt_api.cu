@@ -309,8 +309,10 @@ hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, v
   const int n = a->n;
   const int64_t chunk = std::min<int64_t>(p, 8192);
   const size_t ext_bytes = (ext_entries(chunk, n) * 16 + 255) / 256 * 256;
-  if ((rc = ensure_scratch(s, ext_bytes + (size_t)chunk * s->M * 16))) return rc;
+  const size_t contrib_bytes = ((size_t)chunk * s->M * 16 + 255) / 256 * 256;
+  if ((rc = ensure_scratch(s, ext_bytes + contrib_bytes + adjoint_part_bytes(s->M)))) return rc;
   void* contrib = (char*)s->d_scratch + ext_bytes;
+  void* part = (char*)contrib + contrib_bytes;
   for (int64_t q0 = 0; q0 < p; q0 += chunk) {
     const int64_t cnt = std::min(chunk, p - q0);
     EvalOut out;
@@ -318,7 +320,7 @@ hpt_status hpt_adjoint(hpt_system s, int64_t p, const void* x, const void* gx, v
     const void* xq = (const char*)x + q0 * n * 16;
     e = launch_eval_fp64(a, cnt, xq, nullptr, 0, out, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint evaluation launch");
-    e = launch_adjoint(a, cnt, s->d_scratch, xq, (const char*)gx + q0 * n * 16, contrib, 0, gc, st);
+    e = launch_adjoint(a, cnt, s->d_scratch, xq, (const char*)gx + q0 * n * 16, contrib, part, gc, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
   }
   return HPT_OK;

@@ -18,14 +18,18 @@
 //   drain warps (warps 16-19, one per lane quarter): read the coefficient
 //               accumulator J of unit i from tensor memory and store the row
 //               [D_z h_k | D_tau h_k | h_k] of every point to the scratch;
-//   MMA warp    (warp 20, one thread): issues the exponent GEMM of unit i + 1
-//               before the coefficient GEMM of unit i, so the tensor core
-//               works on i + 1 while the exp warps work on i;
+//   MMA warp    (warp 20; the whole warp runs the issue loop, one elected lane
+//               issues each MMA and commit): issues the exponent GEMMs of
+//               up to kWBuf - 1 units ahead of the coefficient GEMM of unit
+//               i, so the tensor core works ahead while the exp warps work
+//               on i;
 //   load warp   (warp 21, one thread): bulk-copies the constant image of
 //               each unit's equation (exponent operand, t-exponents, B_k hi/lo)
 //               into a ring of kCBuf buffers, so that a copy starts kCBuf - 1
 //               units ahead of the exponent GEMM that reads it.
-// W, E and J are double-buffered; the log coordinates of two tiles are kept.  Every mbarrier wait is bounded (about two seconds);
+// W is a ring of kWBuf tensor-memory buffers, E a ring of kEBuf shared-memory
+// buffers and J a ring of kJBuf tensor-memory buffers; the log coordinates of
+// two tiles are kept.  Every mbarrier wait is bounded (about two seconds);
 // a wait that gives up raises the device error flag and the CTA winds down
 // after the copies and MMAs it issued have landed.
 #include <algorithm>
@@ -138,8 +142,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
-  // tensor-memory columns: W[0], W[1] (Re MP, Im MP each), then J[0], J[1]
-  // (each the three pass accumulators of the coefficient GEMM, NJ columns apiece)
+  // tensor-memory columns: the W ring (Re MP, Im MP each), then the J ring
   auto tw_col = [&](int b) { return tbase + (uint32_t)(b * 2 * S.MP); };
   // unit i's buffer in a ring of R, and the completion of that buffer's
   // barrier that unit i waits for: its (i / R)-th as "full", the (i / R - 1)-th
@@ -161,7 +164,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
     for (int q = 1; q < kCBuf; ++q) o = c == q ? P.s_c[q] : o;
     return o;
   };
-  auto tj_col = [&](int b) { return tbase + (uint32_t)(kWBuf * 2 * S.MP + b * 3 * S.NJ); };   // three pass accumulators
+  auto tj_col = [&](int b) { return tbase + (uint32_t)(kWBuf * 2 * S.MP + b * S.NJ); };
 
   if (warp < kExpWarps) {
     // ---------------- exp warps ----------------
@@ -255,13 +258,14 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       const bool live = pos < P.p;
       float2* erow = ext + ext_index(pos, k, 0, n);
       for (int c0 = 0; c0 < 2 * (n + 2); c0 += 8) {
-        float jr[8];
-        tmem_ld8_coef(tj_col(b) + lane_base + c0, (uint32_t)S.NJ, jr);
+        uint32_t jr[8];
+        tmem_ld8(tj_col(b) + lane_base + c0, jr);
+        tmem_wait_ld();
         if (live) {
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const int u = c0 / 2 + v;
-            if (u < n + 2) erow[(size_t)u * 128] = make_float2(jr[2 * v], jr[2 * v + 1]);
+            if (u < n + 2) erow[(size_t)u * 128] = make_float2(__uint_as_float(jr[2 * v]), __uint_as_float(jr[2 * v + 1]));
           }
         }
       }
@@ -316,8 +320,8 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         const uint32_t cb = su32(sm + coff(c));
         const uint32_t ah0 = su32(sm + eoff(e)), al0 = ah0 + (uint32_t)P.e_lo;
         const uint32_t tj = tj_col(b);
-        coef_gemm3<true>(tj, (uint32_t)S.NJ, smem_desc(ah0, 128, sbo_c), smem_desc(al0, 128, sbo_c),
-                   smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
+        coef_gemm(tj, smem_desc(ah0, 128, sbo_c), smem_desc(al0, 128, sbo_c), smem_desc(cb + S.off_bhi, 128, sbo_c),
+                  smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
         mma_commit_w(bar(B_DONE + ring(i, kDone)));
         last_coef = i;
       }
@@ -361,9 +365,8 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
 // Shared memory the pipelined kernel needs for these shapes (0: it does not
 // serve them).
 int eval_pipe_smem(const MixedSys& s) {
-  // two W buffers and two J buffers of three pass accumulators in the 512
-  // tensor-memory columns of the SM
-  if (s.n > 16 || s.ne != s.n || kWBuf * 2 * s.MP + kJBuf * 3 * s.NJ > 512) return 0;
+  // the W and J rings in the 512 tensor-memory columns of the SM
+  if (s.n > 16 || s.ne != s.n || kWBuf * 2 * s.MP + kJBuf * s.NJ > 512) return 0;
   auto r1k = [](int v) { return (v + 1023) / 1024 * 1024; };
   const int z = r1k(2 * 128 * s.KX * 2 + 128 * 4 + (s.off_aint ? 128 * s.n * 4 : 0));
   const int e = r1k(2 * 128 * s.KC * 2);
@@ -381,7 +384,7 @@ cudaError_t launch_eval_pipe(hpt_system prof, const MixedSys& s, int64_t p, cons
   const int64_t ntiles = (p + 127) / 128;
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
   a.ntiles = (int)ntiles;
-  int cols = kWBuf * 2 * s.MP + kJBuf * 3 * s.NJ, t = 32;
+  int cols = kWBuf * 2 * s.MP + kJBuf * s.NJ, t = 32;
   while (t < cols) t *= 2;
   if (t > 512) return cudaErrorInvalidValue;
   a.tmem_cols = t;

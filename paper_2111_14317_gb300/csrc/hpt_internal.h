@@ -39,7 +39,7 @@ struct MixedLayout {
   // int16, both in the exponent part; 0 when the system has none
   int off_bigm = 0, off_aint = 0;
   int chunk_bytes = 0;
-  int tmem_cols = 0;     // power of two >= 4 MP + 3 NJ
+  int tmem_cols = 0;     // power of two >= 4 MP + NJ
   int smem_bytes = 0;    // dynamic shared memory of the eval kernel
 };
 
@@ -285,8 +285,10 @@ cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void*
 // Adjoint: per-solution lambda and the per-block partial sums of the
 // coefficient gradient (two kernels).
 cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void* x,
-                           const void* gx, void* partial, int64_t nblk, void* gc,
+                           const void* gx, void* partial, void* part, void* gc,
                            cudaStream_t st);
+// Bytes of the adjoint's partial column sums (part) for M coefficients.
+size_t adjoint_part_bytes(int M);
 
 // FP64 Newton polish at t = 1 of p solutions x (complex128) whose done flag
 // is 0, polish_iters rounds over chunks of `chunk` paths; ext holds the

@@ -261,13 +261,14 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       // with stride 128 (ext_index); the solve applies diag(1/y)
       float2* erow = ext ? ext + ext_index(pos, kk, 0, nmax) : nullptr;
       for (int c0 = 8 * half; c0 < S.NJ; c0 += 16) {
-        float jr[8];
-        tmem_ld8_coef(tj + c0, (uint32_t)S.NJ, jr);
+        uint32_t jr[8];
+        tmem_ld8(tj + c0, jr);
+        tmem_wait_ld();
         if (!live) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int u = c0 / 2 + q;
-          const float2 v = make_float2(jr[2 * q], jr[2 * q + 1]);
+          const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
           if (erow) {
             if (u < n + 2) erow[(size_t)u * 128] = v;
             continue;
@@ -332,8 +333,8 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
         // cb + off_bhi addresses the coefficient part in either layout
         const uint32_t cb = SPLIT ? su32(sm + P.s_cpart) - (uint32_t)S.off_bhi : su32(cbuf(g));
         const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
-        coef_gemm3<true>(t_j, (uint32_t)S.NJ, smem_desc(su32(sAcHi), 128, sbo_c), smem_desc(su32(sAcLo), 128, sbo_c),
-                   smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
+        coef_gemm(t_j, smem_desc(su32(sAcHi), 128, sbo_c), smem_desc(su32(sAcLo), 128, sbo_c),
+                  smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
         mma_commit_w(su32(&bars[4]));
       }
       ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[4]), (uint32_t)g & 1u));
@@ -439,7 +440,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.nbuf = c[0];
     a.wbuf = c[1];
     a.split = c[2];
-    int cols = a.wbuf * 2 * maxs.MP + 3 * maxs.NJ, t = 32;   // W buffers, three coefficient accumulators
+    int cols = a.wbuf * 2 * maxs.MP + maxs.NJ, t = 32;   // W buffers, coefficient accumulator
     while (t < cols) t *= 2;
     if (t > 512) continue;
     a.tmem_cols = t;
@@ -519,7 +520,7 @@ bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, boo
   // and the fixed angles of large exponents included
   const int smem = r(128 * KX * 2) * 2 + r(128 * n * 8) + (big ? r(128 * n * 4) : 0) + r(128 * KC * 2) * 2 +
                    r(chunk_bytes) + r(128) + 1024;
-  return smem <= max_smem && 2 * MP + 3 * NJ <= 512;
+  return smem <= max_smem && 2 * MP + NJ <= 512;
 }
 
 int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }

@@ -1135,14 +1135,42 @@ adjoint_kernel(int n, int64_t p, const int32_t* __restrict__ msz, const int32_t*
 }
 
 // Adjoint, part 2: gc[i] += sum over the chunk's solutions of contrib[q][i],
-// in order.
-__global__ void sum_columns_kernel(int64_t p, int M, const double2* __restrict__ contrib,
-                                   double2* __restrict__ gc) {
+// in a fixed order (the same bits on every run).  First pass: block (cb, r)
+// sums rows r, r + kAdjRowBlocks, ... of 32 consecutive columns, its 8 warps
+// each a strided subset, the warps' sums added in warp order (a warp reads 32
+// consecutive columns of one row: coalesced); second pass: every column's
+// kAdjRowBlocks partial sums added in order.
+constexpr int kAdjRowBlocks = 64;
+
+__global__ void __launch_bounds__(256) sum_columns_part_kernel(int64_t p, int M, const double2* __restrict__ contrib,
+                                                                double2* __restrict__ part) {
+  __shared__ double2 red[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + tx;
+  double2 acc = make_double2(0.0, 0.0);
+  if (i < M)
+    for (int64_t q = (int64_t)blockIdx.y + (int64_t)kAdjRowBlocks * ty; q < p; q += (int64_t)kAdjRowBlocks * 8) {
+      const double2 v = contrib[(size_t)q * M + i];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && i < M) {
+    for (int w = 1; w < 8; ++w) {
+      acc.x += red[w][tx].x;
+      acc.y += red[w][tx].y;
+    }
+    part[(size_t)blockIdx.y * M + i] = acc;
+  }
+}
+
+__global__ void sum_columns_kernel(int M, const double2* __restrict__ part, double2* __restrict__ gc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   double2 acc = make_double2(0.0, 0.0);
-  for (int64_t q = 0; q < p; ++q) {
-    const double2 v = contrib[(size_t)q * M + i];
+  for (int r = 0; r < kAdjRowBlocks; ++r) {
+    const double2 v = part[(size_t)r * M + i];
     acc.x += v.x;
     acc.y += v.y;
   }
@@ -1393,9 +1421,10 @@ cudaError_t launch_newton_update(hpt_system s, int64_t p, const void* ext, void*
   return e;
 }
 
+size_t adjoint_part_bytes(int M) { return (size_t)kAdjRowBlocks * M * 16; }
+
 cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void* x, const void* gx,
-                           void* partial, int64_t nblk, void* gc, cudaStream_t st) {
-  (void)nblk;
+                           void* partial, void* part, void* gc, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
   const int shape = shape_of(s->n);
   int pi = prof_begin(s, "adjoint_fp64", st);
@@ -1405,7 +1434,9 @@ cudaError_t launch_adjoint(hpt_system s, int64_t p, const void* ext, const void*
   prof_end(s, pi, st);
   if (e != cudaSuccess) return e;
   pi = prof_begin(s, "adjoint_sum", st);
-  sum_columns_kernel<<<blocks_for(s->M, 128), 128, 0, st>>>(p, s->M, (const double2*)partial, (double2*)gc);
+  sum_columns_part_kernel<<<dim3((unsigned)((s->M + 31) / 32), kAdjRowBlocks), 256, 0, st>>>(
+      p, s->M, (const double2*)partial, (double2*)part);
+  sum_columns_kernel<<<blocks_for(s->M, 128), 128, 0, st>>>(s->M, (const double2*)part, (double2*)gc);
   prof_end(s, pi, st);
   return cudaGetLastError();
 }

@@ -41,16 +41,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// The coefficient GEMM [D_z h | D_tau h | h] = E B^T in three passes,
-// hi*hi, hi*lo and lo*hi, each into an accumulator of its own (tensor-memory
-// columns tj, tj + nj, tj + 2 nj), so that no pass waits on another: four
-// dependent MMAs per accumulator at K = 64 instead of one chain of twelve.
-// a_hi, a_lo, b_hi, b_lo are the descriptors of the first 256-byte K-slice;
-// a K-slice adds 16 to a descriptor's address field.
-// WARP: the whole warp calls it (elected issue), else one thread.
-template <bool WARP>
-__device__ __forceinline__ void coef_gemm3(uint32_t tj, uint32_t nj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
-                                           uint64_t b_lo, uint32_t idesc, int kslices);
+// The coefficient GEMM [D_z h | D_tau h | h] = E B^T in three passes per
+// K-slice, hi*hi, hi*lo and lo*hi, into one accumulator at tensor-memory
+// column tj.  a_hi, a_lo, b_hi, b_lo are the descriptors of the first
+// 256-byte K-slice; a K-slice adds 16 to a descriptor's address field.  The
+// whole warp calls it; one elected lane issues.  (Three accumulators, one per
+// pass, measured no faster: the MMAs here are bound by their issue, not by
+// the accumulation chain.)
+__device__ __forceinline__ void coef_gemm(uint32_t tj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi, uint64_t b_lo,
+                                          uint32_t idesc, int kslices);
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -81,32 +80,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <bool WARP>
-__device__ __forceinline__ void coef_gemm3(uint32_t tj, uint32_t nj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi,
-                                           uint64_t b_lo, uint32_t idesc, int kslices) {
+__device__ __forceinline__ void coef_gemm(uint32_t tj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi, uint64_t b_lo,
+                                          uint32_t idesc, int kslices) {
   for (int s = 0; s < kslices; ++s) {
-    if (WARP) {
-      mma_bf16_w(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
-      mma_bf16_w(tj + nj, a_hi + 16 * s, b_lo + 16 * s, idesc, s > 0);
-      mma_bf16_w(tj + 2 * nj, a_lo + 16 * s, b_hi + 16 * s, idesc, s > 0);
-    } else {
-      mma_bf16(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
-      mma_bf16(tj + nj, a_hi + 16 * s, b_lo + 16 * s, idesc, s > 0);
-      mma_bf16(tj + 2 * nj, a_lo + 16 * s, b_hi + 16 * s, idesc, s > 0);
-    }
+    mma_bf16_w(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
+    mma_bf16_w(tj, a_hi + 16 * s, b_lo + 16 * s, idesc, 1);
+    mma_bf16_w(tj, a_lo + 16 * s, b_hi + 16 * s, idesc, 1);
   }
-}
-
-// One 8-column chunk of the coefficient GEMM's result: the three pass
-// accumulators at taddr, taddr + nj, taddr + 2 nj, summed (hh + hl) + lh.
-__device__ __forceinline__ void tmem_ld8_coef(uint32_t taddr, uint32_t nj, float (&v)[8]) {
-  uint32_t a[8], b[8], c[8];
-  tmem_ld8(taddr, a);
-  tmem_ld8(taddr + nj, b);
-  tmem_ld8(taddr + 2 * nj, c);
-  tmem_wait_ld();
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = (__uint_as_float(a[q]) + __uint_as_float(b[q])) + __uint_as_float(c[q]);
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
