@@ -558,6 +558,8 @@ hpt_status hpt_batch_create(int32_t nsys, const hpt_system* systems, hpt_batch* 
     mx.off_bhi = std::max(mx.off_bhi, h->ml.off_bhi);     // the largest exponent part
     mx.off_aint = std::max(mx.off_aint, h->ml.off_aint);   // nonzero: some system has large exponents
     mx.off_bigm = std::max(mx.off_bigm, h->ml.off_bigm);
+    mx.tcols1 = std::max(mx.tcols1, tab[s].tcols1);   // per system: its own W and J widths
+    mx.tcols2 = std::max(mx.tcols2, tab[s].tcols2);
     b->tmem_cols = std::max(b->tmem_cols, h->ml.tmem_cols);
     b->nmax = std::max(b->nmax, h->n);
     // evaluation work of one tile: n equations x (exponent + coefficient GEMM + exp)

@@ -14,16 +14,19 @@
 //               its BF16 hi/lo parts as the A operand of the coefficient GEMM;
 //               at the first unit of a tile they also form the log
 //               coordinates (op. 1) of the next tile, a quarter of the
-//               variables per warpgroup;
+//               variables per warpgroup (the four drain warps alone took
+//               three times as long);
 //   drain warps (warps 16-19, one per lane quarter): read the coefficient
 //               accumulator J of unit i from tensor memory and store the row
 //               [D_z h_k | D_tau h_k | h_k] of every point to the scratch;
-//   MMA warp    (warp 20; the whole warp runs the issue loop, one elected lane
-//               issues each MMA and commit): issues the exponent GEMMs of
-//               up to kWBuf - 1 units ahead of the coefficient GEMM of unit
-//               i, so the tensor core works ahead while the exp warps work
-//               on i;
-//   load warp   (warp 21, one thread): bulk-copies the constant image of
+//   MMA issuers (warps 20-23, one per SM sub-partition; each walks its loop
+//               as a whole warp and lane 0 issues): XR and XI issue the Re
+//               and Im halves of the exponent GEMM up to kWBuf units ahead,
+//               CH and CL the E_hi and E_lo parts of the coefficient GEMM
+//               into their own column groups of J, so that four MMAs are in
+//               issue at once (an MMA holds its issuing thread for about a
+//               hundred cycles, whatever its N);
+//   load warp   (warp 24, one thread): bulk-copies the constant image of
 //               each unit's equation (exponent operand, t-exponents, B_k hi/lo)
 //               into a ring of kCBuf buffers, so that a copy starts kCBuf - 1
 //               units ahead of the exponent GEMM that reads it.
@@ -42,9 +45,13 @@ namespace {
 
 constexpr int kExpWarps = 16;
 constexpr int kDrainWarps = 4;
-constexpr int kMmaWarp = kExpWarps + kDrainWarps;
-constexpr int kLoadWarp = kMmaWarp + 1;
-constexpr int kPipeThreads = (kLoadWarp + 1) * 32;   // 704
+constexpr int kXrWarp = kExpWarps + kDrainWarps;      // exponent GEMM, Re half
+constexpr int kXiWarp = kXrWarp + 1;                  // exponent GEMM, Im half
+constexpr int kChWarp = kXrWarp + 2;                  // coefficient GEMM, E_hi part
+constexpr int kClWarp = kXrWarp + 3;                  // coefficient GEMM, E_lo part
+constexpr int kLoadWarp = kXrWarp + 4;
+constexpr int kPipeThreads = (kLoadWarp + 1) * 32;   // 800
+static_assert(kChWarp % 4 != kClWarp % 4 && kXrWarp % 4 != kXiWarp % 4, "issuers on separate sub-partitions");
 constexpr int kCBuf = 4;                              // constant-image ring
 constexpr int kWBuf = 3;                              // exponent accumulators W in tensor memory
 constexpr int kEBuf = 3;                              // coefficient-GEMM A operands E in shared memory
@@ -65,9 +72,11 @@ struct PipeArgs {
 };
 
 // Barriers.  One "coefficient GEMM of unit i done" ring (slot i % kDone)
-// stands for three events: J of unit i full (drain), E buffer of unit i free
-// (exp warps, kEBuf units later), constant buffer of unit i free (loader,
-// kCBuf units later); every waiter is at most one completion behind its slot.
+// stands for three events: J of unit i full (drain), constant buffer of
+// unit i free (loader, kCBuf units later) and E buffer of unit i free (the
+// exponent-GEMM issuers, kEBuf units later, before they issue the GEMM whose
+// W the exp warps wait for); every waiter is at most one completion behind
+// its slot.  The exp warps' "E full" also frees their W buffer.
 // The exp warps' "E full" also frees their W buffer: the MMA warp issues the
 // exponent GEMM into it only after it has waited for that arrival.
 constexpr int kDone = kCBuf;
@@ -122,18 +131,18 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
 
   if (tid == 0) {
     for (int q = 0; q < kCBuf; ++q) mbar_init(bar(B_CFULL + q), 1);
-    for (int q = 0; q < kDone; ++q) mbar_init(bar(B_DONE + q), 1);
+    for (int q = 0; q < kDone; ++q) mbar_init(bar(B_DONE + q), 2);   // CH and CL commits
     for (int q = 0; q < 2; ++q) {
       mbar_init(bar(B_ZFULL + q), kExpWarps);
-      mbar_init(bar(B_ZEMPTY + q), 1);
+      mbar_init(bar(B_ZEMPTY + q), 2);   // XR and XI commits
     }
-    for (int q = 0; q < kWBuf; ++q) mbar_init(bar(B_WFULL + q), 1);
+    for (int q = 0; q < kWBuf; ++q) mbar_init(bar(B_WFULL + q), 2);
     for (int q = 0; q < kEBuf; ++q) mbar_init(bar(B_EFULL + q), kExpWarps);
     for (int q = 0; q < kJBuf; ++q) mbar_init(bar(B_JEMPTY + q), kDrainWarps);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kMmaWarp) {
+  if (warp == kXrWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                  "r"(P.tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -164,7 +173,8 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
     for (int q = 1; q < kCBuf; ++q) o = c == q ? P.s_c[q] : o;
     return o;
   };
-  auto tj_col = [&](int b) { return tbase + (uint32_t)(kWBuf * 2 * S.MP + b * S.NJ); };
+  const int jw = 3 * S.NJ;   // tensor-memory columns of one J buffer (grouped form)
+  auto tj_col = [&](int b) { return tbase + (uint32_t)(kWBuf * 2 * S.MP + b * jw); };
 
   if (warp < kExpWarps) {
     // ---------------- exp warps ----------------
@@ -179,14 +189,23 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       uint8_t* zim = zre + P.z_im;
       const int64_t pos = (int64_t)(t_first + lt) * 128 + row;
       const bool live = pos < P.p;
-      if (wg == 0) {
-        const double tau = live ? tau_in[pos] : 0.0;
-        ((float*)(zre + P.z_tau))[row] = (float)(tau * (double)S.inv_D * 1.4426950408889634);   // (tau/D) log2(e)
+      // all loads first (n <= 16: at most four variables per warpgroup), so
+      // that their latency is paid once
+      float2 yv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = wg + 4 * q;
+        yv[q] = live && j < n ? y[(size_t)pos * n + j] : make_float2(1.f, 0.f);
       }
-      for (int j = wg; j < n; j += 4) {
-        const float2 v = live ? y[(size_t)pos * n + j] : make_float2(1.f, 0.f);
+      const double tau = live && wg == 0 ? tau_in[pos] : 0.0;
+      if (wg == 0)
+        ((float*)(zre + P.z_tau))[row] = (float)(tau * (double)S.inv_D * 1.4426950408889634);   // (tau/D) log2(e)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = wg + 4 * q;
+        if (j >= n) break;
         float rem_r, rem_i;
-        log_coords(v, rem_r, rem_i);
+        log_coords(yv[q], rem_r, rem_i);
         if (S.off_aint) ((uint32_t*)(zre + P.z_q))[j * 128 + row] = fixed_angle(rem_i);
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
@@ -217,8 +236,9 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         tau2 = ((const float*)(sm + zoff(lt & 1) + P.z_tau))[row];
         zq = (const uint32_t*)(sm + zoff(lt & 1) + P.z_q) + row;
       }
+      // W of unit i full; its issuers waited for the coefficient GEMM of
+      // unit i - kEBuf first, so E buffer e is free as well
       if (!wait(B_WFULL + w, use(i, kWBuf))) break;
-      if (i >= kEBuf && !wait(B_DONE + ring(i - kEBuf, kDone), use(i - kEBuf, kDone))) break;
       tc_fence_after();
       // the t-exponents (and large-exponent tables) of unit i's equation,
       // read through L1 from its constant image in global memory
@@ -246,7 +266,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_EFULL + e));   // E full, W buffer free
     }
-  } else if (warp < kMmaWarp) {
+  } else if (warp < kXrWarp) {
     // ---------------- drain warps ----------------
     const int row = (warp & 3) * 32 + lane;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
@@ -258,14 +278,13 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       const bool live = pos < P.p;
       float2* erow = ext + ext_index(pos, k, 0, n);
       for (int c0 = 0; c0 < 2 * (n + 2); c0 += 8) {
-        uint32_t jr[8];
-        tmem_ld8(tj_col(b) + lane_base + c0, jr);
-        tmem_wait_ld();
+        float jr[8];
+        tmem_ld8_j(tj_col(b) + lane_base + c0, S.NJ, true, jr);
         if (live) {
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const int u = c0 / 2 + v;
-            if (u < n + 2) erow[(size_t)u * 128] = make_float2(__uint_as_float(jr[2 * v]), __uint_as_float(jr[2 * v + 1]));
+            if (u < n + 2) erow[(size_t)u * 128] = make_float2(jr[2 * v], jr[2 * v + 1]);
           }
         }
       }
@@ -273,65 +292,63 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_JEMPTY + b));
     }
-  } else if (warp == kMmaWarp) {
-    // ---------------- MMA issuer: the whole warp runs the loop, one elected
-    // lane issues each MMA and commit ----------------
-    {
-      // a failed (timed-out) wait in any lane stops every lane: elect.sync
-      // needs the whole warp
-      auto waitw = [&](int bb, int uu) { return __all_sync(0xffffffffu, wait(bb, uu)); };
+  } else if (warp < kLoadWarp) {
+    // ---------------- MMA issuers: each warp walks its loop together, lane 0
+    // issues each MMA and commit.  Four warps on the four SM sub-partitions,
+    // each owning its own accumulator columns: XR and XI the Re and Im halves
+    // of the exponent GEMM, CH and CL the hi and lo parts of the coefficient
+    // GEMM (an MMA holds its issuing thread for about a hundred cycles, so
+    // four issuers keep the tensor core four times as busy as one) ----------------
+    // a failed (timed-out) wait in any lane stops every lane, so the warp
+    // walks the loop together
+    auto waitw = [&](int bb, int uu) { return __all_sync(0xffffffffu, wait(bb, uu)); };
+    int last = -1;   // the last unit this warp committed
+    if (warp == kXrWarp || warp == kXiWarp) {
+      const bool im = warp == kXiWarp;
       const uint32_t idx_x = idesc_bf16(128, S.MP), sbo_x = S.KX * 16;
-      const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
-      int last_exp = -1, last_coef = -1;
-      auto issue_exp = [&](const Unit& u) -> bool {
+      for (Unit u = first_unit; u.i < U; u = next_unit(u)) {
         const int i = u.i, w = ring(i, kWBuf), c = ring(i, kCBuf), lt = u.lt;
-        if (first_of_tile(u) && !waitw(B_ZFULL + (lt & 1), lt >> 1)) return false;
-        if (!waitw(B_CFULL + c, use(i, kCBuf))) return false;
+        if (first_of_tile(u) && !waitw(B_ZFULL + (lt & 1), lt >> 1)) break;
+        if (!waitw(B_CFULL + c, use(i, kCBuf))) break;
+        // W buffer w free: the exp warps have read W of unit i - kWBuf
+        if (i >= kWBuf && !waitw(B_EFULL + ring(i - kWBuf, kEBuf), use(i - kWBuf, kEBuf))) break;
+        // E buffer of unit i free: the coefficient GEMM of unit i - kEBuf is
+        // done.  The exp warps see it through W of unit i, which completes
+        // after this wait.
+        if (i >= kEBuf && !waitw(B_DONE + ring(i - kEBuf, kDone), use(i - kEBuf, kDone))) break;
         tc_fence_after();
         const uint32_t cb = su32(sm + coff(c));
-        const uint32_t zre = su32(sm + zoff(lt & 1)), zim = zre + (uint32_t)P.z_im;
-        const uint32_t tw = tw_col(w);
+        const uint32_t za = su32(sm + zoff(lt & 1)) + (im ? (uint32_t)P.z_im : 0u);
+        const uint32_t tw = tw_col(w) + (im ? (uint32_t)S.MP : 0u);
         // a K-slice of 256 bytes adds 16 to a descriptor's address field
-        const uint64_t bd = smem_desc(cb + S.off_bexp, 128, sbo_x);
-        const uint64_t ar = smem_desc(zre, 128, sbo_x), ai = smem_desc(zim, 128, sbo_x);
-        for (int s = 0; s < S.KX / 16; ++s) {
-          mma_bf16_w(tw, ar + 16 * s, bd + 16 * s, idx_x, s > 0);
-          mma_bf16_w(tw + S.MP, ai + 16 * s, bd + 16 * s, idx_x, s > 0);
-        }
+        const uint64_t bd = smem_desc(cb + S.off_bexp, 128, sbo_x), ad = smem_desc(za, 128, sbo_x);
+        for (int s = 0; s < S.KX / 16; ++s) mma_bf16_w(tw, ad + 16 * s, bd + 16 * s, idx_x, s > 0);
         mma_commit_w(bar(B_WFULL + w));
         if (last_of_tile(u)) mma_commit_w(bar(B_ZEMPTY + (lt & 1)));
-        last_exp = i;
-        return true;
-      };
-      // the exponent GEMMs run kWBuf - 1 units ahead of the coefficient GEMM
-      // (the exp warps prepare a tile's log coordinates a tile ahead)
-      Unit ahead = first_unit;
-      bool ok = true;
-      for (int q = 0; ok && q < kWBuf - 1 && ahead.i < U; ++q, ahead = next_unit(ahead)) ok = issue_exp(ahead);
-      for (Unit u = first_unit; ok && u.i < U; u = next_unit(u)) {
+        last = i;
+      }
+      if (*sAbort && last >= 0)   // let the MMAs issued land before the CTA's memory goes away
+        mbar_wait(bar(B_WFULL + ring(last, kWBuf)), (uint32_t)use(last, kWBuf) & 1u);
+    } else {
+      const bool lo = warp == kClWarp;
+      const uint32_t sbo_c = S.KC * 16;
+      for (Unit u = first_unit; u.i < U; u = next_unit(u)) {
         const int i = u.i, e = ring(i, kEBuf), b = ring(i, kJBuf), c = ring(i, kCBuf);
-        if (ahead.i < U) {
-          if (!(ok = issue_exp(ahead))) break;
-          ahead = next_unit(ahead);
-        }
-        if (!waitw(B_EFULL + e, use(i, kEBuf))) break;
+        if (!waitw(B_EFULL + e, use(i, kEBuf))) break;   // E of unit i (and so its constants) ready
         if (i >= kJBuf && !waitw(B_JEMPTY + b, use(i, kJBuf) - 1)) break;
         tc_fence_after();
         const uint32_t cb = su32(sm + coff(c));
-        const uint32_t ah0 = su32(sm + eoff(e)), al0 = ah0 + (uint32_t)P.e_lo;
-        const uint32_t tj = tj_col(b);
-        coef_gemm(tj, smem_desc(ah0, 128, sbo_c), smem_desc(al0, 128, sbo_c), smem_desc(cb + S.off_bhi, 128, sbo_c),
-                  smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
+        const uint32_t ea = su32(sm + eoff(e)) + (lo ? (uint32_t)P.e_lo : 0u);
+        const uint64_t ad = smem_desc(ea, 128, sbo_c), bd = smem_desc(cb + S.off_bhi, 128, sbo_c);
+        if (lo)
+          coef_gemm_lo(tj_col(b), ad, bd, S.NJ, S.KC / 16);
+        else
+          coef_gemm_hi(tj_col(b), ad, bd, S.NJ, S.KC / 16);
         mma_commit_w(bar(B_DONE + ring(i, kDone)));
-        last_coef = i;
+        last = i;
       }
-      if (*sAbort) {
-        // let the MMAs issued land before the CTA's memory goes away
-        if (last_coef >= 0)
-          mbar_wait(bar(B_DONE + ring(last_coef, kDone)), (uint32_t)use(last_coef, kDone) & 1u);
-        if (last_exp > last_coef)
-          mbar_wait(bar(B_WFULL + ring(last_exp, kWBuf)), (uint32_t)use(last_exp, kWBuf) & 1u);
-      }
+      if (*sAbort && last >= 0)
+        mbar_wait(bar(B_DONE + ring(last, kDone)), (uint32_t)use(last, kDone) & 1u);
     }
   } else {
     // ---------------- constant loads ----------------
@@ -354,7 +371,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
   tc_fence_before();
   __syncthreads();
   if (*sAbort && tid == 0) atomicExch(err, 1);
-  if (warp == kMmaWarp) {
+  if (warp == kXrWarp) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(P.tmem_cols));
   }
@@ -366,7 +383,7 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
 // serve them).
 int eval_pipe_smem(const MixedSys& s) {
   // the W and J rings in the 512 tensor-memory columns of the SM
-  if (s.n > 16 || s.ne != s.n || kWBuf * 2 * s.MP + kJBuf * s.NJ > 512) return 0;
+  if (s.n > 16 || s.ne != s.n || !s.jst || kWBuf * 2 * s.MP + kJBuf * 3 * s.NJ > 512) return 0;
   auto r1k = [](int v) { return (v + 1023) / 1024 * 1024; };
   const int z = r1k(2 * 128 * s.KX * 2 + 128 * 4 + (s.off_aint ? 128 * s.n * 4 : 0));
   const int e = r1k(2 * 128 * s.KC * 2);
@@ -384,7 +401,7 @@ cudaError_t launch_eval_pipe(hpt_system prof, const MixedSys& s, int64_t p, cons
   const int64_t ntiles = (p + 127) / 128;
   if (ntiles > 0x7fffffff) return cudaErrorInvalidValue;
   a.ntiles = (int)ntiles;
-  int cols = kWBuf * 2 * s.MP + kJBuf * s.NJ, t = 32;
+  int cols = kWBuf * 2 * s.MP + kJBuf * 3 * s.NJ, t = 32;
   while (t < cols) t *= 2;
   if (t > 512) return cudaErrorInvalidValue;
   a.tmem_cols = t;

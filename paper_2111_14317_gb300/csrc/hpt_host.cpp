@@ -357,7 +357,7 @@ static MixedLayout mixed_layout(int n, int max_m, bool big) {
   L.off_bhi = round_up(end, 128);
   L.off_blo = L.off_bhi + L.NJ * L.KC * 2;
   L.chunk_bytes = round_up(L.off_blo + L.NJ * L.KC * 2, 128);
-  int cols = 4 * L.MP + L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
+  int cols = 4 * L.MP + (j_grouped(L.MP, L.NJ) ? 3 : 1) * L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
   while (t < cols) t *= 2;
   L.tmem_cols = t;
   return L;

@@ -53,6 +53,9 @@ struct MixedSys {
   int n, MP, KX, NJ, KC;
   int chunk_bytes, off_bexp, off_bhi, off_blo, off_texp;
   int off_bigm, off_aint;   // 0: no monomial with sum |a_j| > kBigPhase
+  int jst;                  // coefficient GEMM in the grouped form (j_grouped)
+  int tcols1, tcols2;       // tensor-memory columns with one / two W buffers and J
+                            // (for the maxima of a batch: the largest over its systems)
   float inv_D;
   int ne;
   int64_t chunk_off;   // byte offset of the system's constant images
@@ -67,6 +70,14 @@ struct Fp64Sys {
   const double* ahat;
   const double2* b;
 };
+
+// Whether a system's coefficient GEMM takes the grouped form, two MMAs per
+// K-slice into three groups of NJ tensor-memory columns instead of three
+// MMAs into one: when two W accumulators (Re and Im each) and the three J
+// groups fit in the 512 columns of an SM and 2 NJ is a valid MMA width.  It
+// depends on the shapes alone, so every evaluation kernel of a system gives
+// the same bits.
+inline bool j_grouped(int MP, int NJ) { return 4 * MP + 3 * NJ <= 512 && 2 * NJ <= 256; }
 
 // Byte offset of element (r, k) of an R x K bf16 operand in the canonical
 // K-major no-swizzle layout used by the tensor-core descriptors: 8-row x

@@ -119,7 +119,8 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   };
 
   if (tid == 0) {
-    for (int i = 0; i < (SPLIT ? 6 : 5); ++i) mbar_init(su32(&bars[i]), 1);
+    // 2, 3 (W full) and 4 (J full): warps 0 and 1 commit
+    for (int i = 0; i < (SPLIT ? 6 : 5); ++i) mbar_init(su32(&bars[i]), i >= 2 && i <= 4 ? 2 : 1);
     *sAbort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -138,8 +139,8 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
   auto cpar = [&](int g) -> uint32_t { return (uint32_t)(P.nbuf == 2 ? (g >> 1) : g) & 1u; };
 
   // exponent GEMM of work item g (an equation of system S) into W[g & 1];
-  // the whole of warp 0 (one elected lane issues; the operands stay
-  // warp-uniform)
+  // the whole of warps 0 and 1, the Re and the Im half (lane 0 issues; the
+  // operands stay warp-uniform)
   auto issue_exp = [&](int g, const MixedSys& S) -> bool {
     if (!__all_sync(0xffffffffu, mbar_wait(su32(&bars[P.nbuf == 2 ? (g & 1) : 0]), cpar(g)))) return false;
     tc_fence_after();
@@ -148,11 +149,10 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     const uint32_t idx_x = idesc_bf16(128, S.MP), sbo_x = S.KX * 16;
     // a K-slice of 256 bytes adds 16 to a descriptor's address field
     const uint64_t bd = smem_desc(cb + S.off_bexp, 128, sbo_x);
-    const uint64_t ar = smem_desc(su32(sAre), 128, sbo_x), ai = smem_desc(su32(sAim), 128, sbo_x);
-    for (int s = 0; s < S.KX / 16; ++s) {
-      mma_bf16_w(tw, ar + 16 * s, bd + 16 * s, idx_x, s > 0);
-      mma_bf16_w(tw + S.MP, ai + 16 * s, bd + 16 * s, idx_x, s > 0);
-    }
+    const bool im = warp == 1;
+    const uint64_t ad = smem_desc(su32(im ? sAim : sAre), 128, sbo_x);
+    const uint32_t td = tw + (im ? (uint32_t)S.MP : 0u);
+    for (int s = 0; s < S.KX / 16; ++s) mma_bf16_w(td, ad + 16 * s, bd + 16 * s, idx_x, s > 0);
     mma_commit_w(su32(&bars[2 + (g & 1)]));
     return true;
   };
@@ -251,7 +251,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     proxy_fence();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0 && lookahead && !issue_exp(g, S)) atomicExch(sAbort, 1);
+    if (warp < 2 && lookahead && !issue_exp(g, S)) atomicExch(sAbort, 1);
 
     // row kk of the outputs from J: 8-column chunks (4 complex entries)
     // alternate between the warpgroups (NJ is a multiple of 16)
@@ -261,14 +261,13 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       // with stride 128 (ext_index); the solve applies diag(1/y)
       float2* erow = ext ? ext + ext_index(pos, kk, 0, nmax) : nullptr;
       for (int c0 = 8 * half; c0 < S.NJ; c0 += 16) {
-        uint32_t jr[8];
-        tmem_ld8(tj + c0, jr);
-        tmem_wait_ld();
+        float jr[8];
+        tmem_ld8_j(tj + c0, S.NJ, S.jst != 0, jr);
         if (!live) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int u = c0 / 2 + q;
-          const float2 v = make_float2(__uint_as_float(jr[2 * q]), __uint_as_float(jr[2 * q + 1]));
+          const float2 v = make_float2(jr[2 * q], jr[2 * q + 1]);
           if (erow) {
             if (u < n + 2) erow[(size_t)u * 128] = v;
             continue;
@@ -290,7 +289,7 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
     for (int k = kb; k < ke; ++k, ++g) {
       // ---- op. 2a: W = Z A_k (exponent GEMM); with two constant buffers the
       // GEMM of equation k+1 is issued now and runs under this epilogue
-      if (warp == 0) {
+      if (warp < 2) {
         const bool ok1 = lookahead ? (k + 1 < ke ? issue_exp(g + 1, S) : true) : issue_exp(g, S);
         if (!ok1) atomicExch(sAbort, 1);
       }
@@ -325,17 +324,28 @@ eval_mixed_kernel(MixedArgs P, const float2* __restrict__ y, const double* __res
       tc_fence_before();
       __syncthreads();
       if (*sAbort) goto teardown;
-      // ---- op. 2b: [D_z h | D_tau h | h] = E_k B_k^T, split passes
-      if (warp == 0) {   // one elected lane issues (operands warp-uniform)
+      // ---- op. 2b: [D_z h | D_tau h | h] = E_k B_k^T, split passes.  Lane 0
+      // of warp 0 issues (operands warp-uniform); in the grouped form warp 1
+      // issues the E_lo part at the same time (an MMA holds its issuing
+      // thread for about a hundred cycles).  Both commit.
+      if (warp < 2) {
         // split mode: the coefficient part of item g in its own buffer
         if (SPLIT && !__all_sync(0xffffffffu, mbar_wait(su32(&bars[5]), (uint32_t)g & 1u))) atomicExch(sAbort, 1);
         tc_fence_after();
         // cb + off_bhi addresses the coefficient part in either layout
         const uint32_t cb = SPLIT ? su32(sm + P.s_cpart) - (uint32_t)S.off_bhi : su32(cbuf(g));
-        const uint32_t idx_c = idesc_bf16(128, S.NJ), sbo_c = S.KC * 16;
-        coef_gemm(t_j, smem_desc(su32(sAcHi), 128, sbo_c), smem_desc(su32(sAcLo), 128, sbo_c),
-                  smem_desc(cb + S.off_bhi, 128, sbo_c), smem_desc(cb + S.off_blo, 128, sbo_c), idx_c, S.KC / 16);
-        mma_commit_w(su32(&bars[4]));
+        const uint32_t sbo_c = S.KC * 16;
+        const uint64_t ahd = smem_desc(su32(sAcHi), 128, sbo_c), ald = smem_desc(su32(sAcLo), 128, sbo_c);
+        const uint64_t bhd = smem_desc(cb + S.off_bhi, 128, sbo_c);
+        if (S.jst) {
+          if (warp == 0)
+            coef_gemm_hi(t_j, ahd, bhd, S.NJ, S.KC / 16);
+          else
+            coef_gemm_lo(t_j, ald, bhd, S.NJ, S.KC / 16);
+        } else if (warp == 0) {
+          coef_gemm(t_j, ahd, ald, bhd, smem_desc(cb + S.off_blo, 128, sbo_c), S.NJ, S.KC / 16, false);
+        }
+        mma_commit_w(su32(&bars[4]));   // warp 1 without MMAs: arrives at once
       }
       ok = __all_sync(0xffffffffu, mbar_wait(su32(&bars[4]), (uint32_t)g & 1u));
       if (!ok) atomicExch(sAbort, 1);
@@ -440,7 +450,7 @@ cudaError_t launch_core(hpt_system prof, const MixedSys& sys, const MixedSys& ma
     a.nbuf = c[0];
     a.wbuf = c[1];
     a.split = c[2];
-    int cols = a.wbuf * 2 * maxs.MP + maxs.NJ, t = 32;   // W buffers, coefficient accumulator
+    int cols = a.wbuf == 2 ? maxs.tcols2 : maxs.tcols1, t = 32;   // W buffers, coefficient accumulator
     while (t < cols) t *= 2;
     if (t > 512) continue;
     a.tmem_cols = t;
@@ -520,7 +530,7 @@ bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, boo
   // and the fixed angles of large exponents included
   const int smem = r(128 * KX * 2) * 2 + r(128 * n * 8) + (big ? r(128 * n * 4) : 0) + r(128 * KC * 2) * 2 +
                    r(chunk_bytes) + r(128) + 1024;
-  return smem <= max_smem && 2 * MP + NJ <= 512;
+  return smem <= max_smem && 2 * MP + (j_grouped(MP, NJ) ? 3 : 1) * NJ <= 512;
 }
 
 int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }
@@ -539,6 +549,9 @@ MixedSys mixed_sys_of(const hpt_system s) {
   m.off_bhi = L.off_bhi;
   m.off_blo = L.off_blo;
   m.off_texp = L.off_texp;
+  m.jst = j_grouped(L.MP, L.NJ) ? 1 : 0;
+  m.tcols1 = 2 * L.MP + (m.jst ? 3 : 1) * L.NJ;
+  m.tcols2 = 4 * L.MP + (m.jst ? 3 : 1) * L.NJ;
   m.off_bigm = L.off_bigm;
   m.off_aint = L.off_aint;
   m.inv_D = (float)(1.0 / (double)s->D);

@@ -42,14 +42,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b
 }
 
 // The coefficient GEMM [D_z h | D_tau h | h] = E B^T in three passes per
-// K-slice, hi*hi, hi*lo and lo*hi, into one accumulator at tensor-memory
-// column tj.  a_hi, a_lo, b_hi, b_lo are the descriptors of the first
-// 256-byte K-slice; a K-slice adds 16 to a descriptor's address field.  The
-// whole warp calls it; one elected lane issues.  (Three accumulators, one per
-// pass, measured no faster: the MMAs here are bound by their issue, not by
-// the accumulation chain.)
+// K-slice, hi*hi, hi*lo and lo*hi.  a_hi, a_lo, b_hi, b_lo are the
+// descriptors of the first 256-byte K-slice (B_lo's rows follow B_hi's, so
+// b_hi with N = 2 NJ spans both); a K-slice adds 16 to a descriptor's address
+// field.  Grouped (MixedSys::jst): J in three column groups, E_hi [B_hi;
+// B_lo]^T into columns [tj, tj + 2 NJ) by coef_gemm_hi and E_lo B_hi^T into
+// [tj + 2 NJ, tj + 3 NJ) by coef_gemm_lo, J = (hh + hl) + lh; two MMAs per
+// K-slice, and the two parts can be issued by two threads at once (an MMA
+// costs its issuing thread about a hundred cycles whatever its N).  Else
+// three MMAs per K-slice into one accumulator of NJ columns.  The whole warp
+// calls these; lane 0 issues.
+__device__ __forceinline__ void coef_gemm_hi(uint32_t tj, uint64_t a_hi, uint64_t b_hi, int NJ, int kslices);
+__device__ __forceinline__ void coef_gemm_lo(uint32_t tj, uint64_t a_lo, uint64_t b_hi, int NJ, int kslices);
 __device__ __forceinline__ void coef_gemm(uint32_t tj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi, uint64_t b_lo,
-                                          uint32_t idesc, int kslices);
+                                          int NJ, int kslices, bool grouped);
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
@@ -58,17 +64,20 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
 
 // The same two instructions for a whole warp that runs the issue loop
 // together: the operands stay warp-uniform (no per-thread copies into the
-// uniform datapath on every MMA) and one elected lane issues.
+// uniform datapath on every MMA) and lane 0 issues.  Always the same lane:
+// a commit tracks the MMAs its own thread issued before it, and the
+// pipelined evaluation relies on that order.
 __device__ __forceinline__ void mma_bf16_w(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                            uint32_t accumulate) {
   asm volatile(
-      "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+      "{\n .reg .pred p, e;\n .reg .u32 l;\n setp.ne.b32 p, %4, 0;\n mov.u32 l, %%laneid;\n"
+      " setp.eq.u32 e, l, 0;\n"
       " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_commit_w(uint32_t mbar) {
   asm volatile(
-      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      "{\n .reg .pred e;\n .reg .u32 l;\n mov.u32 l, %%laneid;\n setp.eq.u32 e, l, 0;\n"
       " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(mbar)
       : "memory");
 }
@@ -80,13 +89,42 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void coef_gemm_hi(uint32_t tj, uint64_t a_hi, uint64_t b_hi, int NJ, int kslices) {
+  const uint32_t id = idesc_bf16(128, 2 * NJ);
+  for (int s = 0; s < kslices; ++s) mma_bf16_w(tj, a_hi + 16 * s, b_hi + 16 * s, id, s > 0);
+}
+__device__ __forceinline__ void coef_gemm_lo(uint32_t tj, uint64_t a_lo, uint64_t b_hi, int NJ, int kslices) {
+  const uint32_t id = idesc_bf16(128, NJ);
+  for (int s = 0; s < kslices; ++s) mma_bf16_w(tj + 2 * (uint32_t)NJ, a_lo + 16 * s, b_hi + 16 * s, id, s > 0);
+}
 __device__ __forceinline__ void coef_gemm(uint32_t tj, uint64_t a_hi, uint64_t a_lo, uint64_t b_hi, uint64_t b_lo,
-                                          uint32_t idesc, int kslices) {
-  for (int s = 0; s < kslices; ++s) {
-    mma_bf16_w(tj, a_hi + 16 * s, b_hi + 16 * s, idesc, s > 0);
-    mma_bf16_w(tj, a_hi + 16 * s, b_lo + 16 * s, idesc, 1);
-    mma_bf16_w(tj, a_lo + 16 * s, b_hi + 16 * s, idesc, 1);
+                                          int NJ, int kslices, bool grouped) {
+  if (grouped) {
+    coef_gemm_hi(tj, a_hi, b_hi, NJ, kslices);
+    coef_gemm_lo(tj, a_lo, b_hi, NJ, kslices);
+    return;
   }
+  const uint32_t id = idesc_bf16(128, NJ);
+  for (int s = 0; s < kslices; ++s) {
+    mma_bf16_w(tj, a_hi + 16 * s, b_hi + 16 * s, id, s > 0);
+    mma_bf16_w(tj, a_hi + 16 * s, b_lo + 16 * s, id, 1);
+    mma_bf16_w(tj, a_lo + 16 * s, b_hi + 16 * s, id, 1);
+  }
+}
+
+// Eight J columns from c0 of the coefficient accumulator at taddr (grouped:
+// the three column groups added, (hh + hl) + lh).
+__device__ __forceinline__ void tmem_ld8_j(uint32_t taddr, int NJ, bool grouped, float (&v)[8]) {
+  uint32_t a[8], b[8], c[8];
+  tmem_ld8(taddr, a);
+  if (grouped) {
+    tmem_ld8(taddr + (uint32_t)NJ, b);
+    tmem_ld8(taddr + 2 * (uint32_t)NJ, c);
+  }
+  tmem_wait_ld();
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    v[q] = grouped ? (__uint_as_float(a[q]) + __uint_as_float(b[q])) + __uint_as_float(c[q]) : __uint_as_float(a[q]);
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
