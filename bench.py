@@ -147,8 +147,11 @@ def _traffic(kernel):
     rec = json.load(open(path)).get(kernel)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2111_14317_gb300", "csrc", rec["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
+    srcs = rec["source"] if isinstance(rec["source"], list) else [rec["source"]]
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(os.path.join(ROOT, "paper_2111_14317_gb300", "csrc", f), "rb").read())
+    if h.hexdigest()[:16] != rec["source_sha"]:
         return None
     return rec["bytes_per_launch_full"]
 
@@ -804,10 +807,10 @@ def main():
     ap.add_argument("--skip-predictors", action="store_true",
                     help="batch: skip the Euler/Hermite comparison at tol 1e-3 (shorter profiling runs)")
     ap.add_argument("--workload", default="all", choices=["all", "step", "batch", "projective", "paper_shapes",
-                                                             "start_points", "step100"],
+                                                             "start_points", "step100", "adjoint"],
                     help="step: the n=16 hpt_step line only; batch: the many-systems batch only; "
-                         "projective: the projective-form step only (the last two print their own JSON "
-                         "object, for profiling)")
+                         "projective: the projective-form step only; adjoint: the track + adjoint "
+                         "workload only (the others print their own JSON object, for profiling)")
     args = ap.parse_args()
     ws, rank, _ = _dist()
 
@@ -840,13 +843,13 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"batch": run_batch(args, torch.device("cuda", 0))}))
         return
-    if args.workload in ("paper_shapes", "start_points", "step100"):
+    if args.workload in ("paper_shapes", "start_points", "step100", "adjoint"):
         import torch
         from paper_2111_14317_gb300 import build as hbuild
         hbuild.build()
         torch.cuda.set_device(0)
         fn = {"paper_shapes": run_paper_shapes, "start_points": run_start_points,
-              "step100": run_step100}[args.workload]
+              "step100": run_step100, "adjoint": run_track_adjoint}[args.workload]
         print(json.dumps({args.workload: fn(args, torch.device("cuda", 0))}))
         return
     if args.workload == "projective":
