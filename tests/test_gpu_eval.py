@@ -5,7 +5,11 @@ returns): FP64 form <= 1e-11, mixed split-BF16 form <= 2e-4 per evaluation.
 The mixed form holds FP32/BF16 values, whose normal range ends at 1.2e-38
 (BF16 low parts sit 2^-8 lower), so its scale has an absolute floor of 1e-30:
 entries whose whole magnitude sum lies below it (terms with large t-exponents
-at small t, down to 1e-291 here) are compared absolutely.
+at small t, down to 1e-291 here) are compared absolutely.  For H_t = H_tau / t
+the floor applies to H_tau, the FP32 value the kernel accumulates before its
+exact division by t (at t = 2.4e-4 an H_tau of 7e-38 is still an FP32 sum
+of flushed terms, while H_t = 3e-34 would clear a floor applied after the
+division).
 Sizes span several 128-point tiles and a ragged tail; the full 65,536-point
 throughput workload is checked on sampled points.
 """
@@ -41,7 +45,7 @@ def _run(hpt, oracle_mod, s, cell, prec, y, t, sample=None):
     # the library returns dH/dt = (dH/dtau) / t; the oracle returns dH/dtau
     f = FLOOR[prec]
     return (_util.scaled_err(H, Ho, np.maximum(SH, f)), _util.scaled_err(Hy, Hyo, np.maximum(SHy, f)),
-            _util.scaled_err(Ht, Hto / t[:, None], np.maximum(SHt / t[:, None], f)))
+            _util.scaled_err(Ht, Hto / t[:, None], np.maximum(SHt, f) / t[:, None]))
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])

@@ -45,7 +45,7 @@ def _errs(got, ref, scale, t, f):
     (H, Hy, Ht), (Ho, Hyo, Hto), (SH, SHy, SHt) = got, ref, scale
     # the library returns dH/dt = (dH/dtau) / t; the oracles return dH/dtau
     return (_util.scaled_err(H, Ho, np.maximum(SH, f)), _util.scaled_err(Hy, Hyo, np.maximum(SHy, f)),
-            _util.scaled_err(Ht, Hto / t[:, None], np.maximum(SHt / t[:, None], f)))
+            _util.scaled_err(Ht, Hto / t[:, None], np.maximum(SHt, f) / t[:, None]))
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])

@@ -62,7 +62,7 @@ def test_projective_eval_parity(hpt, oracle_mod, name, prec):
     SH, SHy, SHt = ps.scale(y, np.log(t))
     f = FLOOR[prec]
     errs = (_util.scaled_err(H, Ho, np.maximum(SH, f)), _util.scaled_err(Hy, Hyo, np.maximum(SHy, f)),
-            _util.scaled_err(Ht, Hto / t[:, None], np.maximum(SHt / t[:, None], f)))
+            _util.scaled_err(Ht, Hto / t[:, None], np.maximum(SHt, f) / t[:, None]))
     assert max(errs) <= TOL[prec], errs
 
 
