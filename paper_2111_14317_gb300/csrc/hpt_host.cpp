@@ -337,7 +337,7 @@ static void split2(double v, uint16_t& hi, uint16_t& lo) {
 
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-static MixedLayout mixed_layout(int n, int max_m, bool big) {
+static MixedLayout mixed_layout(int n, int max_m, bool big, bool affine) {
   MixedLayout L;
   L.MP = round_up(max_m, 16);
   L.KX = round_up(3 * n, 16);
@@ -357,7 +357,8 @@ static MixedLayout mixed_layout(int n, int max_m, bool big) {
   L.off_bhi = round_up(end, 128);
   L.off_blo = L.off_bhi + L.NJ * L.KC * 2;
   L.chunk_bytes = round_up(L.off_blo + L.NJ * L.KC * 2, 128);
-  int cols = 4 * L.MP + (j_grouped(L.MP, L.NJ) ? 3 : 1) * L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
+  L.grouped = affine && j_grouped(L.MP, L.NJ);
+  int cols = 4 * L.MP + (L.grouped ? 3 : 1) * L.NJ, t = 32;   // two exponent accumulators (Re, Im each) and J
   while (t < cols) t *= 2;
   L.tmem_cols = t;
   return L;
@@ -412,10 +413,10 @@ static hpt_status upload_constants(hpt_system s, const int32_t* ex) {
     for (int j = 0; j < nv; ++j) s1 += std::abs(ex[(size_t)i * nv + j]);
     big = big || s1 > kBigPhase;
   }
-  ml = mixed_layout(nv, s->max_m, big);
+  ml = mixed_layout(nv, s->max_m, big, nv == s->n);
   int max_smem = 0;
   CUU(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
-  if (!eval_mixed_fits(nv, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, big, max_smem)) {
+  if (!eval_mixed_fits(nv, ml.MP, ml.KX, ml.NJ, ml.KC, ml.chunk_bytes, big, ml.grouped, max_smem)) {
     set_error("%d variables with m_k up to %d exceed the mixed form's on-chip memory", nv, s->max_m);
     return HPT_ENOTSUP;
   }

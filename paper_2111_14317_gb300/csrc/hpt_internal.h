@@ -39,7 +39,8 @@ struct MixedLayout {
   // int16, both in the exponent part; 0 when the system has none
   int off_bigm = 0, off_aint = 0;
   int chunk_bytes = 0;
-  int tmem_cols = 0;     // power of two >= 4 MP + NJ
+  bool grouped = false;  // coefficient GEMM in the grouped form (j_grouped; affine systems only)
+  int tmem_cols = 0;     // power of two >= 4 MP + NJ (3 NJ grouped)
   int smem_bytes = 0;    // dynamic shared memory of the eval kernel
 };
 
@@ -74,9 +75,11 @@ struct Fp64Sys {
 // Whether a system's coefficient GEMM takes the grouped form, two MMAs per
 // K-slice into three groups of NJ tensor-memory columns instead of three
 // MMAs into one: when two W accumulators (Re and Im each) and the three J
-// groups fit in the 512 columns of an SM and 2 NJ is a valid MMA width.  It
-// depends on the shapes alone, so every evaluation kernel of a system gives
-// the same bits.
+// groups fit in the 512 columns of an SM and 2 NJ is a valid MMA width.
+// Affine systems only (the pipelined evaluation and the batch serve those;
+// a projective system keeps the narrower J, so that the bulk-synchronous
+// kernel keeps two CTAs per SM).  It is fixed per system at creation, so
+// every evaluation kernel of a system gives the same bits.
 inline bool j_grouped(int MP, int NJ) { return 4 * MP + 3 * NJ <= 512 && 2 * NJ <= 256; }
 
 // Byte offset of element (r, k) of an R x K bf16 operand in the canonical
@@ -243,7 +246,7 @@ cudaError_t launch_bounded_wait_probe(int32_t* err, cudaStream_t st);
 // Whether the mixed evaluation kernel can run these operand shapes at all
 // (its leanest configuration within max_smem bytes of shared memory and the
 // 512 tensor-memory columns of an SM).
-bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, bool big, int max_smem);
+bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, bool big, bool grouped, int max_smem);
 // Resident eval CTAs per SM the tensor memory allows for tmem_cols (1 or 2).
 int eval_mixed_max_ctas(int tmem_cols);
 MixedSys mixed_sys_of(const hpt_system s);

@@ -524,13 +524,13 @@ cudaError_t launch_bounded_wait_probe(int32_t* err, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, bool big, int max_smem) {
+bool eval_mixed_fits(int n, int MP, int KX, int NJ, int KC, int chunk_bytes, bool big, bool grouped, int max_smem) {
   auto r = [](int v) { return (v + 1023) / 1024 * 1024; };
   // the leanest configuration (one constant buffer, one W accumulator), 1/y
   // and the fixed angles of large exponents included
   const int smem = r(128 * KX * 2) * 2 + r(128 * n * 8) + (big ? r(128 * n * 4) : 0) + r(128 * KC * 2) * 2 +
                    r(chunk_bytes) + r(128) + 1024;
-  return smem <= max_smem && 2 * MP + (j_grouped(MP, NJ) ? 3 : 1) * NJ <= 512;
+  return smem <= max_smem && 2 * MP + (grouped ? 3 : 1) * NJ <= 512;
 }
 
 int eval_mixed_max_ctas(int tmem_cols) { return 512 / tmem_cols >= 2 ? 2 : 1; }
@@ -549,7 +549,7 @@ MixedSys mixed_sys_of(const hpt_system s) {
   m.off_bhi = L.off_bhi;
   m.off_blo = L.off_blo;
   m.off_texp = L.off_texp;
-  m.jst = j_grouped(L.MP, L.NJ) ? 1 : 0;
+  m.jst = L.grouped ? 1 : 0;
   m.tcols1 = 2 * L.MP + (m.jst ? 3 : 1) * L.NJ;
   m.tcols2 = 4 * L.MP + (m.jst ? 3 : 1) * L.NJ;
   m.off_bigm = L.off_bigm;
