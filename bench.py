@@ -233,28 +233,30 @@ def run_gpu(args):
         kern = h.profile_read()
         # end-to-end through the C ABI: every step copies the whole state (one
         # contiguous arena) from pinned host memory to the device, steps it and
-        # copies it back.  Two device states alternate, with the copies in on
+        # copies it back.  Three device states rotate, with the copies in on
         # one stream, the steps on another and the copies out on a third, so
         # step i runs while step i+1's input arrives and step i-1's result
-        # leaves (each direction is ordered against the others by events).
-        e2e_steps = max(4, steps // 2)
-        hin = [hpt.PathState(PATHS, N_VARS, prec, device="cpu", pin=True) for _ in range(2)]
-        hout = [hpt.PathState(PATHS, N_VARS, prec, device="cpu", pin=True) for _ in range(2)]
+        # leaves, and a state's copy out and next copy in have two steps'
+        # time (each direction is ordered against the others by events).
+        e2e_steps = max(6, steps // 2)
+        NB = 3
+        hin = [hpt.PathState(PATHS, N_VARS, prec, device="cpu", pin=True) for _ in range(NB)]
+        hout = [hpt.PathState(PATHS, N_VARS, prec, device="cpu", pin=True) for _ in range(NB)]
         for hh in hin:
             hh.load(pristine)
-        dev2 = [st, hpt.PathState(PATHS, N_VARS, prec, device=dev)]
+        dev2 = [st] + [hpt.PathState(PATHS, N_VARS, prec, device=dev) for _ in range(NB - 1)]
         h2d = hin[0].arena.numel()
         s_in, s_run, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_run = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(NB)]
+        ev_run = [torch.cuda.Event() for _ in range(NB)]
+        ev_out = [torch.cuda.Event() for _ in range(NB)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
-            b = i % 2
+            b = i % NB
             with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev_out[b])          # step i-2's result has left dev2[b]
+                if i >= NB:
+                    s_in.wait_event(ev_out[b])          # step i-NB's result has left dev2[b]
                 dev2[b].arena.copy_(hin[b].arena, non_blocking=True)
                 ev_in[b].record(s_in)
             s_run.wait_event(ev_in[b])
