@@ -794,6 +794,19 @@ def cpu_baseline(seconds=12.0, max_paths=PATHS):
     return done / el, oracle.num_threads(), f"{done} of the {PATHS} paths, one step each, complex128 oracle"
 
 
+def cpu_baseline_one_core(seconds=2.0):
+    """The same oracle step on one host thread (the paper compares one core
+    with eight, Section 8)."""
+    import oracle
+    k = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        v, _, sample = cpu_baseline(seconds)
+    finally:
+        oracle.set_threads(k)
+    return v, sample
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -872,6 +885,7 @@ def main():
     fp_value = whole_job_rate(ws, PATHS, fp["ms_per_step"] * 1e-3)
     kinfo, roof, step_roof = step_roofline(mx, peaks, peak_kind, out["sms"])
     cpu_v, cores, sample = cpu_baseline(args.cpu_seconds)
+    one_v, one_sample = cpu_baseline_one_core(min(3.0, max(0.5, args.cpu_seconds / 4)))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": mx["steps"],
         "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
@@ -887,7 +901,8 @@ def main():
         "roofline": roof,
         "step_roofline": step_roof,
         "kernels": kinfo,
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "one_core": {"value": one_v, "unit": UNIT, "cores": 1, "sample": one_sample}},
         "e2e": {"value": ws * PATHS / mx["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": mx["h2d"],
                 "d2h_bytes_per_step": mx["d2h"]},
         "clocks": mx["clocks"],
