@@ -794,6 +794,37 @@ def cpu_baseline(seconds=12.0, max_paths=PATHS):
     return done / el, oracle.num_threads(), f"{done} of the {PATHS} paths, one step each, complex128 oracle"
 
 
+def cpu_baseline_step100(n_paths=4096):
+    """The oracle (complex128, all host cores) on the paper's protocol: 100
+    consecutive steps in one call on the first n_paths start points of the
+    planted-cell workload that bench's step100 tracks on the GPU."""
+    import oracle
+    import workloads as W
+    from oracle import cells
+    from paper_2111_14317_gb300 import hpt
+    n = N_VARS
+    s, pairs = W.paper_shape(n, N_VARS * M_PER_EQ)
+    ks = np.zeros((n_paths, n), np.int64)
+    ks[:, 0] = np.arange(n_paths)
+    x0 = np.ascontiguousarray(hpt.binomial_points(n, s.m, s.exponents, s.coeffs, pairs, ks))
+    cell = {"kind": "pairs", "pairs": pairs}
+    te = cells.t_exponents(s, cell)
+    osys = oracle.System(s, te["e"], te["D"])
+    P = oracle.Params(tol_accept=1e-3)
+    h = hpt.System.from_laurent(s, cell, hpt.HPT_FP64)   # tau0 = ln(eps0) / s_min, as hpt_paths_init
+    tau0 = h.tau0()
+    h.close()
+    st = oracle.PathState.start(x0, tau0, P.dtau_init)
+    t0 = time.perf_counter()
+    osys.step(P, st, 100)
+    el = time.perf_counter() - t0
+    steps = int(st.steps.sum())
+    return {"paths": n_paths, "path_steps": steps, "s": el, "value": steps / el, "unit": UNIT,
+            "cores": oracle.num_threads(),
+            "sample": f"the first {n_paths} of the step100 workload's paths, 100 steps in one call, "
+                      "complex128 oracle"}
+
+
 def cpu_baseline_one_core(seconds=2.0):
     """The same oracle step on one host thread (the paper compares one core
     with eight, Section 8)."""
@@ -886,6 +917,7 @@ def main():
     kinfo, roof, step_roof = step_roofline(mx, peaks, peak_kind, out["sms"])
     cpu_v, cores, sample = cpu_baseline(args.cpu_seconds)
     one_v, one_sample = cpu_baseline_one_core(min(3.0, max(0.5, args.cpu_seconds / 4)))
+    s100 = cpu_baseline_step100() if args.workload == "all" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": mx["steps"],
         "warmup": args.warmup, "ms_per_step": mx["ms_per_step"], "higher_is_better": True,
@@ -902,7 +934,8 @@ def main():
         "step_roofline": step_roof,
         "kernels": kinfo,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-                         "one_core": {"value": one_v, "unit": UNIT, "cores": 1, "sample": one_sample}},
+                         "one_core": {"value": one_v, "unit": UNIT, "cores": 1, "sample": one_sample},
+                         "step100": s100},
         "e2e": {"value": ws * PATHS / mx["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": mx["h2d"],
                 "d2h_bytes_per_step": mx["d2h"]},
         "clocks": mx["clocks"],
