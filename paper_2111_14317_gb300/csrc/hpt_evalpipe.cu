@@ -76,11 +76,12 @@ struct PipeArgs {
 // unit i free (loader, kCBuf units later) and E buffer of unit i free (the
 // exponent-GEMM issuers, kEBuf units later, before they issue the GEMM whose
 // W the exp warps wait for); every waiter is at most one completion behind
-// its slot.  The exp warps' "E full" also frees their W buffer.
-// The exp warps' "E full" also frees their W buffer: the MMA warp issues the
-// exponent GEMM into it only after it has waited for that arrival.
+// its slot.  The exp warps' "E full" also frees their W buffer: the
+// coefficient GEMM of that unit waits for it, so "done" of unit i - kEBuf
+// tells the exponent-GEMM issuers that W buffer i - kWBuf is free as well.
 constexpr int kDone = kCBuf;
 static_assert(kDone >= kEBuf && kDone >= kJBuf, "done ring");
+static_assert(kWBuf == kEBuf, "the wait for E buffer i - kEBuf also frees W buffer i - kWBuf");
 enum { B_CFULL = 0, B_DONE = B_CFULL + kCBuf, B_ZFULL = B_DONE + kDone, B_ZEMPTY = B_ZFULL + 2,
        B_WFULL = B_ZEMPTY + 2, B_EFULL = B_WFULL + kWBuf, B_JEMPTY = B_EFULL + kEBuf, B_COUNT = B_JEMPTY + kJBuf };
 
@@ -310,11 +311,11 @@ eval_pipe_kernel(PipeArgs P, const float2* __restrict__ y, const double* __restr
         const int i = u.i, w = ring(i, kWBuf), c = ring(i, kCBuf), lt = u.lt;
         if (first_of_tile(u) && !waitw(B_ZFULL + (lt & 1), lt >> 1)) break;
         if (!waitw(B_CFULL + c, use(i, kCBuf))) break;
-        // W buffer w free: the exp warps have read W of unit i - kWBuf
-        if (i >= kWBuf && !waitw(B_EFULL + ring(i - kWBuf, kEBuf), use(i - kWBuf, kEBuf))) break;
         // E buffer of unit i free: the coefficient GEMM of unit i - kEBuf is
-        // done.  The exp warps see it through W of unit i, which completes
-        // after this wait.
+        // done (the exp warps see it through W of unit i, which completes
+        // after this wait).  That GEMM was issued after "E full" of unit
+        // i - kEBuf = i - kWBuf, which the exp warps signal once they have
+        // read its W: so W buffer w is free too, without a wait of its own.
         if (i >= kEBuf && !waitw(B_DONE + ring(i - kEBuf, kDone), use(i - kEBuf, kDone))) break;
         tc_fence_after();
         const uint32_t cb = su32(sm + coff(c));
