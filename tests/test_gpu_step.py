@@ -335,15 +335,34 @@ def test_mixed_step_newton_directions(hpt, oracle_mod, n, m):
     sysm = W.laurent_system(70 + n, n, m, -3, 3, 64, nnz=min(4, n))
     alpha = W.random_alpha(70 + n, n)
     cell = {"kind": "lower", "alpha_num": alpha.tolist(), "denom": 1}
+    y, t = W.random_points(11, 3000, n)
+    _newton_direction_check(hpt, oracle_mod, sysm, cell, y, t, f"n={n}")
+
+
+def test_mixed_step_large_exponents(hpt, oracle_mod):
+    """The pipelined evaluation's fixed-point phase (monomials with sum |a_j|
+    > 64, here 160..820) inside a whole FP32 step: n = 6, 8 monomials per
+    equation, 3,000 points near the unit torus (23 full tiles and a ragged
+    tail), Newton directions as in test_mixed_step_newton_directions."""
+    s = W.large_exponent_system(31, 6, 8, 3, 40, 250)
+    assert (np.abs(s.exponents).sum(1) > 64).sum() == 18
+    cell = {"kind": "lower", "alpha_num": [0] * 6, "denom": 1}
+    y, t = W.torus_points(8, 3000, 6, 0.005)
+    _newton_direction_check(hpt, oracle_mod, s, cell, y, t, "large exponents")
+
+
+def _newton_direction_check(hpt, oracle_mod, sysm, cell, y, t, label):
     te = cells.t_exponents(sysm, cell)
     osys = oracle_mod.System(sysm, te["e"], te["D"])
-    p = 3000
-    y, t = W.random_points(11, p, n)
+    p, n = y.shape
     y = y.astype(np.complex64).astype(np.complex128)
     h = hpt.System.from_laurent(sysm, cell, hpt.HPT_MIXED)
     st = _bench_like_state(hpt, y, t, 1, 0)
+    h.profile(True)
     h.step(st, 1, hpt.Params(tol_accept=3e-3))
     torch.cuda.synchronize()
+    h.profile(False)
+    assert "eval_pipe_tc" in h.profile_read()   # n <= 16: the pipelined evaluation
     g = {k: v.numpy() for k, v in st.to_host().items()}
     o = oracle_mod.PathState.start(y, 0.0, 0.01)
     o.tau[:] = np.log(t)
@@ -362,7 +381,7 @@ def test_mixed_step_newton_directions(hpt, oracle_mod, n, m):
     kappa = np.linalg.cond(A)
     e = np.abs(dg - do).max(-1) / np.abs(do).max(-1)
     miss = int((e > 1e-3 * kappa).sum())
-    print(f"n={n}: {miss} of {e.size} paths beyond 1e-3 kappa_eq, worst e/kappa_eq "
+    print(f"{label}: {miss} of {e.size} paths beyond 1e-3 kappa_eq, worst e/kappa_eq "
           f"{float(np.max(e / kappa)):.3e}, median e {float(np.median(e)):.2e}")
     assert miss == 0 and float(np.median(e)) < 1e-3
     h.close()
