@@ -592,24 +592,24 @@ solve_update_kernel(int n, int64_t p, const void* __restrict__ ext, hpt_paths S,
 // unknowns of the column it pivoted are b_i / u_i.  The pivot of a column is
 // the one of group_solve (largest |.|^2 among the unused rows, ties to the
 // lowest row), so the pivots, the condition proxy and the FP64 re-solve
-// list are those of the LU form.  The owner writes the live part of the
-// pivot row once to shared memory, each entry as (re, im, im, re): a row's
-// update a - l u is then two paired FMAs on one 16-byte load shared by the
-// R rows of a lane.  Rows are shifted as in group_solve (column j is always
-// register 0).
+// list are those of the LU form.  Each entry of the pivot row reaches the
+// group by a shuffle from its owner (every lane selects the pivot's slot, the
+// same in the whole group): no shared-memory round trip, and no per-entry
+// packing by the owner alone, which cost 25 of 140 us.  A row's update
+// a - l u is two paired FMAs with u and u swapped.  Rows are shifted as in
+// group_solve (column j is always register 0).
 template <int NC>
 struct GjSmem {
   union {
     float cm[NC][NC + 4];       // the rows' entry magnitudes, read back by column
     struct {
-      float4 piv[2][NC + 3];    // pivot rows of alternate steps: [0] the pivot, [1..NC) entries, [NC], [NC+1] bE, bN
       float4 x[NC];             // the solutions by column: (xE.re, xE.im, xN.re, xN.im)
     } e;
   } u;
   float dcol[NC];               // the column scales
 };
-// Per-group stride in words, = G (mod 32): the column reads of cm and the
-// broadcast pivot-row reads of the groups of a warp fall on distinct banks.
+// Per-group stride in words, = G (mod 32): the column reads of cm by the
+// groups of a warp fall on distinct banks.
 template <int G, int NC>
 struct GjLayout {
   static constexpr int raw = (int)(sizeof(GjSmem<NC>) / 4);
@@ -717,7 +717,6 @@ __device__ __forceinline__ void gj_path(int n, int nmax, int64_t q, int64_t path
   float pmax = 0.f, pmin = 0.f;   // extreme |u_jj|^2
 #pragma unroll 1
   for (int j = 0; j < n; ++j) {
-    float4* buf = sh.u.e.piv[j & 1];
     unsigned key = 0u;
 #pragma unroll
     for (int s = 0; s < R; ++s) {
@@ -730,36 +729,16 @@ __device__ __forceinline__ void gj_path(int n, int nmax, int64_t q, int64_t path
     const int bs = br / G;
     const bool owner = lane == (br & (G - 1));
     const int lim = n - 1 - j;   // live registers 1..lim
+    // the pivot row by shuffles from its owner: every lane picks slot bs
+    // (uniform in the group) and reads the owner's copy
+    const int ol = br & (G - 1);
+    auto pick_bcast = [&](const uint64_t* col) -> uint64_t {   // col[s] for s < R
+      uint64_t v = col[0];
+#pragma unroll
+      for (int s = 1; s < R; ++s) v = bs == s ? col[s] : v;
+      return __shfl_sync(0xffffffffu, v, ol, G);
+    };
     if (owner) {
-      // the owner's slot chosen entry by entry (a per-slot conditional store
-      // would be turned into a dynamically indexed, local-memory row)
-      uint64_t v0 = a[0][0];
-#pragma unroll
-      for (int s = 1; s < R; ++s) v0 = bs == s ? a[s][0] : v0;
-      const float2 w0 = upk2(v0);
-      buf[0] = make_float4(w0.x, w0.y, 0.f, 0.f);
-#pragma unroll
-      for (int c0 = 1; c0 < NC; c0 += 4) {
-        if (c0 <= lim) {
-#pragma unroll
-          for (int c = c0; c < c0 + 4 && c < NC; ++c) {
-            uint64_t v = a[0][c];
-#pragma unroll
-            for (int s = 1; s < R; ++s) v = bs == s ? a[s][c] : v;
-            const float2 w = upk2(v);
-            buf[c] = make_float4(w.x, w.y, w.y, w.x);
-          }
-        }
-      }
-      uint64_t e = bE[0], f = bN[0];
-#pragma unroll
-      for (int s = 1; s < R; ++s) {
-        e = bs == s ? bE[s] : e;
-        f = bs == s ? bN[s] : f;
-      }
-      const float2 we = upk2(e), wf = upk2(f);
-      buf[NC] = make_float4(we.x, we.y, we.y, we.x);
-      buf[NC + 1] = make_float4(wf.x, wf.y, wf.y, wf.x);
 #pragma unroll
       for (int s = 0; s < R; ++s) {
         if (bs == s) {
@@ -769,8 +748,10 @@ __device__ __forceinline__ void gj_path(int n, int nmax, int64_t q, int64_t path
         }
       }
     }
-    __syncwarp();
-    const float4 pv = buf[0];
+    uint64_t col0[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) col0[s] = a[s][0];
+    const float2 pv = upk2(pick_bcast(col0));
     const float p2 = pv.x * pv.x + pv.y * pv.y;
     if (!(p2 > 0.f) || !isfinite(p2)) ok = false;
     pmax = j == 0 ? p2 : fmaxf(pmax, p2);
@@ -797,16 +778,21 @@ __device__ __forceinline__ void gj_path(int n, int nmax, int64_t q, int64_t path
       if (c0 <= lim) {
 #pragma unroll
         for (int c = c0; c < c0 + 4 && c < NC; ++c) {
-          const float4 u = buf[c];
-          const uint64_t U = pk2(u.x, u.y), US = pk2(u.z, u.w);
+          uint64_t colc[R];
+#pragma unroll
+          for (int s = 0; s < R; ++s) colc[s] = a[s][c];
+          const uint64_t U = pick_bcast(colc);
+          const float2 uf = upk2(U);
+          const uint64_t US = pk2(uf.y, uf.x);
 #pragma unroll
           for (int s = 0; s < R; ++s) a[s][c - 1] = fma_x2(LS[s], US, fma_x2(NL[s], U, a[s][c]));
         }
       }
     }
     {
-      const float4 u = buf[NC], v = buf[NC + 1];
-      const uint64_t U = pk2(u.x, u.y), US = pk2(u.z, u.w), V = pk2(v.x, v.y), VS = pk2(v.z, v.w);
+      const uint64_t U = pick_bcast(bE), V = pick_bcast(bN);
+      const float2 uf = upk2(U), vf = upk2(V);
+      const uint64_t US = pk2(uf.y, uf.x), VS = pk2(vf.y, vf.x);
 #pragma unroll
       for (int s = 0; s < R; ++s) {
         bE[s] = fma_x2(LS[s], US, fma_x2(NL[s], U, bE[s]));
